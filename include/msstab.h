@@ -1,0 +1,248 @@
+/*
+ * msstab.h -- C ABI of libmsstab: M(s)stab(l) and IDR(s)stab(l) for sequences
+ * of sparse linear systems A x^(i) = b^(i) with fixed A, on one GB300 (sm_103a).
+ *
+ * Method: Neuenhofen, "M(s)stab(l): A Generalization of IDR(s)stab(l) for
+ * Sequences of Linear Systems" (arXiv:1604.06043).  msstab_solve runs
+ * Algorithm 1 (IDRstab); the handle keeps the cut space P and, from the
+ * fetching point of an earlier solve on (Section 5), the recycled basis U, V
+ * with V = A U, which later solves take as their start basis -- the M(s)stab
+ * method of Section 4.2.
+ *
+ * Conventions for every entry point below:
+ *  - Pointers named d_* are CUDA device pointers, owned by the caller; pointers
+ *    without the prefix are host pointers.  Vectors are dense, contiguous and
+ *    aligned to their element size.  A block of s vectors of length n is stored
+ *    column by column ("column-major"), column q at base + q * ld.
+ *  - All work is ordered on the stream given at create time (options.stream;
+ *    NULL = the legacy default stream).  Calls on one handle must not overlap;
+ *    a handle is not thread safe.
+ *  - Errors are returned as msstab_status codes, never by abort; the text of
+ *    the last error of a handle is msstab_last_error(h) (h may be NULL for
+ *    errors of msstab_create).
+ *  - Scalars are FP64.  Indices are int32 (n and nnz must fit).
+ */
+#ifndef MSSTAB_H
+#define MSSTAB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct msstab_s* msstab_t;
+
+typedef enum msstab_status {
+  MSSTAB_OK = 0,
+  MSSTAB_ERR_INVALID_ARG = 1, /* bad size, pointer, alignment or CSR structure */
+  MSSTAB_ERR_CUDA = 2,        /* a CUDA runtime call failed (text in msstab_last_error) */
+  MSSTAB_ERR_OOM = 3,         /* device or pinned-host allocation failed */
+  MSSTAB_ERR_BREAKDOWN = 4,   /* a projected s x s system was singular (Section 2.2 canonical case violated) */
+  MSSTAB_ERR_MAXIT = 5,       /* options.max_mvs reached before the tolerance */
+  MSSTAB_ERR_NAN = 6          /* the residual norm became NaN or Inf */
+} msstab_status;
+
+enum { MSSTAB_PREC_FP64 = 0, MSSTAB_PREC_FP32_INNER = 1 };
+enum { MSSTAB_FETCH_ONCE = 0, MSSTAB_FETCH_EVERY = 1, MSSTAB_FETCH_NEVER = 2 };
+enum { MSSTAB_FORMAT_SELL = 0, MSSTAB_FORMAT_CSR = 1 };
+
+/* Kernel families, the index into msstab_stats.t_ms / n_launch. */
+enum {
+  MSSTAB_K_SPMV = 0,     /* y = A x, r = b - A x (+ norms) */
+  MSSTAB_K_SPMV_DOT = 1, /* y = A x fused with P^T y and the next small solve */
+  MSSTAB_K_GAMMA = 2,    /* r^(k) -= V^(k) gamma */
+  MSSTAB_K_ETA = 3,      /* v_q^(k) = r^(k+1) - W^(k) eta_q */
+  MSSTAB_K_LAZY = 4,     /* the same updates on levels below k, once per level step */
+  MSSTAB_K_TAU = 5,      /* Gram, tau step, P^T [r, V] */
+  MSSTAB_K_OTHER = 6,    /* Arnoldi start, orthonormalisation, conversions, copies */
+  MSSTAB_K_CNN = 7,      /* learned initial guess */
+  MSSTAB_K_COUNT = 8
+};
+
+typedef struct msstab_options {
+  int32_t precision;       /* MSSTAB_PREC_FP64 (default) or MSSTAB_PREC_FP32_INNER: FP32 inner
+                              M(s)stab on A/rho inside an FP64 defect-correction loop */
+  int32_t fetch_policy;    /* MSSTAB_FETCH_ONCE (default): fetch U,V in the first solve and reuse
+                              them for all later solves; EVERY: pass each solve's final U,V on
+                              (Miltenberger, Section 3.1); NEVER: IDRstab with an Arnoldi start
+                              for every system */
+  double fetch_threshold;  /* fetch at the first cycle end with relres <= this; <= 0: sqrt(tol) */
+  int32_t fetch_cycle;     /* > 0: fetch at the end of this cycle instead of by threshold */
+  int32_t orth_recycle;    /* 1 (default): orthonormalise the fetched V (and U alongside) by
+                              Cholesky QR twice; 0: keep them as fetched */
+  int64_t max_mvs;         /* products with A per solve; <= 0: min(100000, 20 sqrt(n) + 1 + s + 2l(s+1)) */
+  double inner_tol;        /* FP32 inner: relative tolerance of each inner solve (tested on its
+                              recursive residual); <= 0: max(1e-4, 0.5 tol ||b|| / ||r_outer||) */
+  int32_t spmv_format;     /* MSSTAB_FORMAT_SELL (default, SELL-32-sigma) or MSSTAB_FORMAT_CSR */
+  int32_t sell_sigma;      /* SELL sorting window in rows (1 = no sorting, default; else a
+                              multiple of 32) */
+  int32_t kernel_timing;   /* 1: time every launch with CUDA events (msstab_stats.t_ms) */
+  int32_t max_outer;       /* FP32 inner: defect-correction iterations per solve; <= 0: 20 */
+  int32_t reserved[4];
+  void* stream;            /* cudaStream_t for all work of the handle; NULL = default stream */
+} msstab_options;
+
+typedef struct msstab_stats {
+  int64_t mvs;            /* all products with A in the call (FP64 and FP32) */
+  int64_t mvs_fp32;       /* of which with the FP32 copy A/rho */
+  int64_t cycles;         /* cycles of Algorithm 1 (inner cycles for FP32_INNER) */
+  int64_t outer;          /* defect-correction iterations (FP32_INNER), else 0 */
+  int64_t launches;       /* kernel launches of this library in the call */
+  double relres_true;     /* ||b - A x|| / ||b|| of the returned x (FP64) */
+  double relres_rec;      /* recursive residual at the last cycle end (FP64 mode) */
+  double ms;              /* device time of the call (CUDA events on the stream) */
+  int32_t status;         /* the returned msstab_status */
+  int32_t fetched;        /* 1 if this call wrote the recycle store */
+  int32_t used_recycle;   /* 1 if this call started from recycled U,V */
+  int32_t guess_used;     /* set by msstab_select_guess */
+  double t_ms[MSSTAB_K_COUNT];     /* per kernel family, when options.kernel_timing */
+  int64_t n_launch[MSSTAB_K_COUNT];
+} msstab_stats;
+
+/* Fill *opt with the defaults described above. */
+void msstab_default_options(msstab_options* opt);
+
+/*
+ * Create a solver for the n x n matrix A (CSR: d_row_ptr[n+1], d_col[nnz],
+ * d_val[nnz], int32 indices, FP64 values) with cut-space dimension s and
+ * stabilisation degree l (Algorithm 1's s and l; 1 <= s <= 16, 1 <= l <= 8,
+ * s <= n).  d_p_raw (s columns of length n, ld = n) is the raw random basis of
+ * the cut space P; it is orthonormalised on the device (Cholesky QR, twice) and
+ * kept, with an FP32 copy, for the lifetime of the handle (Section 2.4: the
+ * basis of P may be random; Section 4.2: P stays fixed over the sequence).
+ * The matrix is copied (the caller may free its arrays afterwards), converted
+ * to SELL-32-sigma if chosen, and an FP32 copy of A/rho, rho = max|a_ii|, is
+ * made.  The CSR structure is validated on the device (row_ptr monotone,
+ * columns in range).  opt may be NULL (defaults).
+ */
+msstab_status msstab_create(int64_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col,
+                            const double* d_val, int32_t s, int32_t ell, const double* d_p_raw,
+                            const msstab_options* opt, msstab_t* out);
+
+/*
+ * Solve A x = b to ||b - A x|| <= tol ||b|| (Algorithm 1; the stopping test is
+ * the recursive residual at cycle ends, confirmed by the true residual, which
+ * replaces r if it fails).  d_x holds x0 on entry and the solution on return.
+ * The start basis is the recycled U, V if the handle holds them (M(s)stab), else
+ * the Arnoldi basis of level s of the initial residual (IDRstab).  In the first
+ * solves, U, V are written to the recycle store at the fetching point
+ * (Section 5).  Blocks until the stats are final.  On BREAKDOWN, MAXIT or NAN,
+ * d_x holds the iterate of the last completed cycle (a basis fetched earlier in
+ * the same solve is kept).  st may be NULL.
+ */
+msstab_status msstab_solve(msstab_t h, const double* d_b, double* d_x, double tol, msstab_stats* st);
+
+/* As msstab_solve with host buffers b[n] and x[n]: the copies to and from the
+ * device (through handle-owned staging memory) are part of the call. */
+msstab_status msstab_solve_host(msstab_t h, const double* b, double* x, double tol, msstab_stats* st);
+
+/* Free all device and host memory of the handle.  NULL is accepted. */
+msstab_status msstab_destroy(msstab_t h);
+
+/* Text of the last error of h (or of the last failed create when h is NULL). */
+const char* msstab_last_error(msstab_t h);
+
+/* The per-cycle relative recursive residuals of the last solve (the start value
+ * first) and the MV count at each of those points; copies min(cap, count). */
+msstab_status msstab_history(msstab_t h, double* relres, int64_t* mvs, int32_t cap, int32_t* count);
+
+/* Drop the recycled U, V (the next solve starts from an Arnoldi basis again). */
+msstab_status msstab_reset_recycle(msstab_t h);
+
+/* *flag = 1 if the handle holds recycled U, V. */
+msstab_status msstab_has_recycle(msstab_t h, int32_t* flag);
+
+/* Copy the recycled basis out (d_U, d_V: s columns each, ld = n) or in.  With
+ * these a sequence can be resumed by another handle on the same A and P. */
+msstab_status msstab_export_recycle(msstab_t h, double* d_U, double* d_V);
+msstab_status msstab_import_recycle(msstab_t h, const double* d_U, const double* d_V);
+
+/*
+ * Learned initial guess (selection step).  Given the previous solution d_xprev
+ * and a correction d_delta (e.g. from msstab_cnn_infer), set
+ *   d_x = d_xprev + d_delta  if ||b - A (x_prev + delta)|| < ||b - A x_prev||,
+ *   d_x = d_xprev            otherwise,
+ * using two products with A (FP64).  *used = 1 if the correction was kept.
+ */
+msstab_status msstab_select_guess(msstab_t h, const double* d_b, const double* d_xprev,
+                                  const double* d_delta, double* d_x, int32_t* used);
+
+/* ---------------------------------------------------------------------------
+ * Kernel-level entry points on a handle (for testing and measuring single
+ * kernels).  prec selects FP64 (0: double vectors, the matrix A) or FP32 (1:
+ * float vectors, the matrix A/rho).  They use the handle's matrix format,
+ * orthonormal P, stream and scratch.  Layout of the level arrays, as in the
+ * solver: d_R holds r^(0..l) (l+1 columns), d_V holds V^(-1..l) with v_q^(i)
+ * (q = 0..s-1) in column (i+1)*s + q; both with leading dimension ld >= n.
+ * Small coefficient vectors (gamma, eta, tau) are FP64 device arrays.
+ * ------------------------------------------------------------------------- */
+
+/* y = A x (products with A; Algorithm 1, the MV steps). */
+msstab_status msstab_op_spmv(msstab_t h, int32_t prec, const void* d_x, void* d_y);
+
+/* r = b - A x and d_out[0] = ||r||^2, d_out[1] = ||b||^2 (FP64). */
+msstab_status msstab_op_residual(msstab_t h, const double* d_b, const double* d_x, double* d_r,
+                                 double* d_out);
+
+/* y = A x fused with d_dots[c] = p_c . y, c = 0..s-1, and d_dots[s] = y . y
+ * (the projections P^T w that the gamma and eta solves of Algorithm 1 need). */
+msstab_status msstab_op_spmv_dot(msstab_t h, int32_t prec, const void* d_x, void* d_y, double* d_dots);
+
+/* d_y = alpha d_x + beta d_z (FP64, n entries; d_y may alias d_x or d_z).  Forms
+ * the implicit-Euler right-hand side b = x^(i)/tau + f of a time-stepping
+ * sequence on the device. */
+msstab_status msstab_op_axpby(msstab_t h, double alpha, const double* d_x, double beta, const double* d_z,
+                              double* d_y);
+
+/* Copy the orthonormal cut-space basis P out (s columns, ld = n). */
+msstab_status msstab_op_get_p(msstab_t h, int32_t prec, void* d_P);
+
+/* d_out[t * ny + c] = X_t . Y_c for t < nx, c < ny (nx, ny <= 16; columns at
+ * base + index * ld). */
+msstab_status msstab_op_multidot(msstab_t h, int32_t prec, const void* d_X, int64_t ldx, int32_t nx,
+                                 const void* d_Y, int64_t ldy, int32_t ny, double* d_out);
+
+/* r^(k) -= V^(k) gamma (Algorithm 1, the gamma update on the top level k). */
+msstab_status msstab_op_gamma_update(msstab_t h, int32_t prec, void* d_R, const void* d_V, int64_t ld,
+                                     int32_t k, const double* d_gamma);
+
+/* v_q^(k) = r^(k+1) - [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}] eta_q (Algorithm 1, the
+ * eta update on level k for column q, 0-based). */
+msstab_status msstab_op_eta_update(msstab_t h, int32_t prec, const void* d_R, void* d_V, int64_t ld,
+                                   int32_t k, int32_t q, const double* d_eta);
+
+/* The updates of level step k on the levels below k, applied once after the
+ * q loop: x^(0) += V^(-1) gamma and r^(i) -= V^(i) gamma for i < k (with the
+ * V^(i) of the start of the step), then for each level i = k-1..-1 and
+ * q = 0..s-1: v_q^(i) = r^(i+1) - [V^(i+1)_{0:q-1} (new), V^(i)_{q:s-1} (old)] eta_q.
+ * d_eta is s x s, row q = eta_q.  This yields the values of Algorithm 1's
+ * level-by-level updates.  If d_gram is not NULL, d_gram[a*(l+1)+c] =
+ * r^(a) . r^(c) (a, c = 0..l) after the updates. */
+msstab_status msstab_op_lazy_update(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x,
+                                    int64_t ld, int32_t k, const double* d_gamma, const double* d_eta,
+                                    double* d_gram);
+
+/* The degree-l step of Algorithm 1 in place: r = r^(0) - sum tau_i r^(i),
+ * x += sum tau_i r^(i-1), v_q = v_q^(0) - sum tau_i v_q^(i),
+ * u_q = v_q^(-1) - sum tau_i v_q^(i-1) (r into r^(0), v_q into V^(0), u_q into V^(-1)). */
+msstab_status msstab_op_tau_update(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x, int64_t ld,
+                                   const double* d_tau);
+
+/* Solve the n x n system d_M z = d_rhs (d_M row-major, n <= 16) on the device by
+ * Gaussian elimination with partial pivoting; *d_flag = 1 if a pivot fell
+ * below 1e-14 max|M| (z is then zero).  The small solves of Algorithm 1. */
+msstab_status msstab_op_small_solve(msstab_t h, int32_t n, const double* d_M, const double* d_rhs,
+                                    double* d_z, int32_t* d_flag);
+
+/* tau from the (l+1) x (l+1) Gram matrix of [r^(0..l)] (row-major): the normal
+ * equations of min ||r^(0) - Z tau||, diagonally scaled, by Cholesky (LU if
+ * that fails); tau = 0 if a level vector is zero. */
+msstab_status msstab_op_tau_solve(msstab_t h, int32_t ell, const double* d_gram, double* d_tau);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSSTAB_H */

@@ -83,14 +83,17 @@ def lu_solve_pp(M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
     return z
 
 
-def cholesky_upper(G: np.ndarray) -> np.ndarray:
+CHOLQR_REL_TOL = 1e-14
+
+
+def cholesky_upper(G: np.ndarray, rel_tol: float = 0.0) -> np.ndarray:
     """Upper triangular R with R^T R = G, written out; raises ValueError when a
-    diagonal element is not positive."""
+    pivot is not above rel_tol * G_jj (rel_tol = 0: not positive)."""
     n = G.shape[0]
     R = np.zeros_like(G, dtype=np.float64)
     for j in range(n):
         d = G[j, j] - R[:j, j] @ R[:j, j]
-        if not d > 0.0:
+        if not d > rel_tol * G[j, j]:
             raise ValueError("matrix not positive definite")
         R[j, j] = math.sqrt(d)
         for k in range(j + 1, n):
@@ -147,13 +150,14 @@ def orthonormalize_mgs2(X: np.ndarray) -> np.ndarray:
 def cholqr2(U: np.ndarray, V: np.ndarray):
     """Orthonormalise the recycled V and carry U along: V <- V R^-1, U <- U R^-1
     with R^T R = V^T V, twice.  Keeps V = A U and range(V) (only the basis of
-    the recycled space changes)."""
+    the recycled space changes).  Raises ValueError if V is numerically rank
+    deficient (a Cholesky pivot below 1e-14 of its diagonal entry)."""
     U = np.array(U, dtype=np.float64, copy=True)
     V = np.array(V, dtype=np.float64, copy=True)
     s = V.shape[0]
     for _ in range(2):
         G = V @ V.T
-        R = cholesky_upper(G)
+        R = cholesky_upper(G, CHOLQR_REL_TOL)
         # columns: V_new[:, j] = (V[:, j] - sum_{i<j} V_new[:, i] R[i, j]) / R[j, j]
         for j in range(s):
             for i in range(j):
@@ -410,6 +414,14 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
 # M(s)stab over a sequence of systems
 # ----------------------------------------------------------------------------
 
+def _orth_or_none(UV):
+    """The orthonormalised recycled basis, or None (no fetch) if V is rank deficient."""
+    try:
+        return cholqr2(*UV)
+    except ValueError:
+        return None
+
+
 @dataclasses.dataclass
 class SequenceResult:
     x: np.ndarray
@@ -448,9 +460,9 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
         res = idrstab(mv.A, b, x, s, ell, P, U, V, tol, max_mvs=max_mvs,
                       fetch_threshold=thr if want_fetch else None, mv=mv)
         if want_fetch and res.fetched is not None:
-            rec = cholqr2(*res.fetched) if orth_recycle else res.fetched
-        elif policy == "every" and res.U is not None:
-            rec = cholqr2(res.U, res.V) if orth_recycle else (res.U, res.V)
+            rec = _orth_or_none(res.fetched) if orth_recycle else res.fetched
+        elif policy == "every" and res.U is not None and res.cycles > 0 and res.status == OK:
+            rec = _orth_or_none((res.U, res.V)) if orth_recycle else (res.U, res.V)
         solves.append(res)
         if on_solve is not None:
             on_solve(res)

@@ -1,0 +1,542 @@
+// Tall-skinny block kernels of libmsstab: the vector updates of Algorithm 1
+// (gamma step, eta steps, degree-l step), multi-dots with a deterministic
+// single grid-level combine, and the helpers of the Arnoldi start and of the
+// Cholesky-QR orthonormalisation.
+//
+// One row per thread, grid-stride over rows; every column is read with
+// consecutive threads on consecutive rows, so each warp load is one contiguous
+// segment.  Coefficients (gamma, eta, tau) live in device memory, written by
+// the small solve that ran in the last block of the preceding reduction, and
+// are staged in shared memory at kernel start: the host never waits for them.
+
+#include "launch.h"
+
+namespace msk {
+
+template <typename K>
+static int max_grid(K kernel, const Ctx& c, int cap_blocks = MAXBLK) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, NT, 0) != cudaSuccess || nb < 1) nb = 1;
+  int g = nb * c.sms;
+  return g > cap_blocks ? cap_blocks : g;
+}
+
+static inline int clamp_grid(int64_t need, int cap) { return (int)(need < 1 ? 1 : (need < cap ? need : cap)); }
+
+// ---------------------------------------------------------------------------
+// gamma step on the top level:  r^(k) -= V^(k) gamma
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) gamma_eager_kernel(int n, int s, T* __restrict__ R,
+                                                         const T* __restrict__ V, int64_t ld, int k,
+                                                         const double* __restrict__ gamma) {
+  __shared__ T g[SMAX];
+  if (threadIdx.x < s) g[threadIdx.x] = (T)gamma[threadIdx.x];
+  __syncthreads();
+  T* rk = R + (int64_t)k * ld;
+  const T* vk = V + (int64_t)(k + 1) * s * ld;
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
+    T v = rk[row];
+#pragma unroll 4
+    for (int j = 0; j < s; ++j) v -= g[j] * __ldg(vk + (int64_t)j * ld + row);
+    rk[row] = v;
+  }
+}
+
+template <typename T>
+cudaError_t gamma_eager(const Ctx& c, int n, int s, T* R, const T* V, int64_t ld, int k, const double* gamma) {
+  static int cap = max_grid(gamma_eager_kernel<T>, c);
+  gamma_eager_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, R, V, ld, k, gamma);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// eta step on the top level:  v_q^(k) = r^(k+1) - [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}] eta
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) eta_eager_kernel(int n, int s, const T* __restrict__ R, T* V, int64_t ld,
+                                                       int k, int q, const double* __restrict__ eta) {
+  __shared__ T e[SMAX];
+  if (threadIdx.x < s) e[threadIdx.x] = (T)eta[threadIdx.x];
+  __syncthreads();
+  const T* r1 = R + (int64_t)(k + 1) * ld;
+  const T* vk = V + (int64_t)(k + 1) * s * ld;      // V^(k)
+  const T* vk1 = V + (int64_t)(k + 2) * s * ld;     // V^(k+1)
+  T* out = V + ((int64_t)(k + 1) * s + q) * ld;     // v_q^(k)
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
+    T v = __ldg(r1 + row);
+#pragma unroll 4
+    for (int j = 0; j < s; ++j) {
+      const T* col = (j < q ? vk1 : vk) + (int64_t)j * ld;
+      v -= e[j] * col[row];
+    }
+    out[row] = v;
+  }
+}
+
+template <typename T>
+cudaError_t eta_eager(const Ctx& c, int n, int s, const T* R, T* V, int64_t ld, int k, int q, const double* eta) {
+  static int cap = max_grid(eta_eager_kernel<T>, c);
+  eta_eager_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, R, V, ld, k, q, eta);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// updates of level step k on the levels below k, applied once after the q loop
+// ---------------------------------------------------------------------------
+template <typename T, int S>
+__global__ void __launch_bounds__(NT) lazy_kernel(int n, int s, T* R, T* V, T* x, int64_t ld, int k,
+                                                  const double* __restrict__ gamma,
+                                                  const double* __restrict__ eta, int eta_ld) {
+  __shared__ T g[SMAX];
+  __shared__ T e[SMAX * SMAX];
+  if (threadIdx.x < s) g[threadIdx.x] = (T)gamma[threadIdx.x];
+  for (int i = threadIdx.x; i < s * s; i += NT) e[(i / s) * SMAX + (i % s)] = (T)eta[(i / s) * eta_ld + (i % s)];
+  __syncthreads();
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
+    T above[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j)
+      if (j < s) above[j] = V[((int64_t)(k + 1) * s + j) * ld + row];
+    T rup = R[(int64_t)k * ld + row];
+    for (int i = k - 1; i >= -1; --i) {
+      T old[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+        if (j < s) old[j] = V[((int64_t)(i + 1) * s + j) * ld + row];
+      // gamma step of this level step, with V^(i) as it was at its start
+      if (i >= 0) {
+        T ri = R[(int64_t)i * ld + row];
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+          if (j < s) ri -= g[j] * old[j];
+        R[(int64_t)i * ld + row] = ri;
+        // eta steps of this level: new columns from r^(i+1), new V^(i+1), old V^(i)
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q < s) {
+            T v = rup;
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+              if (j < s) v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
+            V[((int64_t)(i + 1) * s + q) * ld + row] = v;
+            old[q] = v;  // later columns q' > q read old[j] only for j >= q' > q
+          }
+        }
+        rup = ri;
+      } else {
+        T xv = x[row];
+#pragma unroll
+        for (int j = 0; j < S; ++j)
+          if (j < s) xv += g[j] * old[j];
+        x[row] = xv;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q < s) {
+            T v = rup;
+#pragma unroll
+            for (int j = 0; j < S; ++j)
+              if (j < s) v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
+            V[(int64_t)q * ld + row] = v;
+            old[q] = v;
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j)
+        if (j < s) above[j] = old[j];
+    }
+  }
+}
+
+template <typename T>
+cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld, int k, const double* gamma,
+                        const double* eta, int eta_ld) {
+  const int64_t need = (n + NT - 1) / NT;
+  if (s <= 4) {
+    static int cap = max_grid(lazy_kernel<T, 4>, c);
+    lazy_kernel<T, 4><<<clamp_grid(need, cap), NT, 0, c.stream>>>(n, s, R, V, x, ld, k, gamma, eta, eta_ld);
+  } else if (s <= 8) {
+    static int cap = max_grid(lazy_kernel<T, 8>, c);
+    lazy_kernel<T, 8><<<clamp_grid(need, cap), NT, 0, c.stream>>>(n, s, R, V, x, ld, k, gamma, eta, eta_ld);
+  } else {
+    static int cap = max_grid(lazy_kernel<T, 16>, c);
+    lazy_kernel<T, 16><<<clamp_grid(need, cap), NT, 0, c.stream>>>(n, s, R, V, x, ld, k, gamma, eta, eta_ld);
+  }
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// degree-l step with fused projections P^T r, P^T V^(0), r.r
+// ---------------------------------------------------------------------------
+template <typename T>
+struct TauArgs {
+  int n, s, ell;
+  T* R;
+  T* V;
+  T* x;
+  T* xbak;
+  int64_t ld;
+  const double* tau;
+  const T* P;
+  int64_t ldp;
+  int do_update, proj;
+  DevState* st;
+  Epi epi;
+  RedScratch rs;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) tau_kernel(TauArgs<T> a) {
+  __shared__ T tau[LMAX];
+  __shared__ EpiScratch ew;
+  __shared__ double smem_w[NWARP * MAXRED];
+  __shared__ double red[MAXRED];
+  __shared__ int s_last;
+  const int nt = a.s + 1;
+  const int t = blockIdx.x % nt;
+  const int chunk = blockIdx.x / nt;
+  const int nchunks = gridDim.x / nt;
+  if (threadIdx.x < a.ell) tau[threadIdx.x] = (T)(a.do_update ? a.tau[threadIdx.x] : 0.0);
+  __syncthreads();
+  double acc[SMAX];
+#pragma unroll
+  for (int i = 0; i < SMAX; ++i) acc[i] = 0.0;
+  double accr = 0.0;
+  const int64_t ld = a.ld;
+  const int stride = nchunks * NT;
+  for (int row = chunk * NT + threadIdx.x; row < a.n; row += stride) {
+    T out;
+    if (t == 0) {
+      T r = a.R[row];
+      if (a.do_update) {
+        const T r0 = r;
+        T xv = a.x[row];
+        T prev = r0;  // r^(i-1)
+        for (int i = 1; i <= a.ell; ++i) {
+          const T ri = a.R[(int64_t)i * ld + row];
+          r -= tau[i - 1] * ri;
+          xv += tau[i - 1] * prev;
+          prev = ri;
+        }
+        a.R[row] = r;
+        a.x[row] = xv;
+        if (a.xbak) a.xbak[row] = xv;
+      }
+      out = r;
+    } else {
+      const int q = t - 1;
+      T v0 = a.V[((int64_t)a.s + q) * ld + row];     // v_q^(0)
+      if (a.do_update) {
+        T um = a.V[(int64_t)q * ld + row];           // v_q^(-1)
+        T vnew = v0, unew = um;
+        T prev = v0;                                  // v_q^(i-1)
+        for (int i = 1; i <= a.ell; ++i) {
+          const T vi = a.V[((int64_t)(i + 1) * a.s + q) * ld + row];
+          vnew -= tau[i - 1] * vi;
+          unew -= tau[i - 1] * prev;
+          prev = vi;
+        }
+        a.V[((int64_t)a.s + q) * ld + row] = vnew;
+        a.V[(int64_t)q * ld + row] = unew;
+        v0 = vnew;
+      }
+      out = v0;
+    }
+    if (a.proj) {
+      const double od = (double)out;
+#pragma unroll
+      for (int c = 0; c < SMAX; ++c)
+        if (c < a.s) acc[c] = fma(od, (double)__ldg(a.P + (int64_t)c * a.ldp + row), acc[c]);
+      accr = fma(od, od, accr);
+    }
+  }
+  if (!a.proj) return;
+  const int m = a.s + (t == 0 ? 1 : 0);
+  double fin[MAXRED];
+#pragma unroll
+  for (int i = 0; i < MAXRED; ++i) fin[i] = i < SMAX && i < a.s ? acc[i < SMAX ? i : 0] : (i == a.s ? accr : 0.0);
+  block_reduce<MAXRED>(fin, m, smem_w, red);
+  if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
+  if (!groups_done(a.rs, t, nt, m, red, &s_last)) return;
+  // very last block: scatter all groups' sums into the device state
+  DevState* st = a.st;
+  for (int i = threadIdx.x; i < nt * a.s; i += NT) {
+    const int tt = i / a.s, cc = i % a.s;
+    const double v = __ldcg(a.rs.group_out + tt * MAXRED + cc);
+    if (tt == 0)
+      st->projR[cc] = v;
+    else
+      st->projV[(tt - 1) * SMAX + cc] = v;
+  }
+  if (threadIdx.x == 0) st->rr = __ldcg(a.rs.group_out + a.s);
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) run_epilogue(a.epi, ew);
+}
+
+template <typename T>
+cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
+                       const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
+                       Epi epi) {
+  static int cap = max_grid(tau_kernel<T>, c, MAXBLK);
+  const int nt = s + 1;
+  int64_t chunks = (n + NT - 1) / NT;
+  int64_t capc = cap / nt;
+  if (capc < 1) capc = 1;
+  if (chunks > capc) chunks = capc;
+  if (chunks < 1) chunks = 1;
+  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs};
+  tau_kernel<T><<<(int)(chunks * nt), NT, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// multi-dot with per-target groups
+// ---------------------------------------------------------------------------
+template <typename T>
+struct MdArgs {
+  MdCols<T> cols;
+  int n, nt, ny, self, ostride;
+  double* out;
+  Epi epi;
+  RedScratch rs;
+};
+
+template <typename T>
+__global__ void __launch_bounds__(NT) multidot_kernel(MdArgs<T> a) {
+  __shared__ EpiScratch ew;
+  __shared__ double smem_w[NWARP * MAXRED];
+  __shared__ double red[MAXRED];
+  __shared__ int s_last;
+  const int t = blockIdx.x % a.nt;
+  const int chunk = blockIdx.x / a.nt;
+  const int nchunks = gridDim.x / a.nt;
+  double acc[MD_MAXC];
+#pragma unroll
+  for (int i = 0; i < MD_MAXC; ++i) acc[i] = 0.0;
+  double accs = 0.0;
+  const T* xt = a.cols.x[t];
+  const int stride = nchunks * NT;
+  for (int row = chunk * NT + threadIdx.x; row < a.n; row += stride) {
+    const double xv = (double)__ldg(xt + row);
+#pragma unroll
+    for (int c = 0; c < MD_MAXC; ++c)
+      if (c < a.ny) acc[c] = fma(xv, (double)__ldg(a.cols.y[c] + row), acc[c]);
+    accs = fma(xv, xv, accs);
+  }
+  const int m = a.ny + a.self;
+  double fin[MAXRED];
+#pragma unroll
+  for (int i = 0; i < MAXRED; ++i) fin[i] = i < MD_MAXC && i < a.ny ? acc[i < MD_MAXC ? i : 0] : (i == a.ny ? accs : 0.0);
+  block_reduce<MAXRED>(fin, m, smem_w, red);
+  if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
+  if (!groups_done(a.rs, t, a.nt, m, red, &s_last)) return;
+  for (int i = threadIdx.x; i < a.nt * m; i += NT) {
+    const int tt = i / m, cc = i % m;
+    a.out[tt * a.ostride + cc] = __ldcg(a.rs.group_out + tt * MAXRED + cc);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) run_epilogue(a.epi, ew);
+}
+
+template <typename T>
+cudaError_t multidot(const Ctx& c, int n, const MdCols<T>& cols, int nt, int ny, int self, double* out,
+                     int ostride, Epi epi) {
+  if (nt < 1 || nt > MD_MAXT || ny < 0 || ny + self > MAXRED || ny > MD_MAXC) return cudaErrorInvalidValue;
+  static int cap = max_grid(multidot_kernel<T>, c, MAXBLK);
+  int64_t chunks = (n + NT - 1) / NT;
+  int64_t capc = cap / nt;
+  if (capc < 1) capc = 1;
+  if (chunks > capc) chunks = capc;
+  if (chunks < 1) chunks = 1;
+  MdArgs<T> a{cols, n, nt, ny, self, ostride, out, epi, c.rs};
+  multidot_kernel<T><<<(int)(chunks * nt), NT, 0, c.stream>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Arnoldi / Cholesky QR helpers
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(NT) cols_axpy_kernel(int n, T* w, const T* U, int64_t ld, int nc,
+                                                       const double* h) {
+  __shared__ double hc[SMAX + 1];
+  if (threadIdx.x < nc) hc[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
+    double v = (double)w[row];
+    for (int c = 0; c < nc; ++c) v -= hc[c] * (double)U[(int64_t)c * ld + row];
+    w[row] = (T)v;
+  }
+}
+
+template <typename T>
+cudaError_t cols_axpy(const Ctx& c, int n, T* w, const T* U, int64_t ld, int nc, const double* h) {
+  static int cap = max_grid(cols_axpy_kernel<T>, c);
+  cols_axpy_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, w, U, ld, nc, h);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) scale_rsqrt_kernel(int n, const T* x, T* y, const double* nrm2) {
+  const double f = 1.0 / sqrt(*nrm2);
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) y[row] = (T)((double)x[row] * f);
+}
+
+template <typename T>
+cudaError_t scale_rsqrt(const Ctx& c, int n, const T* x, T* y, const double* nrm2) {
+  static int cap = max_grid(scale_rsqrt_kernel<T>, c);
+  scale_rsqrt_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, x, y, nrm2);
+  return cudaGetLastError();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(NT) tri_apply_kernel(int n, int s, T* V, T* U, int64_t ld, const double* R) {
+  __shared__ double r[SMAX * SMAX];
+  for (int i = threadIdx.x; i < s * s; i += NT) r[i] = R[i];
+  __syncthreads();
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
+    for (int pass = 0; pass < (U ? 2 : 1); ++pass) {
+      T* M = pass == 0 ? V : U;
+      double v[SMAX];
+#pragma unroll
+      for (int j = 0; j < SMAX; ++j)
+        if (j < s) v[j] = (double)M[(int64_t)j * ld + row];
+#pragma unroll
+      for (int j = 0; j < SMAX; ++j) {
+        if (j < s) {
+          double t = v[j];
+#pragma unroll
+          for (int i = 0; i < SMAX; ++i)
+            if (i < j) t -= v[i] * r[i * s + j];
+          v[j] = t / r[j * s + j];
+          M[(int64_t)j * ld + row] = (T)v[j];
+        }
+      }
+    }
+  }
+}
+
+template <typename T>
+cudaError_t tri_apply(const Ctx& c, int n, int s, T* V, T* U, int64_t ld, const double* R) {
+  static int cap = max_grid(tri_apply_kernel<T>, c);
+  tri_apply_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, V, U, ld, R);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// single-thread small solves
+// ---------------------------------------------------------------------------
+__global__ void small_cholesky_kernel(int s, const double* G, double* R, int* flag) {
+  double g[SMAX * SMAX], r[SMAX * SMAX];
+  for (int i = 0; i < s * s; ++i) g[i] = G[i];
+  const bool ok = cholesky_upper(g, r, s, CHOLQR_REL_TOL);
+  for (int i = 0; i < s * s; ++i) R[i] = ok ? r[i] : (i % (s + 1) == 0 ? 1.0 : 0.0);
+  if (!ok) *flag |= FLAG_CHOL;
+}
+
+cudaError_t small_cholesky(const Ctx& c, int s, const double* G, double* R, int* flag) {
+  small_cholesky_kernel<<<1, 1, 0, c.stream>>>(s, G, R, flag);
+  return cudaGetLastError();
+}
+
+__global__ void small_lu_kernel(int n, const double* M, const double* rhs, double* z, int* flag) {
+  double a[SMAX * SMAX], y[SMAX];
+  for (int i = 0; i < n * n; ++i) a[i] = M[i];
+  for (int i = 0; i < n; ++i) y[i] = rhs[i];
+  const bool ok = lu_solve_pp(a, y, n);
+  for (int i = 0; i < n; ++i) z[i] = y[i];
+  *flag = ok ? 0 : 1;
+}
+
+cudaError_t small_lu(const Ctx& c, int n, const double* M, const double* rhs, double* z, int* flag) {
+  small_lu_kernel<<<1, 1, 0, c.stream>>>(n, M, rhs, z, flag);
+  return cudaGetLastError();
+}
+
+__global__ void small_tau_kernel(int ell, const double* G, double* tau) {
+  double g[(LMAX + 1) * (LMAX + 1)], t[LMAX], wk[2 * LMAX * LMAX + 2 * LMAX];
+  for (int i = 0; i < (ell + 1) * (ell + 1); ++i) g[i] = G[i];
+  tau_from_gram(g, ell, t, wk);
+  for (int i = 0; i < ell; ++i) tau[i] = t[i];
+}
+
+cudaError_t small_tau(const Ctx& c, int ell, const double* G, double* tau) {
+  small_tau_kernel<<<1, 1, 0, c.stream>>>(ell, G, tau);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// precision conversions and vector helpers
+// ---------------------------------------------------------------------------
+__global__ void to_f32_scaled_kernel(int n, const double* x, float* y, double alpha) {
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) y[row] = (float)(x[row] * alpha);
+}
+
+cudaError_t to_f32_scaled(const Ctx& c, int n, const double* x, float* y, double alpha) {
+  static int cap = max_grid(to_f32_scaled_kernel, c);
+  to_f32_scaled_kernel<<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, x, y, alpha);
+  return cudaGetLastError();
+}
+
+__global__ void axpy_f32_into_f64_kernel(int n, const float* x, double* y, double alpha) {
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) y[row] += alpha * (double)x[row];
+}
+
+cudaError_t axpy_f32_into_f64(const Ctx& c, int n, const float* x, double* y, double alpha) {
+  static int cap = max_grid(axpy_f32_into_f64_kernel, c);
+  axpy_f32_into_f64_kernel<<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, x, y, alpha);
+  return cudaGetLastError();
+}
+
+__global__ void axpby_f64_kernel(int n, double alpha, const double* x, double beta, const double* z, double* y) {
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) y[row] = alpha * x[row] + beta * z[row];
+}
+
+cudaError_t axpby_f64(const Ctx& c, int n, double alpha, const double* x, double beta, const double* z,
+                      double* y) {
+  static int cap = max_grid(axpby_f64_kernel, c);
+  axpby_f64_kernel<<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, alpha, x, beta, z, y);
+  return cudaGetLastError();
+}
+
+__global__ void f64_to_f32_n_kernel(int64_t n, const double* x, float* y, double alpha) {
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t i = blockIdx.x * (int64_t)NT + threadIdx.x; i < n; i += stride) y[i] = (float)(x[i] * alpha);
+}
+
+cudaError_t f64_to_f32_n(const Ctx& c, int64_t n, const double* x, float* y, double alpha) {
+  static int cap = max_grid(f64_to_f32_n_kernel, c);
+  f64_to_f32_n_kernel<<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, x, y, alpha);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// explicit instantiations
+// ---------------------------------------------------------------------------
+#define MSK_INST(T)                                                                                       \
+  template cudaError_t multidot<T>(const Ctx&, int, const MdCols<T>&, int, int, int, double*, int, Epi);  \
+  template cudaError_t gamma_eager<T>(const Ctx&, int, int, T*, const T*, int64_t, int, const double*);   \
+  template cudaError_t eta_eager<T>(const Ctx&, int, int, const T*, T*, int64_t, int, int, const double*); \
+  template cudaError_t lazy_update<T>(const Ctx&, int, int, T*, T*, T*, int64_t, int, const double*,      \
+                                      const double*, int);                                                \
+  template cudaError_t tau_update<T>(const Ctx&, int, int, int, T*, T*, T*, T*, int64_t, const double*,   \
+                                     const T*, int64_t, int, int, DevState*, Epi);                        \
+  template cudaError_t cols_axpy<T>(const Ctx&, int, T*, const T*, int64_t, int, const double*);          \
+  template cudaError_t scale_rsqrt<T>(const Ctx&, int, const T*, T*, const double*);                      \
+  template cudaError_t tri_apply<T>(const Ctx&, int, int, T*, T*, int64_t, const double*);
+MSK_INST(double)
+MSK_INST(float)
+
+}  // namespace msk

@@ -1,0 +1,326 @@
+// Internal definitions shared by the CUDA translation units of libmsstab.
+//
+// Deterministic grid reductions: every reduction kernel accumulates per thread
+// over a fixed row mapping, reduces per block in a fixed tree, writes one
+// partial per block and takes a ticket; the last block to arrive sums the
+// partials in index order.  The result does not depend on the order in which
+// blocks run, and no thread ever waits on another block (no spin-waits).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace msk {
+
+constexpr int SMAX = 16;            // largest s
+constexpr int LMAX = 8;             // largest l
+constexpr int NT = 256;             // threads per block of the streaming kernels
+constexpr int NWARP = NT / 32;
+constexpr int MAXRED = 20;          // values per block in one reduction
+constexpr int MAXGRP = 32;          // groups of a two-level reduction; tickets[MAXGRP] is the global one
+constexpr int MAXBLK = 2048;        // blocks of one reduction group
+constexpr double PIVOT_REL_TOL = 1e-14;
+constexpr double CHOLQR_REL_TOL = 1e-14;   // rank test of the Cholesky QR
+
+// Flags raised on the device and read by the host at the cycle end.
+constexpr int FLAG_BREAKDOWN = 1;
+constexpr int FLAG_CHOL = 2;
+
+// ---------------------------------------------------------------------------
+// device-resident state of one solve: projections, coefficients, norms
+// ---------------------------------------------------------------------------
+struct DevState {
+  double projR[(LMAX + 1) * SMAX];          // [i][c] = p_c . r^(i)
+  double projV[(LMAX + 1) * SMAX * SMAX];   // [i][q][c] = p_c . v_q^(i)
+  double gamma[LMAX * SMAX];                // [k][j]
+  double eta[LMAX * SMAX * SMAX];           // [k][q][j] (row q = eta_q)
+  double gram[(LMAX + 1) * (LMAX + 1)];     // [a][c] = r^(a) . r^(c)
+  double tau[LMAX];
+  double rr;                                // ||r||^2 (last reduction that produced it)
+  double bb;                                // ||b||^2
+  double scal[2 * SMAX + 8];                // scratch scalars (Arnoldi, Cholesky QR)
+  double chol[SMAX * SMAX];                 // Cholesky factor R (upper, row-major)
+  double gmat[SMAX * SMAX];                 // Gram matrix for the Cholesky QR
+  int flag;
+};
+
+// What the last block of a reduction kernel does after the final sums.
+enum EpiKind { EPI_NONE = 0, EPI_GAMMA = 1, EPI_ETA = 2, EPI_TAU = 3 };
+
+struct Epi {
+  int kind;
+  int k, q, s, ell;
+  DevState* st;
+};
+
+struct RedScratch {
+  double* partials;       // [blocks][values]
+  double* group_out;      // [groups][values] (two-level reductions)
+  unsigned int* tickets;  // [MAXGRP + 1], zero between launches
+  int max_blocks;         // = MAXBLK
+};
+
+// ---------------------------------------------------------------------------
+// matrices
+// ---------------------------------------------------------------------------
+template <typename T>
+struct CsrMat {
+  int n;
+  const int* row_ptr;
+  const int* col;
+  const T* val;
+};
+
+template <typename T>
+struct SellMat {           // SELL-32-sigma: slice k holds rows perm[32k .. 32k+31]
+  int n;
+  int nslices;
+  const int* slice_ptr;    // [nslices + 1] offsets into col/val
+  const int* slice_w;      // [nslices] entries per row in the slice
+  const int* perm;         // position -> original row, or NULL (sigma = 1)
+  const int* col;          // [slice_ptr[k] + j*32 + lane]
+  const T* val;
+};
+
+// ---------------------------------------------------------------------------
+// reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Reduce acc[0..m) of all threads of the block into red[0..m) (shared).
+// Uses smem_w[NWARP * MAXRED].  Ends with a __syncthreads().
+template <int MAXM>
+__device__ __forceinline__ void block_reduce(const double (&acc)[MAXM], int m, double* smem_w, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+  for (int i = 0; i < MAXM; ++i) {
+    if (i < m) {
+      double v = warp_sum(acc[i]);
+      if (lane == 0) smem_w[w * MAXRED + i] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < m) {
+    double v = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += smem_w[j * MAXRED + threadIdx.x];
+    red[threadIdx.x] = v;
+  }
+  __syncthreads();
+}
+
+// Publish this block's m values as partial `blk` of group `grp` (nblk blocks in
+// the group) and take a ticket.  Returns true in the last block of the group,
+// which then holds the group's sums (in block order) in red[0..m).  The group's
+// ticket is reset for the next launch.
+__device__ __forceinline__ bool grid_reduce(RedScratch rs, int grp, int blk, int nblk, int m, double* red,
+                                            int* s_last) {
+  double* part = rs.partials + ((size_t)grp * rs.max_blocks + blk) * MAXRED;
+  if (threadIdx.x < m) part[threadIdx.x] = red[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(&rs.tickets[grp], 1u);
+    *s_last = (t == (unsigned)(nblk - 1));
+  }
+  __syncthreads();
+  if (!*s_last) return false;
+  __threadfence();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const double* base = rs.partials + (size_t)grp * rs.max_blocks * MAXRED;
+  for (int i = w; i < m; i += nw) {
+    double v = 0.0;
+    for (int b = lane; b < nblk; b += 32) v += __ldcg(base + (size_t)b * MAXRED + i);
+    v = warp_sum(v);
+    if (lane == 0) red[i] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) rs.tickets[grp] = 0u;
+  return true;
+}
+
+// Second level: after the last block of group grp has its sums, publish them
+// and take the global ticket.  Returns true in the very last group's block,
+// which can then read every group's sums from rs.group_out.
+__device__ __forceinline__ bool groups_done(RedScratch rs, int grp, int ngrp, int m, const double* red,
+                                            int* s_last) {
+  if (threadIdx.x < m) rs.group_out[grp * MAXRED + threadIdx.x] = red[threadIdx.x];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    unsigned t = atomicAdd(&rs.tickets[MAXGRP], 1u);
+    *s_last = (t == (unsigned)(ngrp - 1));
+  }
+  __syncthreads();
+  if (!*s_last) return false;
+  __threadfence();
+  if (threadIdx.x == 0) rs.tickets[MAXGRP] = 0u;
+  return true;
+}
+
+// ---------------------------------------------------------------------------
+// small dense solves (single thread; n <= SMAX)
+// ---------------------------------------------------------------------------
+
+// Gaussian elimination with partial pivoting on a (n x n, row-major, modified)
+// and z (rhs in, solution out).  Returns false on a pivot below
+// PIVOT_REL_TOL * max|a| (z is then zeroed).
+__device__ inline bool lu_solve_pp(double* a, double* z, int n) {
+  double scale = 0.0;
+  for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(a[i]));
+  bool ok = scale > 0.0 && isfinite(scale);
+  for (int k = 0; ok && k < n; ++k) {
+    int p = k;
+    double best = fabs(a[k * n + k]);
+    for (int i = k + 1; i < n; ++i) {
+      double v = fabs(a[i * n + k]);
+      if (v > best) { best = v; p = i; }
+    }
+    if (!(best >= PIVOT_REL_TOL * scale)) { ok = false; break; }
+    if (p != k) {
+      for (int j = 0; j < n; ++j) { double t = a[k * n + j]; a[k * n + j] = a[p * n + j]; a[p * n + j] = t; }
+      double t = z[k]; z[k] = z[p]; z[p] = t;
+    }
+    const double piv = a[k * n + k];
+    for (int i = k + 1; i < n; ++i) {
+      const double l = a[i * n + k] / piv;
+      for (int j = k; j < n; ++j) a[i * n + j] -= l * a[k * n + j];
+      z[i] -= l * z[k];
+    }
+  }
+  if (!ok) {
+    for (int i = 0; i < n; ++i) z[i] = 0.0;
+    return false;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double v = z[k];
+    for (int j = k + 1; j < n; ++j) v -= a[k * n + j] * z[j];
+    z[k] = v / a[k * n + k];
+  }
+  return true;
+}
+
+// Upper Cholesky factor R (row-major, R^T R = G) of the n x n matrix G.
+// Returns false if a pivot d_j is not above rel_tol * G_jj (rel_tol = 0: not
+// positive; a positive rel_tol detects numerically rank-deficient bases).
+__device__ inline bool cholesky_upper(const double* G, double* R, int n, double rel_tol = 0.0) {
+  for (int i = 0; i < n * n; ++i) R[i] = 0.0;
+  for (int j = 0; j < n; ++j) {
+    double d = G[j * n + j];
+    for (int i = 0; i < j; ++i) d -= R[i * n + j] * R[i * n + j];
+    if (!(d > rel_tol * G[j * n + j])) return false;
+    const double rjj = sqrt(d);
+    R[j * n + j] = rjj;
+    for (int k = j + 1; k < n; ++k) {
+      double v = G[j * n + k];
+      for (int i = 0; i < j; ++i) v -= R[i * n + j] * R[i * n + k];
+      R[j * n + k] = v / rjj;
+    }
+  }
+  return true;
+}
+
+// tau from the (l+1) x (l+1) Gram matrix of [r^(0..l)] (row-major): scaled
+// normal equations, Cholesky, LU on failure; tau = 0 if a level vector is zero.
+// wk: 2*LMAX*LMAX + 2*LMAX doubles of scratch.
+__device__ inline void tau_from_gram(const double* G, int ell, double* tau, double* wk) {
+  const int L = ell + 1;
+  double* M = wk;
+  double* R = wk + LMAX * LMAX;
+  double* d = wk + 2 * LMAX * LMAX;
+  double* y = d + LMAX;
+  for (int i = 0; i < ell; ++i) {
+    const double g = G[(i + 1) * L + (i + 1)];
+    if (!(g > 0.0)) {
+      for (int k = 0; k < ell; ++k) tau[k] = 0.0;
+      return;
+    }
+    d[i] = 1.0 / sqrt(g);
+  }
+  for (int i = 0; i < ell; ++i) {
+    for (int j = 0; j < ell; ++j) M[i * ell + j] = d[i] * G[(i + 1) * L + (j + 1)] * d[j];
+    y[i] = d[i] * G[(i + 1) * L + 0];
+  }
+  if (cholesky_upper(M, R, ell)) {
+    for (int i = 0; i < ell; ++i) {        // R^T w = y
+      double v = y[i];
+      for (int k = 0; k < i; ++k) v -= R[k * ell + i] * y[k];
+      y[i] = v / R[i * ell + i];
+    }
+    for (int i = ell - 1; i >= 0; --i) {   // R z = w
+      double v = y[i];
+      for (int k = i + 1; k < ell; ++k) v -= R[i * ell + k] * y[k];
+      y[i] = v / R[i * ell + i];
+    }
+  } else {
+    for (int i = 0; i < ell; ++i)
+      for (int j = 0; j < ell; ++j) M[i * ell + j] = d[i] * G[(i + 1) * L + (j + 1)] * d[j];
+    for (int i = 0; i < ell; ++i) y[i] = d[i] * G[(i + 1) * L + 0];
+    if (!lu_solve_pp(M, y, ell))
+      for (int i = 0; i < ell; ++i) y[i] = 0.0;
+  }
+  for (int i = 0; i < ell; ++i) tau[i] = d[i] * y[i];
+}
+
+// Scratch of the epilogue's small solves (shared memory of the last block).
+struct EpiScratch {
+  double a[SMAX * SMAX];
+  double z[SMAX];
+  double g[(LMAX + 1) * (LMAX + 1)];
+  double wk[2 * LMAX * LMAX + 2 * LMAX];
+};
+
+// The small solve that follows a reduction (run by thread 0 of the last block).
+__device__ inline void run_epilogue(const Epi& e, EpiScratch& w) {
+  if (e.kind == EPI_NONE) return;
+  DevState* st = e.st;
+  const int s = e.s;
+  double* a = w.a;
+  double* z = w.z;
+  if (e.kind == EPI_GAMMA) {
+    // (P^T V^(k)) gamma = P^T r^(k)
+    for (int c = 0; c < s; ++c) {
+      for (int j = 0; j < s; ++j) a[c * s + j] = __ldcg(&st->projV[(e.k * SMAX + j) * SMAX + c]);
+      z[c] = __ldcg(&st->projR[e.k * SMAX + c]);
+    }
+    if (!lu_solve_pp(a, z, s)) st->flag |= FLAG_BREAKDOWN;
+    for (int j = 0; j < s; ++j) st->gamma[e.k * SMAX + j] = z[j];
+  } else if (e.kind == EPI_ETA) {
+    // (P^T W^(k)) eta_q = P^T r^(k+1), W^(k) = [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}]
+    for (int c = 0; c < s; ++c) {
+      for (int j = 0; j < s; ++j) {
+        const int lev = j < e.q ? e.k + 1 : e.k;
+        a[c * s + j] = __ldcg(&st->projV[(lev * SMAX + j) * SMAX + c]);
+      }
+      z[c] = __ldcg(&st->projR[(e.k + 1) * SMAX + c]);
+    }
+    if (!lu_solve_pp(a, z, s)) st->flag |= FLAG_BREAKDOWN;
+    for (int j = 0; j < s; ++j) st->eta[(e.k * SMAX + e.q) * SMAX + j] = z[j];
+  } else if (e.kind == EPI_TAU) {
+    const int L = e.ell + 1;
+    for (int i = 0; i < L * L; ++i) w.g[i] = __ldcg(&st->gram[i]);
+    tau_from_gram(w.g, e.ell, st->tau, w.wk);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// launch helpers
+// ---------------------------------------------------------------------------
+struct LaunchCfg {
+  int sms;              // multiprocessors
+  int blocks_per_sm;    // resident blocks of NT threads we aim for
+};
+
+inline int grid_for(const LaunchCfg& lc, int64_t work_items, int items_per_block, int max_blocks) {
+  int64_t need = (work_items + items_per_block - 1) / items_per_block;
+  int64_t cap = (int64_t)lc.sms * lc.blocks_per_sm;
+  if (cap > max_blocks) cap = max_blocks;
+  if (need > cap) need = cap;
+  if (need < 1) need = 1;
+  return (int)need;
+}
+
+}  // namespace msk

@@ -1,0 +1,120 @@
+// Host-side launchers of the CUDA kernels (internal to libmsstab).
+// Every launcher enqueues on ctx.stream and returns the launch status.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace msk {
+
+struct Ctx {
+  cudaStream_t stream;
+  int sms;
+  RedScratch rs;
+};
+
+// Device copy of A: SELL-32-sigma or CSR, FP64 values and FP32 values of A/rho.
+struct MatDesc {
+  int n;
+  int64_t nnz;
+  int format;                 // 0 SELL, 1 CSR
+  // CSR (format 1)
+  const int* row_ptr;
+  const int* col;
+  const double* val64;
+  const float* val32;
+  // SELL (format 0)
+  int nslices;
+  int64_t nnz_sell;           // stored entries including padding
+  const int* slice_ptr;
+  const int* slice_w;
+  const int* perm;
+  const int* scol;
+  const double* sval64;
+  const float* sval32;
+};
+
+// Bytes one product with A moves at minimum (matrix arrays once, x read once,
+// y written once), for the roofline.
+double spmv_bytes(const MatDesc& A, int prec);
+
+// y = A x  (b == NULL) or y = b - A x; with np > 0: out[c] = P_c . y for
+// c < np (P columns at P + c*ldp), then out[np] = y.y if self, then b.b if
+// bdot.  The last block runs the epilogue.
+template <typename T>
+cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
+                 int np, int self, int bdot, double* out, Epi epi);
+
+// Multi-dot: for targets t < nt: out[t*ostride + c] = X_t . Y_c (c < ny) and,
+// if self, out[t*ostride + ny] = X_t . X_t.  Column pointers are given
+// explicitly.  The last block runs the epilogue.
+constexpr int MD_MAXT = 17;
+constexpr int MD_MAXC = 17;
+template <typename T>
+struct MdCols {
+  const T* x[MD_MAXT];
+  const T* y[MD_MAXC];
+};
+template <typename T>
+cudaError_t multidot(const Ctx& c, int n, const MdCols<T>& cols, int nt, int ny, int self, double* out,
+                     int ostride, Epi epi);
+
+// r^(k) -= V^(k) gamma (gamma: s FP64 device values).
+template <typename T>
+cudaError_t gamma_eager(const Ctx& c, int n, int s, T* R, const T* V, int64_t ld, int k, const double* gamma);
+
+// v_q^(k) = r^(k+1) - [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}] eta (eta: s FP64 device values).
+template <typename T>
+cudaError_t eta_eager(const Ctx& c, int n, int s, const T* R, T* V, int64_t ld, int k, int q, const double* eta);
+
+// Updates of level step k on the levels below k (see msstab_op_lazy_update).
+// eta row q at eta + q*eta_ld.
+template <typename T>
+cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld, int k, const double* gamma,
+                        const double* eta, int eta_ld);
+
+// Degree-l step (tau from st->tau if tau == NULL, else from tau), followed
+// (proj != 0) by P^T r, P^T V^(0) and r.r into st->projR[0], st->projV[0],
+// st->rr and the epilogue.  With do_update == 0 only the projections are
+// computed.  xbak (nullable) receives a copy of the new x.
+template <typename T>
+cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
+                       const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
+                       Epi epi);
+
+// w -= sum_{c<nc} h[c] U_c (h: FP64 device), columns U_c at U + c*ld.
+template <typename T>
+cudaError_t cols_axpy(const Ctx& c, int n, T* w, const T* U, int64_t ld, int nc, const double* h);
+
+// y = x * (1 / sqrt(*nrm2))   (device scalar)
+template <typename T>
+cudaError_t scale_rsqrt(const Ctx& c, int n, const T* x, T* y, const double* nrm2);
+
+// V <- V R^-1 and U <- U R^-1 (R upper s x s row-major FP64 device; U may be NULL).
+template <typename T>
+cudaError_t tri_apply(const Ctx& c, int n, int s, T* V, T* U, int64_t ld, const double* R);
+
+// Single-thread kernels: Cholesky (R^T R = G) with flag, LU solve, tau solve.
+cudaError_t small_cholesky(const Ctx& c, int s, const double* G, double* R, int* flag);
+cudaError_t small_lu(const Ctx& c, int n, const double* M, const double* rhs, double* z, int* flag);
+cudaError_t small_tau(const Ctx& c, int ell, const double* G, double* tau);
+
+// Precision conversions: y32 = (float)(x64 * alpha); y64 += alpha * (double)x32;
+// y64 = alpha * x64 + beta * z64.
+cudaError_t to_f32_scaled(const Ctx& c, int n, const double* x, float* y, double alpha);
+cudaError_t axpy_f32_into_f64(const Ctx& c, int n, const float* x, double* y, double alpha);
+cudaError_t axpby_f64(const Ctx& c, int n, double alpha, const double* x, double beta, const double* z,
+                      double* y);
+cudaError_t f64_to_f32_n(const Ctx& c, int64_t n, const double* x, float* y, double alpha);
+
+// Matrix setup: CSR validation (flag bit 1: bad row_ptr, 2: bad column),
+// max |a_ii| (as ordered bits), SELL fill, FP32 scaled copy.
+cudaError_t csr_validate(const Ctx& c, int n, int64_t nnz, const int* row_ptr, const int* col, int* flag);
+cudaError_t csr_max_diag(const Ctx& c, int n, const int* row_ptr, const int* col, const double* val,
+                         unsigned long long* out_bits);
+cudaError_t sell_fill(const Ctx& c, int n, int nslices, const int* row_ptr, const int* col, const double* val,
+                      const int* slice_ptr, const int* slice_w, const int* perm, int* scol, double* sval);
+
+}  // namespace msk

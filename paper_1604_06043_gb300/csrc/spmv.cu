@@ -1,0 +1,292 @@
+// Sparse matrix-vector products of libmsstab: the MV steps of Algorithm 1
+// (r^(k+1) = A r^(k), v_q^(k+1) = A v_q^(k)), the residual b - A x, and the
+// fused form that also returns the s projections P^T (A w) the next small
+// solve of Algorithm 1 needs, so that A w and P^T A w come from one pass.
+//
+// Formats.  SELL-32-sigma: rows in slices of 32 (one warp per slice, one row
+// per lane), entries stored column-major within the slice so that every load of
+// the warp is one contiguous 128/256-byte segment; padding entries carry
+// column -1 and are skipped.  CSR: one thread per row (the baseline format).
+// All loads of matrix data are single-use and go through the read-only path.
+
+#include "launch.h"
+
+namespace msk {
+
+template <typename T>
+__device__ __forceinline__ T ro(const T* p) { return __ldg(p); }
+
+__device__ __forceinline__ double fma_t(double a, double b, double c) { return fma(a, b, c); }
+__device__ __forceinline__ float fma_t(float a, float b, float c) { return fmaf(a, b, c); }
+
+template <typename T>
+struct SpmvArgs {
+  const T* x;
+  T* y;
+  const T* b;
+  const T* P;
+  int64_t ldp;
+  int np, self, bdot;
+  double* out;
+  Epi epi;
+  RedScratch rs;
+};
+
+// Per-thread accumulators of the fused dot products (P^T y, y.y, b.b).
+struct DotAcc {
+  double p[SMAX];
+  double self, bb;
+};
+
+template <typename T>
+__device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc& acc) {
+  const double yd = (double)yv;
+#pragma unroll
+  for (int c = 0; c < SMAX; ++c)
+    if (c < a.np) acc.p[c] = fma(yd, (double)ro(a.P + (int64_t)c * a.ldp + row), acc.p[c]);
+  acc.self = fma(yd, yd, acc.self);
+  if (a.bdot) {
+    const double bd = (double)a.b[row];
+    acc.bb = fma(bd, bd, acc.bb);
+  }
+}
+
+template <typename T, bool DOT>
+__device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc& acc) {
+  if (!DOT) return;
+  __shared__ double smem_w[NWARP * MAXRED];
+  __shared__ double red[MAXRED];
+  __shared__ int s_last;
+  __shared__ EpiScratch ew;
+  const int m = a.np + a.self + a.bdot;
+  double fin[MAXRED];
+#pragma unroll
+  for (int i = 0; i < MAXRED; ++i) {
+    fin[i] = (i < SMAX && i < a.np) ? acc.p[i < SMAX ? i : 0] : 0.0;
+    if (a.self && i == a.np) fin[i] = acc.self;
+    if (a.bdot && i == a.np + a.self) fin[i] = acc.bb;
+  }
+  block_reduce<MAXRED>(fin, m, smem_w, red);
+  if (grid_reduce(a.rs, 0, blockIdx.x, gridDim.x, m, red, &s_last)) {
+    if (threadIdx.x < m) a.out[threadIdx.x] = red[threadIdx.x];
+    __threadfence();
+    __syncthreads();
+    if (threadIdx.x == 0) run_epilogue(a.epi, ew);
+  }
+}
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(NT) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
+  DotAcc acc;
+#pragma unroll
+  for (int i = 0; i < SMAX; ++i) acc.p[i] = 0.0;
+  acc.self = acc.bb = 0.0;
+  const int lane = threadIdx.x & 31;
+  const int nwarps = gridDim.x * NWARP;
+  for (int sl = (blockIdx.x * NT + threadIdx.x) >> 5; sl < A.nslices; sl += nwarps) {
+    const int w = ro(A.slice_w + sl);
+    const int64_t base = (int64_t)ro(A.slice_ptr + sl) + lane;
+    T sum = T(0);
+    int j = 0;
+    for (; j + 8 <= w; j += 8) {
+      int cc[8];
+      T vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        cc[u] = ro(A.col + base + (int64_t)(j + u) * 32);
+        vv[u] = ro(A.val + base + (int64_t)(j + u) * 32);
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (cc[u] >= 0) sum = fma_t(vv[u], ro(a.x + cc[u]), sum);
+    }
+    if (j < w) {
+      int cc[8];
+      T vv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        cc[u] = -1;
+        vv[u] = T(0);
+        if (j + u < w) {
+          cc[u] = ro(A.col + base + (int64_t)(j + u) * 32);
+          vv[u] = ro(A.val + base + (int64_t)(j + u) * 32);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (cc[u] >= 0) sum = fma_t(vv[u], ro(a.x + cc[u]), sum);
+    }
+    const int pos = sl * 32 + lane;
+    if (pos < A.n) {
+      const int row = A.perm ? ro(A.perm + pos) : pos;
+      const T yv = a.b ? (T)(a.b[row] - sum) : sum;
+      a.y[row] = yv;
+      if (DOT) acc_row(a, row, yv, acc);
+    }
+  }
+  finish<T, DOT>(a, acc);
+}
+
+template <typename T, bool DOT>
+__global__ void __launch_bounds__(NT) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a) {
+  DotAcc acc;
+#pragma unroll
+  for (int i = 0; i < SMAX; ++i) acc.p[i] = 0.0;
+  acc.self = acc.bb = 0.0;
+  const int stride = gridDim.x * NT;
+  for (int row = blockIdx.x * NT + threadIdx.x; row < A.n; row += stride) {
+    const int beg = ro(A.row_ptr + row), end = ro(A.row_ptr + row + 1);
+    T sum = T(0);
+    for (int p = beg; p < end; ++p) sum = fma_t(ro(A.val + p), ro(a.x + ro(A.col + p)), sum);
+    const T yv = a.b ? (T)(a.b[row] - sum) : sum;
+    a.y[row] = yv;
+    if (DOT) acc_row(a, row, yv, acc);
+  }
+  finish<T, DOT>(a, acc);
+}
+
+template <typename K>
+static int max_grid(K kernel, const Ctx& c) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, NT, 0) != cudaSuccess || nb < 1) nb = 1;
+  int g = nb * c.sms;
+  return g > MAXBLK ? MAXBLK : g;
+}
+
+template <typename T>
+static const T* pick_val(const MatDesc& A, bool sell);
+template <>
+const double* pick_val<double>(const MatDesc& A, bool sell) { return sell ? A.sval64 : A.val64; }
+template <>
+const float* pick_val<float>(const MatDesc& A, bool sell) { return sell ? A.sval32 : A.val32; }
+
+template <typename T>
+cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
+                 int np, int self, int bdot, double* out, Epi epi) {
+  SpmvArgs<T> a{x, y, b, P, ldp, np, self, bdot, out, epi, c.rs};
+  const bool dot = (np + self + bdot) > 0;
+  if (A.format == 0) {
+    SellMat<T> M{A.n, A.nslices, A.slice_ptr, A.slice_w, A.perm, A.scol, pick_val<T>(A, true)};
+    const int64_t need = ((int64_t)A.nslices * 32 + NT - 1) / NT;
+    if (dot) {
+      static int cap = max_grid(spmv_sell_kernel<T, true>, c);
+      int g = (int)(need < cap ? need : cap);
+      spmv_sell_kernel<T, true><<<g, NT, 0, c.stream>>>(M, a);
+    } else {
+      static int cap = max_grid(spmv_sell_kernel<T, false>, c);
+      int g = (int)(need < cap ? need : cap);
+      spmv_sell_kernel<T, false><<<g, NT, 0, c.stream>>>(M, a);
+    }
+  } else {
+    CsrMat<T> M{A.n, A.row_ptr, A.col, pick_val<T>(A, false)};
+    const int64_t need = ((int64_t)A.n + NT - 1) / NT;
+    if (dot) {
+      static int cap = max_grid(spmv_csr_kernel<T, true>, c);
+      int g = (int)(need < cap ? need : cap);
+      spmv_csr_kernel<T, true><<<g, NT, 0, c.stream>>>(M, a);
+    } else {
+      static int cap = max_grid(spmv_csr_kernel<T, false>, c);
+      int g = (int)(need < cap ? need : cap);
+      spmv_csr_kernel<T, false><<<g, NT, 0, c.stream>>>(M, a);
+    }
+  }
+  return cudaGetLastError();
+}
+
+template cudaError_t spmv<double>(const Ctx&, const MatDesc&, const double*, double*, const double*,
+                                  const double*, int64_t, int, int, int, double*, Epi);
+template cudaError_t spmv<float>(const Ctx&, const MatDesc&, const float*, float*, const float*, const float*,
+                                 int64_t, int, int, int, double*, Epi);
+
+double spmv_bytes(const MatDesc& A, int prec) {
+  const double vb = prec == 0 ? 8.0 : 4.0;
+  if (A.format == 0)
+    return (double)A.nnz_sell * (4.0 + vb) + 8.0 * A.nslices + (A.perm ? 4.0 * A.n : 0.0) + 2.0 * vb * A.n;
+  return (double)A.nnz * (4.0 + vb) + 4.0 * (A.n + 1) + 2.0 * vb * A.n;
+}
+
+// ---------------------------------------------------------------------------
+// matrix setup
+// ---------------------------------------------------------------------------
+
+__global__ void csr_validate_kernel(int n, int64_t nnz, const int* row_ptr, const int* col, int* flag) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int b = row_ptr[i], e = row_ptr[i + 1];
+    if ((i == 0 && b != 0) || (i == n - 1 && (int64_t)e != nnz) || e < b || b < 0 || (int64_t)e > nnz) {
+      atomicOr(flag, 1);
+      continue;
+    }
+    for (int p = b; p < e; ++p) {
+      const int cidx = col[p];
+      if (cidx < 0 || cidx >= n) {
+        atomicOr(flag, 2);
+        break;
+      }
+    }
+  }
+}
+
+cudaError_t csr_validate(const Ctx& c, int n, int64_t nnz, const int* row_ptr, const int* col, int* flag) {
+  int g = (int)((n + NT - 1) / NT);
+  if (g > c.sms * 8) g = c.sms * 8;
+  csr_validate_kernel<<<g, NT, 0, c.stream>>>(n, nnz, row_ptr, col, flag);
+  return cudaGetLastError();
+}
+
+__global__ void csr_max_diag_kernel(int n, const int* row_ptr, const int* col, const double* val,
+                                    unsigned long long* out_bits) {
+  const int stride = gridDim.x * blockDim.x;
+  double m = 0.0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+    for (int p = row_ptr[i]; p < row_ptr[i + 1]; ++p)
+      if (col[p] == i) m = fmax(m, fabs(val[p]));
+  // non-negative doubles order like their bit patterns
+  if (m > 0.0) atomicMax(out_bits, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t csr_max_diag(const Ctx& c, int n, const int* row_ptr, const int* col, const double* val,
+                         unsigned long long* out_bits) {
+  int g = (int)((n + NT - 1) / NT);
+  if (g > c.sms * 8) g = c.sms * 8;
+  csr_max_diag_kernel<<<g, NT, 0, c.stream>>>(n, row_ptr, col, val, out_bits);
+  return cudaGetLastError();
+}
+
+__global__ void sell_fill_kernel(int n, int nslices, const int* row_ptr, const int* col, const double* val,
+                                 const int* slice_ptr, const int* slice_w, const int* perm, int* scol,
+                                 double* sval) {
+  const int64_t total = (int64_t)nslices * 32;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t pos = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; pos < total; pos += stride) {
+    const int sl = (int)(pos >> 5), lane = (int)(pos & 31);
+    const int w = slice_w[sl];
+    const int64_t base = (int64_t)slice_ptr[sl] + lane;
+    int b = 0, len = 0;
+    if (pos < n) {
+      const int row = perm ? perm[pos] : (int)pos;
+      b = row_ptr[row];
+      len = row_ptr[row + 1] - b;
+    }
+    for (int j = 0; j < w; ++j) {
+      const int64_t o = base + (int64_t)j * 32;
+      if (j < len) {
+        scol[o] = col[b + j];
+        sval[o] = val[b + j];
+      } else {
+        scol[o] = -1;
+        sval[o] = 0.0;
+      }
+    }
+  }
+}
+
+cudaError_t sell_fill(const Ctx& c, int n, int nslices, const int* row_ptr, const int* col, const double* val,
+                      const int* slice_ptr, const int* slice_w, const int* perm, int* scol, double* sval) {
+  int g = (int)(((int64_t)nslices * 32 + NT - 1) / NT);
+  if (g > c.sms * 8) g = c.sms * 8;
+  sell_fill_kernel<<<g, NT, 0, c.stream>>>(n, nslices, row_ptr, col, val, slice_ptr, slice_w, perm, scol, sval);
+  return cudaGetLastError();
+}
+
+}  // namespace msk

@@ -1,0 +1,312 @@
+"""Thin ctypes binding to libmsstab (include/msstab.h).
+
+Argument marshalling only: every step of the solver runs in the library's
+CUDA kernels.  Device buffers are torch CUDA tensors (PyTorch provides device
+memory and the stream); their data pointers are passed straight through.  If
+the library is not built, every call raises -- there is no CPU fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+# status codes (msstab_status)
+OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_MAXIT, ERR_NAN = range(7)
+STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "oom", 4: "breakdown", 5: "maxit", 6: "nan"}
+PREC_FP64, PREC_FP32_INNER = 0, 1
+FETCH_ONCE, FETCH_EVERY, FETCH_NEVER = 0, 1, 2
+FORMAT_SELL, FORMAT_CSR = 0, 1
+KERNEL_FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [
+        ("precision", ctypes.c_int32),
+        ("fetch_policy", ctypes.c_int32),
+        ("fetch_threshold", ctypes.c_double),
+        ("fetch_cycle", ctypes.c_int32),
+        ("orth_recycle", ctypes.c_int32),
+        ("max_mvs", ctypes.c_int64),
+        ("inner_tol", ctypes.c_double),
+        ("spmv_format", ctypes.c_int32),
+        ("sell_sigma", ctypes.c_int32),
+        ("kernel_timing", ctypes.c_int32),
+        ("max_outer", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 4),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [
+        ("mvs", ctypes.c_int64),
+        ("mvs_fp32", ctypes.c_int64),
+        ("cycles", ctypes.c_int64),
+        ("outer", ctypes.c_int64),
+        ("launches", ctypes.c_int64),
+        ("relres_true", ctypes.c_double),
+        ("relres_rec", ctypes.c_double),
+        ("ms", ctypes.c_double),
+        ("status", ctypes.c_int32),
+        ("fetched", ctypes.c_int32),
+        ("used_recycle", ctypes.c_int32),
+        ("guess_used", ctypes.c_int32),
+        ("t_ms", ctypes.c_double * 8),
+        ("n_launch", ctypes.c_int64 * 8),
+    ]
+
+    def as_dict(self):
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("t_ms", "n_launch")}
+        d["status_name"] = STATUS_NAMES.get(self.status, str(self.status))
+        d["t_ms"] = dict(zip(KERNEL_FAMILIES, list(self.t_ms)))
+        d["n_launch"] = dict(zip(KERNEL_FAMILIES, list(self.n_launch)))
+        return d
+
+
+class MsstabError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+_P = ctypes.c_void_p
+_I32, _I64, _D = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+_SIGS = {
+    "msstab_default_options": (None, [ctypes.POINTER(Options)]),
+    "msstab_create": (_I32, [_I64, _I64, _P, _P, _P, _I32, _I32, _P, ctypes.POINTER(Options), ctypes.POINTER(_P)]),
+    "msstab_solve": (_I32, [_P, _P, _P, _D, ctypes.POINTER(Stats)]),
+    "msstab_solve_host": (_I32, [_P, _P, _P, _D, ctypes.POINTER(Stats)]),
+    "msstab_destroy": (_I32, [_P]),
+    "msstab_last_error": (ctypes.c_char_p, [_P]),
+    "msstab_history": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
+    "msstab_reset_recycle": (_I32, [_P]),
+    "msstab_has_recycle": (_I32, [_P, ctypes.POINTER(_I32)]),
+    "msstab_export_recycle": (_I32, [_P, _P, _P]),
+    "msstab_import_recycle": (_I32, [_P, _P, _P]),
+    "msstab_select_guess": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "msstab_op_spmv": (_I32, [_P, _I32, _P, _P]),
+    "msstab_op_residual": (_I32, [_P, _P, _P, _P, _P]),
+    "msstab_op_spmv_dot": (_I32, [_P, _I32, _P, _P, _P]),
+    "msstab_op_get_p": (_I32, [_P, _I32, _P]),
+    "msstab_op_axpby": (_I32, [_P, _D, _P, _D, _P, _P]),
+    "msstab_op_multidot": (_I32, [_P, _I32, _P, _I64, _I32, _P, _I64, _I32, _P]),
+    "msstab_op_gamma_update": (_I32, [_P, _I32, _P, _P, _I64, _I32, _P]),
+    "msstab_op_eta_update": (_I32, [_P, _I32, _P, _P, _I64, _I32, _I32, _P]),
+    "msstab_op_lazy_update": (_I32, [_P, _I32, _P, _P, _P, _I64, _I32, _P, _P, _P]),
+    "msstab_op_tau_update": (_I32, [_P, _I32, _P, _P, _P, _I64, _P]),
+    "msstab_op_small_solve": (_I32, [_P, _I32, _P, _P, _P, _P]),
+    "msstab_op_tau_solve": (_I32, [_P, _I32, _P, _P]),
+}
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.lib_path()
+
+
+def load(path: Optional[str] = None):
+    """Load libmsstab.so (built in-tree by ``build.build()``); raises if absent."""
+    global _lib
+    if _lib is not None and path is None:
+        return _lib
+    path = path or lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"libmsstab.so not found at {path}: build it first "
+                           "(python -c 'import __graft_entry__ as g; g.build()')")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    load().msstab_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        setattr(o, k, v)
+    return o
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return t.data_ptr()
+
+
+def _check(rc, h=None):
+    if rc != OK:
+        msg = load().msstab_last_error(h)
+        raise MsstabError(rc, msg.decode() if msg else "")
+
+
+class Solver:
+    """A handle of libmsstab for one matrix A (CSR) and cut-space dimension s.
+
+    ``A`` is a ``problems.CSR`` (host arrays, copied to the device here) or a
+    tuple ``(n, row_ptr, col, val)`` of CUDA tensors.  ``p_raw`` is the raw
+    random basis of P, shape (s, n).  Keyword arguments set msstab_options
+    fields (precision, fetch_policy, fetch_threshold, fetch_cycle, orth_recycle,
+    max_mvs, inner_tol, spmv_format, sell_sigma, kernel_timing, max_outer).
+    """
+
+    def __init__(self, A, s: int, ell: int, p_raw, device: str = "cuda", stream=None, **options):
+        import torch
+        lib = load()
+        if isinstance(A, tuple):
+            n, row_ptr, col, val = A
+        else:
+            n = A.n
+            row_ptr = torch.as_tensor(A.row_ptr, dtype=torch.int32, device=device)
+            col = torch.as_tensor(A.col, dtype=torch.int32, device=device)
+            val = torch.as_tensor(A.val, dtype=torch.float64, device=device)
+        if not isinstance(p_raw, torch.Tensor):
+            p_raw = torch.as_tensor(np.ascontiguousarray(p_raw), dtype=torch.float64, device=device)
+        if tuple(p_raw.shape) != (s, n):
+            raise ValueError(f"p_raw must have shape (s, n) = {(s, n)}")
+        self.n, self.s, self.ell = int(n), int(s), int(ell)
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        opt = default_options(**options)
+        opt.stream = stream.cuda_stream
+        self._stream = stream
+        self.options = opt
+        h = ctypes.c_void_p()
+        rc = lib.msstab_create(self.n, int(val.numel()), _ptr(row_ptr), _ptr(col), _ptr(val), self.s, self.ell,
+                               _ptr(p_raw.contiguous()), ctypes.byref(opt), ctypes.byref(h))
+        if rc != OK:
+            raise MsstabError(rc, lib.msstab_last_error(None).decode())
+        self._h = h
+
+    # -- lifetime --------------------------------------------------------
+    def close(self):
+        if getattr(self, "_h", None):
+            load().msstab_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    @property
+    def handle(self):
+        return self._h
+
+    # -- solving ---------------------------------------------------------
+    def solve(self, b, x, tol: float = 1e-8, check: bool = True) -> Stats:
+        """Solve A x = b; x (CUDA float64) holds x0 and receives the solution."""
+        st = Stats()
+        rc = load().msstab_solve(self._h, _ptr(b), _ptr(x), float(tol), ctypes.byref(st))
+        if check and rc not in (OK,):
+            _check(rc, self._h)
+        return st
+
+    def solve_host(self, b: np.ndarray, x: np.ndarray, tol: float = 1e-8, check: bool = True) -> Stats:
+        """As solve, with host float64 arrays (copies inside the call)."""
+        if b.dtype != np.float64 or x.dtype != np.float64 or not x.flags.c_contiguous:
+            raise ValueError("b and x must be contiguous float64 arrays")
+        st = Stats()
+        rc = load().msstab_solve_host(self._h, b.ctypes.data, x.ctypes.data, float(tol), ctypes.byref(st))
+        if check and rc != OK:
+            _check(rc, self._h)
+        return st
+
+    def history(self):
+        cnt = ctypes.c_int32()
+        load().msstab_history(self._h, None, None, 0, ctypes.byref(cnt))
+        rel = np.zeros(cnt.value)
+        mv = np.zeros(cnt.value, dtype=np.int64)
+        load().msstab_history(self._h, rel.ctypes.data, mv.ctypes.data, cnt.value, ctypes.byref(cnt))
+        return rel, mv
+
+    def reset_recycle(self):
+        _check(load().msstab_reset_recycle(self._h), self._h)
+
+    def has_recycle(self) -> bool:
+        f = ctypes.c_int32()
+        _check(load().msstab_has_recycle(self._h, ctypes.byref(f)), self._h)
+        return bool(f.value)
+
+    def export_recycle(self, U, V):
+        _check(load().msstab_export_recycle(self._h, _ptr(U), _ptr(V)), self._h)
+
+    def import_recycle(self, U, V):
+        _check(load().msstab_import_recycle(self._h, _ptr(U), _ptr(V)), self._h)
+
+    def select_guess(self, b, xprev, delta, x) -> bool:
+        used = ctypes.c_int32()
+        _check(load().msstab_select_guess(self._h, _ptr(b), _ptr(xprev), _ptr(delta), _ptr(x),
+                                          ctypes.byref(used)), self._h)
+        return bool(used.value)
+
+    # -- kernel-level entry points -----------------------------------------
+    def op_spmv(self, x, y, prec: int = 0):
+        _check(load().msstab_op_spmv(self._h, prec, _ptr(x), _ptr(y)), self._h)
+
+    def op_residual(self, b, x, r, out):
+        _check(load().msstab_op_residual(self._h, _ptr(b), _ptr(x), _ptr(r), _ptr(out)), self._h)
+
+    def op_spmv_dot(self, x, y, dots, prec: int = 0):
+        _check(load().msstab_op_spmv_dot(self._h, prec, _ptr(x), _ptr(y), _ptr(dots)), self._h)
+
+    def op_axpby(self, alpha, x, beta, z, y):
+        """y = alpha x + beta z on the handle's stream (no synchronisation)."""
+        _check(load().msstab_op_axpby(self._h, float(alpha), _ptr(x), float(beta), _ptr(z), _ptr(y)), self._h)
+
+    def op_get_p(self, P, prec: int = 0):
+        _check(load().msstab_op_get_p(self._h, prec, _ptr(P)), self._h)
+
+    def op_multidot(self, X, Y, out, prec: int = 0):
+        nx, ldx = X.shape
+        ny, ldy = Y.shape
+        _check(load().msstab_op_multidot(self._h, prec, _ptr(X), ldx, nx, _ptr(Y), ldy, ny, _ptr(out)), self._h)
+
+    def op_gamma_update(self, R, V, k, gamma, prec: int = 0):
+        _check(load().msstab_op_gamma_update(self._h, prec, _ptr(R), _ptr(V), R.shape[1], k, _ptr(gamma)), self._h)
+
+    def op_eta_update(self, R, V, k, q, eta, prec: int = 0):
+        _check(load().msstab_op_eta_update(self._h, prec, _ptr(R), _ptr(V), R.shape[1], k, q, _ptr(eta)), self._h)
+
+    def op_lazy_update(self, R, V, x, k, gamma, eta, gram=None, prec: int = 0):
+        _check(load().msstab_op_lazy_update(self._h, prec, _ptr(R), _ptr(V), _ptr(x), R.shape[1], k, _ptr(gamma),
+                                            _ptr(eta), _ptr(gram)), self._h)
+
+    def op_tau_update(self, R, V, x, tau, prec: int = 0):
+        _check(load().msstab_op_tau_update(self._h, prec, _ptr(R), _ptr(V), _ptr(x), R.shape[1], _ptr(tau)),
+               self._h)
+
+    def op_small_solve(self, M, rhs, z, flag):
+        _check(load().msstab_op_small_solve(self._h, rhs.numel(), _ptr(M), _ptr(rhs), _ptr(z), _ptr(flag)),
+               self._h)
+
+    def op_tau_solve(self, gram, tau):
+        _check(load().msstab_op_tau_solve(self._h, tau.numel(), _ptr(gram), _ptr(tau)), self._h)
+
+
+def exported_symbols():
+    """Names of the C entry points this binding declares."""
+    return sorted(_SIGS)

@@ -1,0 +1,351 @@
+"""Kernel-level parity: every CUDA kernel of the solver against the FP64
+oracle's definition of the same step, on the same seeded inputs.
+
+Tolerance (FP64): 1e-12 relative to the sum of the absolute values of the
+terms (|A||x| per row for products with A, sum |a_i b_i| for dot products,
+the sum of |coefficient x operand| for block updates), so that cancellation
+cannot make a correct result fail.  FP32 kernels: 1e-6 of the same scale
+(a handful of FP32 roundings, unit roundoff 6e-8).
+"""
+
+import numpy as np
+import pytest
+
+from oracle import idrstab as O
+from paper_1604_06043_gb300 import problems as pb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+TOL64 = 1e-12
+TOL32 = 1e-6
+
+
+@pytest.fixture(scope="module")
+def msstab():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_06043_gb300 import build, msstab as M
+    build.build()
+    return M
+
+
+@pytest.fixture(scope="module")
+def case(msstab):
+    w = pb.WORKLOADS["convdiff3d_33"]     # N = 35937: many blocks and a ragged tail
+    A = w.matrix()
+    return w, A
+
+
+def _solver(msstab, A, s, ell, **opt):
+    return msstab.Solver(A, s, ell, pb.randn_cols(A.n, s, pb.SEED_P), device=DEV, **opt)
+
+
+def _t(x, dtype=torch.float64):
+    return torch.tensor(np.ascontiguousarray(x), dtype=dtype, device=DEV)
+
+
+def _abs_spmv(A, x):
+    return abs(A.to_scipy()) @ np.abs(x)
+
+
+def _random_csr(n, seed):
+    rng = np.random.default_rng(seed)
+    rows, cols, vals = [], [], []
+    for i in range(n):
+        k = int(rng.integers(0, 12))
+        c = np.unique(rng.integers(0, n, size=k))
+        rows += [i] * len(c)
+        cols += list(c)
+        vals += list(rng.standard_normal(len(c)))
+    import scipy.sparse as sp
+    M = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
+    M.sort_indices()
+    return pb.CSR(n, M.indptr.astype(np.int32), M.indices.astype(np.int32), M.data.astype(np.float64))
+
+
+# ---------------------------------------------------------------------------
+# products with A
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("fmt,sigma", [(0, 1), (1, 1), (0, 64)])
+def test_spmv_fp64(msstab, case, fmt, sigma):
+    w, A = case
+    S = _solver(msstab, A, 4, 2, spmv_format=fmt, sell_sigma=sigma)
+    x = pb.uniform(A.n, 11) - 0.5
+    y = torch.empty(A.n, dtype=torch.float64, device=DEV)
+    S.op_spmv(_t(x), y)
+    ref = A.to_scipy() @ x
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= TOL64 * _abs_spmv(A, x))
+
+
+@pytest.mark.parametrize("fmt,sigma", [(0, 1), (1, 1), (0, 32), (0, 128)])
+def test_spmv_irregular_rows(msstab, fmt, sigma):
+    A = _random_csr(3001, 5)            # empty rows, ragged lengths, unsorted lengths
+    S = _solver(msstab, A, 2, 1, spmv_format=fmt, sell_sigma=sigma)
+    x = pb.uniform(A.n, 12) - 0.5
+    y = torch.full((A.n,), np.nan, dtype=torch.float64, device=DEV)
+    S.op_spmv(_t(x), y)
+    ref = A.to_scipy() @ x
+    err = np.abs(y.cpu().numpy() - ref)
+    assert np.all(err <= TOL64 * _abs_spmv(A, x) + 1e-300)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_spmv_fp32_scaled_copy(msstab, case, fmt):
+    w, A = case
+    S = _solver(msstab, A, 4, 2, spmv_format=fmt)
+    x32 = (pb.uniform(A.n, 13) - 0.5).astype(np.float32)
+    y = torch.empty(A.n, dtype=torch.float32, device=DEV)
+    S.op_spmv(_t(x32, torch.float32), y, prec=1)
+    rho = np.max(np.abs(A.to_scipy().diagonal()))
+    As = A.to_scipy() / rho
+    ref = As @ x32.astype(np.float64)
+    err = np.abs(y.cpu().numpy().astype(np.float64) - ref)
+    assert np.all(err <= TOL32 * (abs(As) @ np.abs(x32.astype(np.float64))))
+
+
+def test_residual_and_norms(msstab, case):
+    w, A = case
+    S = _solver(msstab, A, 4, 2)
+    b = w.x0() / w.tau + w.f()
+    x = pb.uniform(A.n, 14)
+    r = torch.empty(A.n, dtype=torch.float64, device=DEV)
+    out = torch.zeros(2, dtype=torch.float64, device=DEV)
+    S.op_residual(_t(b), _t(x), r, out)
+    ref = b - A.to_scipy() @ x
+    scale = np.abs(b) + _abs_spmv(A, x)
+    assert np.all(np.abs(r.cpu().numpy() - ref) <= TOL64 * scale)
+    o = out.cpu().numpy()
+    assert abs(o[0] - ref @ ref) <= 1e-11 * (ref @ ref) + TOL64 * (scale @ scale)
+    assert abs(o[1] - b @ b) <= TOL64 * (b @ b)
+
+
+# ---------------------------------------------------------------------------
+# cut space and projections
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("s", [1, 3, 8, 16])
+def test_cut_space_matches_oracle(msstab, case, s):
+    w, A = case
+    S = _solver(msstab, A, s, 2)
+    P = torch.empty((s, A.n), dtype=torch.float64, device=DEV)
+    S.op_get_p(P)
+    ref = O.orthonormalize_mgs2(pb.randn_cols(A.n, s, pb.SEED_P))
+    assert np.max(np.abs(P.cpu().numpy() - ref)) <= 1e-12
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+@pytest.mark.parametrize("s", [4, 8, 16])
+def test_spmv_dot(msstab, case, fmt, s):
+    w, A = case
+    S = _solver(msstab, A, s, 2, spmv_format=fmt)
+    x = pb.uniform(A.n, 15) - 0.5
+    y = torch.empty(A.n, dtype=torch.float64, device=DEV)
+    d = torch.zeros(s + 1, dtype=torch.float64, device=DEV)
+    S.op_spmv_dot(_t(x), y, d)
+    P = O.orthonormalize_mgs2(pb.randn_cols(A.n, s, pb.SEED_P))
+    yr = A.to_scipy() @ x
+    yabs = _abs_spmv(A, x)
+    assert np.all(np.abs(y.cpu().numpy() - yr) <= TOL64 * yabs)
+    dd = d.cpu().numpy()
+    for c in range(s):
+        assert abs(dd[c] - O.proj(P, yr)[c]) <= TOL64 * (np.abs(P[c]) @ yabs) * 4
+    assert abs(dd[s] - yr @ yr) <= TOL64 * (yabs @ yabs) * 4
+
+
+def test_spmv_dot_fp32(msstab, case):
+    w, A = case
+    s = 8
+    S = _solver(msstab, A, s, 2)
+    x = (pb.uniform(A.n, 16) - 0.5).astype(np.float32)
+    y = torch.empty(A.n, dtype=torch.float32, device=DEV)
+    d = torch.zeros(s + 1, dtype=torch.float64, device=DEV)
+    S.op_spmv_dot(_t(x, torch.float32), y, d, prec=1)
+    P32 = torch.empty((s, A.n), dtype=torch.float32, device=DEV)
+    S.op_get_p(P32, prec=1)
+    yv = y.cpu().numpy().astype(np.float64)
+    P = P32.cpu().numpy().astype(np.float64)
+    dd = d.cpu().numpy()
+    # the dots are accumulated in FP64 from the stored FP32 values
+    ref = P @ yv
+    assert np.all(np.abs(dd[:s] - ref) <= 1e-12 * (np.abs(P) @ np.abs(yv)))
+
+
+@pytest.mark.parametrize("nx,ny", [(1, 1), (5, 5), (16, 16), (3, 9)])
+def test_multidot(msstab, case, nx, ny):
+    w, A = case
+    S = _solver(msstab, A, 4, 2)
+    rng = np.random.default_rng(nx * 100 + ny)
+    X = rng.standard_normal((nx, A.n))
+    Y = rng.standard_normal((ny, A.n))
+    out = torch.zeros(nx * ny, dtype=torch.float64, device=DEV)
+    S.op_multidot(_t(X), _t(Y), out)
+    ref = X @ Y.T
+    scale = np.abs(X) @ np.abs(Y).T
+    assert np.all(np.abs(out.cpu().numpy().reshape(nx, ny) - ref) <= TOL64 * scale)
+
+
+# ---------------------------------------------------------------------------
+# block updates of Algorithm 1
+# ---------------------------------------------------------------------------
+
+def _levels(n, s, ell, seed):
+    rng = np.random.default_rng(seed)
+    R = [rng.standard_normal(n) for _ in range(ell + 1)]
+    Vl = [rng.standard_normal((s, n)) for _ in range(ell + 2)]
+    return R, Vl
+
+
+def _pack(R, Vl):
+    return np.stack(R), np.concatenate(Vl, axis=0)
+
+
+def _unpack(Rg, Vg, s, ell):
+    R = [Rg[i] for i in range(ell + 1)]
+    Vl = [Vg[(i + 1) * s:(i + 2) * s] for i in range(-1, ell + 1)]
+    return R, Vl
+
+
+@pytest.mark.parametrize("s,ell,k", [(8, 4, 0), (8, 4, 3), (4, 2, 1), (16, 4, 2), (1, 1, 0)])
+def test_gamma_update(msstab, case, s, ell, k):
+    w, A = case
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 20 + k)
+    gamma = np.random.default_rng(7).standard_normal(s)
+    Rg, Vg = _pack(R, Vl)
+    Rt, Vt = _t(Rg), _t(Vg)
+    S.op_gamma_update(Rt, Vt, k, _t(gamma))
+    R2 = [r.copy() for r in R]
+    R2[k] = R[k] - gamma @ Vl[k + 1]
+    scale = np.abs(R[k]) + np.abs(gamma) @ np.abs(Vl[k + 1])
+    got = Rt.cpu().numpy()
+    assert np.all(np.abs(got[k] - R2[k]) <= TOL64 * scale)
+    for i in range(ell + 1):
+        if i != k:
+            np.testing.assert_array_equal(got[i], R[i])
+
+
+@pytest.mark.parametrize("s,ell,k,q", [(8, 4, 0, 0), (8, 4, 2, 5), (8, 4, 3, 7), (16, 4, 1, 9), (1, 1, 0, 0)])
+def test_eta_update_top_level(msstab, case, s, ell, k, q):
+    w, A = case
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 40 + q)
+    eta = np.random.default_rng(8).standard_normal(s)
+    Rg, Vg = _pack(R, Vl)
+    Rt, Vt = _t(Rg), _t(Vg)
+    S.op_eta_update(Rt, Vt, k, q, _t(eta))
+    Wk = O.w_block(Vl, k, q)
+    ref = R[k + 1] - eta @ Wk
+    scale = np.abs(R[k + 1]) + np.abs(eta) @ np.abs(Wk)
+    _, V2 = _unpack(Rt.cpu().numpy(), Vt.cpu().numpy(), s, ell)
+    assert np.all(np.abs(V2[k + 1][q] - ref) <= TOL64 * scale)
+
+
+@pytest.mark.parametrize("s,ell,k", [(8, 4, 0), (8, 4, 1), (8, 4, 3), (4, 2, 1), (3, 3, 2), (16, 4, 3), (1, 1, 0)])
+def test_level_step_equals_algorithm1(msstab, case, s, ell, k):
+    """One level step k as Algorithm 1 writes it (gamma update of all levels,
+    then for each q the eta update of all levels and the product with A)
+    against the CUDA path's split: top-level gamma and eta updates plus the
+    products, then the lazy update of the levels below k."""
+    w, A = case
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 60 + k)
+    x0 = np.random.default_rng(9).standard_normal(A.n)
+    rng = np.random.default_rng(10)
+    gamma = rng.standard_normal(s)
+    etas = rng.standard_normal((s, s)) * 0.5
+    # oracle, in the order of Algorithm 1
+    Ro = [r.copy() for r in R]
+    Vo = [v.copy() for v in Vl]
+    xo = x0.copy()
+    O.gamma_update(Ro, Vo, xo, gamma, k)
+    Ro[k + 1] = A.to_scipy() @ Ro[k]
+    for q in range(s):
+        O.eta_update(Ro, Vo, k, q, etas[q])
+        Vo[k + 2][q] = A.to_scipy() @ Vo[k + 1][q]
+    # CUDA path
+    Rg, Vg = _pack(R, Vl)
+    Rt, Vt, xt = _t(Rg), _t(Vg), _t(x0)
+    ld = A.n
+    S.op_gamma_update(Rt, Vt, k, _t(gamma))
+    S.op_spmv(Rt[k], Rt[k + 1])
+    for q in range(s):
+        S.op_eta_update(Rt, Vt, k, q, _t(etas[q]))
+        S.op_spmv(Vt[(k + 1) * s + q], Vt[(k + 2) * s + q])
+    gram = torch.zeros((ell + 1) ** 2, dtype=torch.float64, device=DEV)
+    S.op_lazy_update(Rt, Vt, xt, k, _t(gamma), _t(etas), gram)
+    Rc, Vc = _unpack(Rt.cpu().numpy(), Vt.cpu().numpy(), s, ell)
+    # compare every level; the scale bounds the growth through the chained updates
+    mag = max(np.max(np.abs(v)) for v in Vo + Ro)
+    for i in range(ell + 1):
+        assert np.max(np.abs(Rc[i] - Ro[i])) <= 1e-11 * mag
+    for i in range(ell + 2):
+        assert np.max(np.abs(Vc[i] - Vo[i])) <= 1e-11 * mag
+    assert np.max(np.abs(xt.cpu().numpy() - xo)) <= 1e-11 * max(mag, np.max(np.abs(xo)))
+    G = np.array([[Ro[a] @ Ro[c] for c in range(ell + 1)] for a in range(ell + 1)])
+    Gs = np.array([[np.abs(Ro[a]) @ np.abs(Ro[c]) for c in range(ell + 1)] for a in range(ell + 1)])
+    assert np.all(np.abs(gram.cpu().numpy().reshape(ell + 1, ell + 1) - G) <= 1e-10 * Gs)
+
+
+@pytest.mark.parametrize("s,ell", [(8, 4), (4, 2), (1, 1), (16, 4), (5, 3)])
+def test_tau_update(msstab, case, s, ell):
+    w, A = case
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 80 + s)
+    x0 = np.random.default_rng(11).standard_normal(A.n)
+    tau = np.random.default_rng(12).standard_normal(ell)
+    r, x, U, V = O.tau_update(R, Vl, x0, tau)
+    Rg, Vg = _pack(R, Vl)
+    Rt, Vt, xt = _t(Rg), _t(Vg), _t(x0)
+    S.op_tau_update(Rt, Vt, xt, _t(tau))
+    Rc, Vc = _unpack(Rt.cpu().numpy(), Vt.cpu().numpy(), s, ell)
+    sc = lambda a, terms: np.abs(a) + sum(abs(t_) * np.abs(v_) for t_, v_ in terms)
+    assert np.all(np.abs(Rc[0] - r) <= TOL64 * sc(R[0], [(tau[i - 1], R[i]) for i in range(1, ell + 1)]))
+    assert np.all(np.abs(xt.cpu().numpy() - x) <= TOL64 * sc(x0, [(tau[i - 1], R[i - 1]) for i in range(1, ell + 1)]))
+    for q in range(s):
+        assert np.all(np.abs(Vc[1][q] - V[q]) <= TOL64 * sc(Vl[1][q], [(tau[i - 1], Vl[i + 1][q]) for i in range(1, ell + 1)]))
+        assert np.all(np.abs(Vc[0][q] - U[q]) <= TOL64 * sc(Vl[0][q], [(tau[i - 1], Vl[i][q]) for i in range(1, ell + 1)]))
+
+
+@pytest.mark.parametrize("n", [1, 2, 4, 8, 16])
+def test_small_solve(msstab, case, n):
+    w, A = case
+    S = _solver(msstab, A, 2, 1)
+    rng = np.random.default_rng(n)
+    for trial in range(5):
+        M = rng.standard_normal((n, n))
+        z = rng.standard_normal(n)
+        out = torch.zeros(n, dtype=torch.float64, device=DEV)
+        flag = torch.full((1,), 7, dtype=torch.int32, device=DEV)
+        S.op_small_solve(_t(M), _t(z), out, flag)
+        assert int(flag.item()) == 0
+        ref = O.lu_solve_pp(M, z)
+        assert np.max(np.abs(out.cpu().numpy() - ref)) <= 1e-10 * np.max(np.abs(ref))
+
+
+def test_small_solve_breakdown(msstab, case):
+    w, A = case
+    S = _solver(msstab, A, 2, 1)
+    M = np.array([[1.0, 2.0, 3.0], [2.0, 4.0, 6.0], [0.0, 1.0, 1.0]])
+    out = torch.zeros(3, dtype=torch.float64, device=DEV)
+    flag = torch.zeros(1, dtype=torch.int32, device=DEV)
+    S.op_small_solve(_t(M), _t(np.ones(3)), out, flag)
+    with pytest.raises(O.Breakdown):
+        O.lu_solve_pp(M, np.ones(3))
+    assert int(flag.item()) == 1 and not out.cpu().numpy().any()
+
+
+@pytest.mark.parametrize("ell", [1, 2, 4, 8])
+def test_tau_solve(msstab, case, ell):
+    w, A = case
+    S = _solver(msstab, A, 2, 1)
+    rng = np.random.default_rng(ell)
+    R = [rng.standard_normal(200) * 10.0 ** rng.integers(-4, 4) for _ in range(ell + 1)]
+    G = np.array([[R[a] @ R[c] for c in range(ell + 1)] for a in range(ell + 1)])
+    tau = torch.zeros(ell, dtype=torch.float64, device=DEV)
+    S.op_tau_solve(_t(G), tau)
+    ref = O.tau_from_gram(G)
+    assert np.max(np.abs(tau.cpu().numpy() - ref)) <= 1e-10 * np.max(np.abs(ref))

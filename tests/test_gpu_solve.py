@@ -1,0 +1,355 @@
+"""Solve-level parity of the CUDA path against the FP64 oracle.
+
+The bar: every solve reaches a true relative residual <= tol with an MV count
+within 2 of the oracle's; the solutions agree far below the tolerance-implied
+error; the paper's finite-termination levels (Section 5.2), the BiCGStab
+special case and dense LU on tiny systems hold on the GPU as on the oracle.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import idrstab as O
+from paper_1604_06043_gb300 import problems as pb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_06043_gb300 import build, msstab
+    build.build()
+    return msstab
+
+
+def _t(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.float64, device=DEV)
+
+
+def _gpu_sequence(M, w, A, steps, **opt):
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, **opt)
+    f = _t(w.f())
+    x = _t(w.x0())
+    b = torch.empty_like(x)
+    out = []
+    for _ in range(steps):
+        S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
+        st = S.solve(b, x, w.tol)
+        out.append((st.mvs, st.cycles, st.relres_true, st.fetched, st.used_recycle, x.cpu().numpy().copy()))
+    S.close()
+    return out
+
+
+@pytest.mark.parametrize("policy", ["once", "never", "every"])
+def test_sequence_2d_matches_oracle(M, policy):
+    w = pb.WORKLOADS["convdiff2d_32"]
+    A = w.matrix()
+    pol = {"once": M.FETCH_ONCE, "never": M.FETCH_NEVER, "every": M.FETCH_EVERY}[policy]
+    g = _gpu_sequence(M, w, A, w.steps, fetch_policy=pol)
+    o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol, policy=policy)
+    As = A.to_scipy()
+    xprev = w.x0()
+    for i, (gs, os_) in enumerate(zip(g, o.solves)):
+        mvs, cycles, relres, fetched, used, x = gs
+        assert abs(mvs - os_.mvs) <= 2, (i, mvs, os_.mvs)
+        assert relres <= w.tol
+        b = xprev / w.tau + w.f()
+        assert np.linalg.norm(b - As @ x) <= w.tol * np.linalg.norm(b) * 1.0001
+        assert np.linalg.norm(x - os_.x) <= 1e-6 * np.linalg.norm(os_.x), i
+        xprev = x
+    if policy == "once":
+        assert g[0][3] == 1 and all(s[4] == 1 for s in g[1:])
+    if policy == "never":
+        assert not any(s[4] for s in g)
+
+
+@pytest.mark.parametrize("fmt", [0, 1])
+def test_sequence_3d_matches_oracle(M, fmt):
+    w = pb.WORKLOADS["convdiff3d_33"]
+    A = w.matrix()
+    g = _gpu_sequence(M, w, A, w.steps, spmv_format=fmt)
+    o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol)
+    As = A.to_scipy()
+    xprev = w.x0()
+    for i, (gs, os_) in enumerate(zip(g, o.solves)):
+        mvs, cycles, relres, fetched, used, x = gs
+        b = xprev / w.tau + w.f()
+        assert np.linalg.norm(b - As @ x) <= w.tol * np.linalg.norm(b) * 1.0001
+        assert abs(mvs - os_.mvs) <= 2, (i, mvs, os_.mvs)
+        assert np.linalg.norm(x - os_.x) <= 1e-6 * np.linalg.norm(os_.x)
+        xprev = x
+
+
+def test_history_matches_oracle_cycle_by_cycle(M):
+    w = pb.WORKLOADS["convdiff2d_32"]
+    A = w.matrix()
+    b = w.x0() / w.tau + w.f()
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV)
+    x = _t(w.x0())
+    S.solve(_t(b), x, 1e-10)
+    rel, mvs = S.history()
+    ref = O.idrstab(A, b, w.x0(), w.s, w.ell, O.orthonormalize_mgs2(w.p_raw()), tol=1e-10)
+    assert len(rel) == len(ref.history)
+    np.testing.assert_array_equal(mvs, ref.mv_history)
+    # rounding differences grow with the iteration; they stay far below the residual
+    np.testing.assert_allclose(rel, ref.history, rtol=1e-6)
+
+
+# ---------------------------------------------------------------------------
+# Section 5.2 on the GPU: finite termination on tridiag(2, 3, 1), N = 40
+# ---------------------------------------------------------------------------
+
+TRI = pb.tridiag(40, 2.0, 3.0, 1.0)
+B1, B2 = pb.termination_rhs(40)
+
+
+def _m_after_fetch(M, s, ell_src, fetch_cycle, ell):
+    P = pb.randn_cols(40, s, pb.SEED_P)
+    src = M.Solver(TRI, s, ell_src, P, device=DEV, fetch_cycle=fetch_cycle, orth_recycle=0, max_mvs=2000)
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st = src.solve(_t(B1), x, 1e-15, check=False)
+    assert st.fetched == 1
+    U = torch.zeros((s, 40), dtype=torch.float64, device=DEV)
+    V = torch.zeros((s, 40), dtype=torch.float64, device=DEV)
+    src.export_recycle(U, V)
+    dst = M.Solver(TRI, s, ell, P, device=DEV, orth_recycle=0, max_mvs=2000)
+    dst.import_recycle(U, V)
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st2 = dst.solve(_t(B2), x, 1e-13)
+    rel, _ = dst.history()
+    return rel, st2
+
+
+def _first_below(h, thr):
+    for c, v in enumerate(h):
+        if v < thr:
+            return c
+    return None
+
+
+def test_gpu_idrstab_terminates_at_g20(M):
+    S = M.Solver(TRI, 2, 1, pb.randn_cols(40, 2, pb.SEED_P), device=DEV, max_mvs=2000)
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    S.solve(_t(B1), x, 1e-13)
+    rel, mvs = S.history()
+    c = _first_below(rel, 1e-10)
+    assert c is not None and c <= 21 and rel[18] > 1e-6
+
+
+def test_gpu_fetch_after_60_mvs(M):
+    S = M.Solver(TRI, 2, 1, pb.randn_cols(40, 2, pb.SEED_P), device=DEV, fetch_cycle=19, orth_recycle=0,
+                 max_mvs=2000)
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(B1), x, 1e-15, check=False)
+    rel, mvs = S.history()
+    assert st.fetched == 1 and mvs[19] == 60
+
+
+def test_gpu_m2stab1_terminates_after_m29(M):
+    rel, st = _m_after_fetch(M, 2, 1, 19, 1)
+    c = _first_below(rel, 1e-10)
+    assert c is not None and 11 <= c <= 12 and rel[9] > 1e-8
+
+
+def test_gpu_m4stab1_terminates_after_m12(M):
+    rel, st = _m_after_fetch(M, 4, 1, 9, 1)
+    c = _first_below(rel, 1e-10)
+    assert c is not None and 4 <= c <= 5
+
+
+@pytest.mark.parametrize("ell_src,fetch_cycle", [(1, 8), (2, 4)])
+@pytest.mark.parametrize("ell", [1, 2])
+def test_gpu_data_ab_drop_after_m11(M, ell_src, fetch_cycle, ell):
+    rel, st = _m_after_fetch(M, 4, ell_src, fetch_cycle, ell)
+    c12 = 4 // ell
+    assert rel[c12] < 1e-8 and rel[c12 - 1] > 1e-6
+
+
+# ---------------------------------------------------------------------------
+# special cases
+# ---------------------------------------------------------------------------
+
+def test_gpu_s1_l1_is_bicgstab(M):
+    w = pb.WORKLOADS["convdiff2d_32"]
+    A = w.matrix()
+    b = w.x0() / w.tau + w.f()
+    p_raw = pb.randn_cols(w.n, 1, pb.SEED_P)
+    S = M.Solver(A, 1, 1, p_raw, device=DEV, max_mvs=5000)
+    x = torch.zeros(w.n, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(b), x, 1e-10)
+    rel, _ = S.history()
+    p = O.orthonormalize_mgs2(p_raw)[0]
+    _, hist, mvs = O.bicgstab(A, b, np.zeros(w.n), p, tol=1e-10)
+    np.testing.assert_allclose(rel[:16], hist[:16], rtol=1e-8)
+    assert abs(st.mvs - (mvs + 2)) <= 2
+
+
+@pytest.mark.parametrize("s,ell", [(1, 1), (2, 2), (4, 2), (4, 4)])
+def test_gpu_tiny_matches_dense_lu(M, s, ell):
+    A = pb.convdiff((8, 8), (10.0, 10.0), tau=0.01)
+    b = pb.uniform(64, 1) / 0.01 + pb.uniform(64, 2)
+    S = M.Solver(A, s, ell, pb.randn_cols(64, s, 3), device=DEV, max_mvs=5000)
+    x = torch.zeros(64, dtype=torch.float64, device=DEV)
+    S.solve(_t(b), x, 1e-12)
+    ref = np.linalg.solve(A.to_dense(), b)
+    assert np.linalg.norm(x.cpu().numpy() - ref) <= 1e-8 * np.linalg.norm(ref)
+
+
+def test_gpu_first_msstab_solve_is_idrstab_bitwise(M):
+    w = pb.WORKLOADS["convdiff3d_24"]
+    A = w.matrix()
+    b = _t(w.x0() / w.tau + w.f())
+    xs = []
+    for pol in (M.FETCH_ONCE, M.FETCH_NEVER):
+        S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, fetch_policy=pol)
+        x = _t(w.x0())
+        st = S.solve(b, x, w.tol)
+        xs.append((x.cpu().numpy(), st.mvs))
+    assert xs[0][1] == xs[1][1]
+    np.testing.assert_array_equal(xs[0][0], xs[1][0])
+
+
+def test_gpu_deterministic(M):
+    w = pb.WORKLOADS["convdiff3d_24"]
+    A = w.matrix()
+    b = _t(w.x0() / w.tau + w.f())
+    outs = []
+    for _ in range(2):
+        S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV)
+        x = _t(w.x0())
+        S.solve(b, x, w.tol)
+        outs.append(x.cpu().numpy())
+    np.testing.assert_array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------------------
+# host buffers, statistics, edge cases and errors
+# ---------------------------------------------------------------------------
+
+def test_solve_host_matches_device(M):
+    w = pb.WORKLOADS["convdiff3d_24"]
+    A = w.matrix()
+    b = w.x0() / w.tau + w.f()
+    S1 = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV)
+    xd = _t(w.x0())
+    st1 = S1.solve(_t(b), xd, w.tol)
+    S2 = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV)
+    xh = w.x0().copy()
+    st2 = S2.solve_host(b, xh, w.tol)
+    np.testing.assert_array_equal(xh, xd.cpu().numpy())
+    assert st1.mvs == st2.mvs
+
+
+def test_kernel_timing_and_launch_counts(M):
+    w = pb.WORKLOADS["convdiff3d_24"]
+    A = w.matrix()
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, kernel_timing=1)
+    x = _t(w.x0())
+    st = S.solve(_t(w.x0() / w.tau + w.f()), x, w.tol)
+    d = st.as_dict()
+    assert d["launches"] == sum(d["n_launch"].values())
+    per_cycle = w.ell * (2 + 2 * w.s + 1) + 2
+    assert d["n_launch"]["spmv_dot"] == st.cycles * w.ell * (w.s + 1)
+    assert d["launches"] >= st.cycles * per_cycle
+    assert all(v >= 0 for v in d["t_ms"].values()) and d["t_ms"]["spmv_dot"] > 0
+
+
+def test_zero_rhs(M):
+    A = pb.convdiff((8, 8), (10.0, 10.0), tau=0.01)
+    S = M.Solver(A, 2, 2, pb.randn_cols(64, 2, 3), device=DEV)
+    x = torch.ones(64, dtype=torch.float64, device=DEV)
+    st = S.solve(torch.zeros(64, dtype=torch.float64, device=DEV), x, 1e-8)
+    assert st.status == 0 and st.mvs == 0 and not x.cpu().numpy().any()
+
+
+def test_exact_start(M):
+    A = pb.convdiff((8, 8), (10.0, 10.0), tau=0.01)
+    S = M.Solver(A, 2, 2, pb.randn_cols(64, 2, 3), device=DEV)
+    xs = np.ones(64)
+    x = _t(xs)
+    st = S.solve(_t(A.to_scipy() @ xs), x, 1e-8)
+    assert st.status == 0 and st.mvs == 1 and st.cycles == 0
+
+
+def test_maxit(M):
+    A = pb.convdiff((8, 8), (10.0, 10.0), tau=0.01)
+    S = M.Solver(A, 2, 2, pb.randn_cols(64, 2, 3), device=DEV, max_mvs=10)
+    x = torch.zeros(64, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(pb.uniform(64, 1)), x, 1e-14, check=False)
+    ref = O.idrstab(A, pb.uniform(64, 1), np.zeros(64), 2, 2, O.orthonormalize_mgs2(pb.randn_cols(64, 2, 3)),
+                    tol=1e-14, max_mvs=10)
+    assert st.status == M.ERR_MAXIT and ref.status == O.MAXIT and st.mvs == ref.mvs
+
+
+def test_nan_rhs(M):
+    A = pb.convdiff((8, 8), (10.0, 10.0), tau=0.01)
+    S = M.Solver(A, 2, 2, pb.randn_cols(64, 2, 3), device=DEV)
+    b = pb.uniform(64, 1)
+    b[5] = np.nan
+    x = torch.zeros(64, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(b), x, 1e-8, check=False)
+    assert st.status == M.ERR_NAN
+
+
+def test_breakdown_matches_oracle(M):
+    # A = I, b in span(e0, e1), P = (e10, e11): P^T V is singular after the
+    # Arnoldi start runs out of Krylov directions and continues with P
+    n = 64
+    A = pb.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), np.ones(n))
+    P = np.zeros((2, n))
+    P[0, 10] = 1.0
+    P[1, 11] = 1.0
+    b = np.zeros(n)
+    b[0] = b[1] = 1.0
+    ref = O.idrstab(A, b, np.zeros(n), 2, 1, O.orthonormalize_mgs2(P), tol=1e-8)
+    S = M.Solver(A, 2, 1, P, device=DEV)
+    x = torch.zeros(n, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(b), x, 1e-8, check=False)
+    assert ref.status == O.BREAKDOWN
+    assert st.status == M.ERR_BREAKDOWN
+
+
+def test_invalid_arguments(M):
+    A = pb.convdiff((8, 8), (10.0, 10.0), tau=0.01)
+    with pytest.raises(M.MsstabError) as e:
+        M.Solver(A, 17, 2, pb.randn_cols(64, 17, 3), device=DEV)
+    assert e.value.status == M.ERR_INVALID_ARG
+    bad = pb.CSR(A.n, A.row_ptr.copy(), A.col.copy(), A.val.copy())
+    bad.col[5] = 64
+    with pytest.raises(M.MsstabError) as e:
+        M.Solver(bad, 2, 2, pb.randn_cols(64, 2, 3), device=DEV)
+    assert e.value.status == M.ERR_INVALID_ARG and "column" in str(e.value)
+    dup = np.stack([pb.randn_cols(64, 1, 3)[0]] * 2)
+    with pytest.raises(M.MsstabError) as e:
+        M.Solver(A, 2, 2, dup, device=DEV)
+    assert e.value.status == M.ERR_INVALID_ARG
+    S = M.Solver(A, 2, 2, pb.randn_cols(64, 2, 3), device=DEV)
+    x = torch.zeros(64, dtype=torch.float64, device=DEV)
+    with pytest.raises(M.MsstabError):
+        S.solve(_t(pb.uniform(64, 1)), x, -1.0)
+
+
+# ---------------------------------------------------------------------------
+# FP32 inner solves inside FP64 defect correction
+# ---------------------------------------------------------------------------
+
+def test_fp32_inner_reaches_fp64_accuracy(M):
+    w = pb.WORKLOADS["convdiff3d_33"]
+    A = w.matrix()
+    As = A.to_scipy()
+    g = _gpu_sequence(M, w, A, w.steps, precision=M.PREC_FP32_INNER)
+    o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol)
+    xprev = w.x0()
+    for i, (gs, os_) in enumerate(zip(g, o.solves)):
+        mvs, cycles, relres, fetched, used, x = gs
+        b = xprev / w.tau + w.f()
+        assert np.linalg.norm(b - As @ x) <= w.tol * np.linalg.norm(b) * 1.0001
+        # both residuals are below tol; the solutions differ by at most cond * tol
+        assert np.linalg.norm(x - os_.x) <= 1e-6 * np.linalg.norm(os_.x)
+        xprev = x
+    assert g[0][3] == 1 and all(s[4] == 1 for s in g[1:])
