@@ -1,0 +1,478 @@
+#!/usr/bin/env python
+"""Benchmark of the M(s)stab(l) solver on GB300: ms and products with A per
+system for the 128^3 implicit-Euler convection-diffusion sequence at 1e-8
+relative residual, with the roofline of the dominant kernel.
+
+A step is one system of the sequence: b = x^(i)/tau + f formed on the device,
+then msstab_solve (the whole hot path: products with A fused with the P^T
+projections, the gamma/eta/lazy level updates, the degree-l step, the device
+small solves, the fetch of the recycled basis).  The first --warmup systems
+(system 1 runs IDRstab with its Arnoldi start and fetches U, V) are untimed;
+the next --steps systems are timed.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+With --gpus N > 1 (launched by torchrun) every rank solves its own replica of
+the sequence (the solver does not shard); value = max-over-ranks time / all
+systems solved.  One JSON line is printed by rank 0.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "ms/system & #MVs for 128³ implicit-Euler seq at 1e-8 rel res; SpMV HBM GB/s"
+UNIT = "ms/system"
+WORKLOAD = "convdiff3d_128"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_128.json")
+FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn"]
+FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=20)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["native", "reference"], default="native")
+    p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--no-variants", action="store_true", help="skip the IDRstab and FP32-inner runs")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-level-steps", type=int, default=4, help=argparse.SUPPRESS)
+    p.add_argument("--cpu-k0", type=int, default=0, help=argparse.SUPPRESS)
+    return p.parse_args(argv)
+
+
+# ---------------------------------------------------------------------------
+# distributed helpers (replicas only)
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def aggregate(elapsed_ms: float, steps: int, world: int, dist=None):
+    """Max of the per-rank elapsed times and the whole-job ms per system."""
+    t = elapsed_ms
+    if dist is not None and world > 1:
+        import torch
+        v = torch.tensor([elapsed_ms], dtype=torch.float64)
+        if dist.get_backend() == "nccl":
+            v = v.cuda()
+        dist.all_reduce(v, op=dist.ReduceOp.MAX)
+        t = float(v.item())
+    return t, t / (steps * world)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    QUERY = ("index,uuid,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.QUERY}", "--format=csv,noheader",
+                                          "-lms", "100"], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, smax, power, reasons = [], [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [c.strip() for c in line.split(",")]
+            if len(f) < 10:
+                continue
+            if self.uuid and f[1] != self.uuid:
+                continue
+            try:
+                sm.append(float(f[2].split()[0]))
+                smax.append(float(f[3].split()[0]))
+                power.append(float(f[4].split()[0]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[6:10]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "power_w_max": max(power) if power else None, "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------------------
+# algorithmic bytes and flops per kernel family (FP64 vectors)
+# ---------------------------------------------------------------------------
+
+def sell_entries(A):
+    import numpy as np
+    lens = np.diff(A.row_ptr.astype(np.int64))
+    pad = (-len(lens)) % 32
+    lens = np.concatenate([lens, np.zeros(pad, dtype=np.int64)]).reshape(-1, 32)
+    return int(lens.max(axis=1).sum() * 32), lens.shape[0]
+
+
+def family_model(A, s, ell, cycles, solves, vb=8):
+    """Algorithmic bytes and FP64 flops of the launches of one timed region.
+
+    Every operand is counted once per launch: the matrix arrays, x read once,
+    y written once, each vector column read or written once."""
+    n = A.n
+    nnz_sell, nsl = sell_entries(A)
+    v = vb * n
+    spmv = nnz_sell * (4 + vb) + 8 * nsl + 2 * v
+    m = {}
+    m["spmv_dot"] = dict(launches=cycles * ell * (s + 1), bytes=spmv + s * v, flops=2 * (A.nnz + s * n))
+    m["eta"] = dict(launches=cycles * ell * s, bytes=(s + 2) * v, flops=2 * s * n)
+    m["gamma"] = dict(launches=cycles * ell, bytes=(s + 2) * v, flops=2 * s * n)
+    lazy_b = sum((s + 1) + (k + 1) * (2 * s + 2) for k in range(ell)) * v
+    lazy_f = sum((k + 1) * (s * s + s) for k in range(ell)) * 2 * n
+    m["lazy"] = dict(launches=cycles * ell, bytes=lazy_b / ell, flops=lazy_f / ell)
+    tau_cycle_b = (ell + 1) * v + ((ell + 1) + 1 + s * (ell + 2) + s + 3 + 2 * s) * v
+    tau_cycle_f = 2 * (ell + 1) ** 2 * n + 2 * ((2 * s + 2) * ell + s * (s + 1) + 1) * n
+    tau_b = cycles * tau_cycle_b + solves * (2 * s + 1) * v
+    tau_f = cycles * tau_cycle_f + solves * 2 * s * (s + 1) * n
+    m["tau"] = dict(launches=2 * cycles + solves, bytes=tau_b / max(1, 2 * cycles + solves),
+                    flops=tau_f / max(1, 2 * cycles + solves))
+    return m, spmv
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle, as it stands, on the host cores
+# ---------------------------------------------------------------------------
+
+def golden_cycles(first, count):
+    """Mean cycles and MVs per system of systems first..first+count-1 (1-based)
+    in the oracle's committed record, or None."""
+    try:
+        rec = json.load(open(GOLDEN))
+    except Exception:
+        return None
+    sy = rec["systems"][first - 1:first - 1 + count]
+    if not sy:
+        sy = rec["systems"][1:] or rec["systems"]
+    if not sy:
+        return None
+    return (statistics.mean(x["cycles"] for x in sy), statistics.mean(x["mvs"] for x in sy), len(sy))
+
+
+def cpu_worker(args):
+    """Time the oracle on the host: level steps of Algorithm 1 (s = 8, l = 4) on
+    system 1 of the 128^3 sequence, after its Arnoldi start.  Prints JSON."""
+    import numpy as np
+    from oracle import idrstab as O
+    from paper_1604_06043_gb300 import problems as pb
+    w = pb.WORKLOADS[args.workload]
+    A = w.matrix()
+    mv = O.MatVec(A)
+    P = O.orthonormalize_mgs2(w.p_raw())
+    x = w.x0().copy()
+    b = x / w.tau + w.f()
+    t0 = time.perf_counter()
+    r = b - mv(x)
+    t_mv = time.perf_counter() - t0
+    U, V = O.arnoldi_start(mv, r, w.s, P)
+    R = [r.copy()] + [None] * w.ell
+    Vl = [U.copy(), V.copy()] + [np.zeros((w.s, w.n)) for _ in range(w.ell)]
+    x0 = x.copy()
+    times = []
+    for step in range(args.cpu_level_steps):
+        k = (args.cpu_k0 + step) % w.ell
+        if k == 0 and step > 0:
+            R = [R[0]] + [None] * w.ell
+        t0 = time.perf_counter()
+        gamma = O.gamma_step(P, R, Vl, k)
+        O.gamma_update(R, Vl, x0, gamma, k)
+        R[k + 1] = mv(R[k])
+        for q in range(w.s):
+            eta = O.eta_step(P, R, Vl, k, q)
+            O.eta_update(R, Vl, k, q, eta)
+            Vl[k + 2][q] = mv(Vl[k + 1][q])
+        if k == w.ell - 1:
+            tau = O.tau_step(R)
+            r, x0, U_, V_ = O.tau_update(R, Vl, x0, tau)
+            Vl[0], Vl[1] = U_, V_
+            R[0] = r
+        times.append(time.perf_counter() - t0)
+    print(json.dumps({"level_step_s": times, "mv_s": t_mv, "threads": 1}))
+
+
+def run_cpu_sample(args, level_steps, k0=0):
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-worker", "--workload", args.workload,
+           "--cpu-level-steps", str(level_steps), "--cpu-k0", str(k0)]
+    out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1800)
+    if out.returncode != 0:
+        raise RuntimeError(out.stderr[-2000:])
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def reference_arm(args):
+    """--impl reference: the oracle on the host cores, same metric and unit.
+    Each step is one level step of Algorithm 1 (k cycling through 0..l-1);
+    ms/system = mean level-step time x l x cycles per system + 2 MVs (r0 and
+    the true residual), the cycles per system taken from the oracle's own
+    committed record of the same systems."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_1604_06043_gb300 import problems as pb
+    w = pb.WORKLOADS[args.workload]
+    res = run_cpu_sample(args, args.warmup + args.steps)
+    timed = res["level_step_s"][args.warmup:]
+    g = golden_cycles(args.warmup + 1, args.steps)
+    cyc = g[0] if g else float("nan")
+    ms = statistics.mean(timed) * 1e3 * w.ell * cyc + 2 * res["mv_s"] * 1e3
+    sample = (f"{len(timed)} level steps of Algorithm 1 (s={w.s}, l={w.ell}) of the FP64 oracle on system 1 of "
+              f"the 128^3 sequence, scaled by {cyc:.2f} cycles/system (oracle record, systems "
+              f"{args.warmup + 1}..{args.warmup + args.steps}) + 2 MVs")
+    line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(timed) * 1e3,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded)", "config": {"workload": args.workload},
+            "cpu_baseline": {"value": ms, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# the GPU arm
+# ---------------------------------------------------------------------------
+
+def run_sequence(M, torch, S, f, x, b, tau, tol, count, collect=None):
+    out = []
+    for _ in range(count):
+        S.op_axpby(1.0 / tau, x, 1.0, f, b)
+        st = S.solve(b, x, tol)
+        out.append(st.as_dict())
+        if collect is not None:
+            collect.append(x.clone())
+    return out
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.cpu_worker:
+        cpu_worker(args)
+        return
+    if args.impl == "reference":
+        reference_arm(args)
+        return
+
+    import numpy as np
+    import torch
+    rank, world, local = dist_env()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = f"cuda:{local}" if world > 1 else "cuda:0"
+    torch.cuda.set_device(dev)
+
+    from paper_1604_06043_gb300 import build, msstab as M, problems as pb
+    if rank == 0:
+        build.build()
+    if dist is not None:
+        dist.barrier()
+    w = pb.WORKLOADS[args.workload]
+    A = w.matrix()
+    f_np, x0_np = w.f(), w.x0()
+    K, W = args.steps, args.warmup
+
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, kernel_timing=1)
+    stream = torch.cuda.current_stream()
+    f = torch.tensor(f_np, device=dev)
+    x = torch.tensor(x0_np, device=dev)
+    b = torch.empty_like(x)
+    warm = run_sequence(M, torch, S, f, x, b, w.tau, w.tol, W)
+    xW = x.clone()
+    uuid = None
+    try:
+        uuid = "GPU-" + str(torch.cuda.get_device_properties(dev).uuid)
+    except Exception:
+        pass
+    clocks = Clocks(uuid)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    timed = run_sequence(M, torch, S, f, x, b, w.tau, w.tol, K)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if dist is not None:
+        dist.barrier()
+    elapsed = e0.elapsed_time(e1)
+    T, value = aggregate(elapsed, K, world, dist)
+
+    mvs = [t["mvs"] for t in timed]
+    cycles = sum(t["cycles"] for t in timed)
+    fam_ms = {f_: sum(t["t_ms"][f_] for t in timed) for f_ in FAMILIES}
+    fam_n = {f_: sum(t["n_launch"][f_] for t in timed) for f_ in FAMILIES}
+    launches = sum(t["launches"] for t in timed) + K          # + the right-hand-side launches
+    model, spmv_b = family_model(A, w.s, w.ell, cycles, K)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+    kernels = {}
+    for fam, mod in model.items():
+        if fam_n.get(fam, 0) == 0:
+            continue
+        avg_s = fam_ms[fam] / fam_n[fam] / 1e3
+        gbs = mod["bytes"] / avg_s / 1e9
+        tf = mod["flops"] / avg_s / 1e12
+        kernels[fam] = {"launches": fam_n[fam], "total_ms": round(fam_ms[fam], 3),
+                        "avg_us": round(avg_s * 1e6, 2), "alg_bytes_per_launch": int(mod["bytes"]),
+                        "GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3),
+                        "fp64_tflops": round(tf, 3), "fp64_frac_nominal": round(tf / FP64_NOMINAL_TFLOPS, 3)}
+    dom = max(kernels, key=lambda k_: kernels[k_]["total_ms"])
+    kd = kernels[dom]
+    share = round(fam_ms[dom] / max(1e-9, sum(fam_ms.values())), 3)
+    if kd["fp64_frac_nominal"] > kd["hbm_frac"]:
+        # FP64 FMA throughput, not HBM, binds this kernel on GB300
+        roofline = {"kernel": dom, "bound": "alu", "achieved": kd["fp64_tflops"], "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s (FP64)", "frac": kd["fp64_frac_nominal"], "traffic": None,
+                    "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
+                    "hbm": {"achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s", "frac": kd["hbm_frac"]},
+                    "share_of_step": share}
+    else:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": kd["hbm_frac"], "traffic": None,
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "fp64_frac_of_nominal": kd["fp64_frac_nominal"], "share_of_step": share}
+
+    line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+            "ms_per_step": round(T / K, 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic (seeded generators; the paper's ocean data is not available)",
+            "config": {"workload": f"{w.name}: 3D convection-diffusion, 7-point FD on a 128^3 grid (N={A.n}, "
+                                   f"nnz={A.nnz}), beta=(20,10,5), implicit Euler tau={w.tau}, systems "
+                                   f"{W + 1}..{W + K} of the sequence",
+                       "method": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
+                       "tol": w.tol, "l2": "inputs larger than L2 (matrix 0.18 GB + ~90 vectors of 16.8 MB), no flush",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "mvs_per_system": round(statistics.mean(mvs), 2), "cycles_per_system": round(cycles / K, 3),
+            "relres_true_max": max(t["relres_true"] for t in timed),
+            "system1": {"ms": round(warm[0]["ms"], 3), "mvs": warm[0]["mvs"], "cycles": warm[0]["cycles"]} if warm else None,
+            "spmv_GBps": kernels.get("spmv_dot", {}).get("GBps"),
+            "gpu_launches": int(launches), "roofline": roofline, "kernels": kernels, "clocks": clk}
+
+    # end to end through the public API with host buffers
+    if not args.no_e2e:
+        E = min(K, 10)
+        xh = x.cpu().numpy().copy()
+        wall = []
+        e_mvs = []
+        for _ in range(E):
+            bh = xh / w.tau + f_np
+            t0 = time.perf_counter()
+            st = S.solve_host(bh, xh, w.tol)
+            wall.append((time.perf_counter() - t0) * 1e3)
+            e_mvs.append(st.mvs)
+        line["e2e"] = {"value": round(statistics.mean(wall), 4), "unit": UNIT, "h2d_bytes_per_step": 16 * A.n,
+                       "d2h_bytes_per_step": 8 * A.n, "systems": E,
+                       "note": "msstab_solve_host: b and x0 from host memory, x back, per call"}
+    S.close()
+
+    # the same systems on the same GPU: IDRstab (Arnoldi start per system) and FP32-inner M(s)stab
+    if not args.no_variants:
+        ref_x = []
+        xs = torch.tensor(x0_np, device=dev)
+        variants = {}
+        for name, opts in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER)),
+                           ("msstab_fp32_inner", dict(precision=M.PREC_FP32_INNER))):
+            V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, **opts)
+            xv = torch.tensor(x0_np, device=dev)
+            run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W)
+            torch.cuda.synchronize()
+            v0 = torch.cuda.Event(enable_timing=True)
+            v1 = torch.cuda.Event(enable_timing=True)
+            xs_list = []
+            v0.record(stream)
+            tv = run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, K,
+                              collect=xs_list if name == "msstab_fp32_inner" else None)
+            v1.record(stream)
+            torch.cuda.synchronize()
+            variants[name] = {"ms_per_system": round(v0.elapsed_time(v1) / K, 4),
+                              "mvs_per_system": round(statistics.mean(t["mvs"] for t in tv), 2),
+                              "relres_true_max": max(t["relres_true"] for t in tv)}
+            if name == "msstab_fp32_inner":
+                variants[name]["mvs_fp32_per_system"] = round(statistics.mean(t["mvs_fp32"] for t in tv), 2)
+                variants[name]["outer_per_system"] = round(statistics.mean(t["outer"] for t in tv), 2)
+                variants[name]["_xs"] = xs_list
+            V.close()
+        # error of the FP32-inner solutions against the FP64 solutions of the same systems
+        P64 = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev)
+        x64 = torch.tensor(x0_np, device=dev)
+        run_sequence(M, torch, P64, f, x64, b, w.tau, w.tol, W)
+        errs = []
+        for xv32 in variants["msstab_fp32_inner"].pop("_xs"):
+            P64.op_axpby(1.0 / w.tau, x64, 1.0, f, b)
+            P64.solve(b, x64, w.tol)
+            errs.append(float(torch.linalg.norm(xv32 - x64) / torch.linalg.norm(x64)))
+        P64.close()
+        variants["msstab_fp32_inner"]["rel_err_vs_fp64_max"] = max(errs)
+        line["variants"] = variants
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        try:
+            res = run_cpu_sample(args, 4)
+            cyc = cycles / K
+            ms = statistics.mean(res["level_step_s"]) * 1e3 * w.ell * cyc + 2 * res["mv_s"] * 1e3
+            line["cpu_baseline"] = {"value": round(ms, 1), "unit": UNIT, "cores": res["threads"], "kind": "oracle",
+                                    "sample": f"one cycle (4 level steps, 36 MVs) of Algorithm 1 of the FP64 oracle on "
+                                              f"system 1 of the 128^3 sequence, scaled by the timed run's "
+                                              f"{cyc:.2f} cycles/system, + 2 MVs"}
+        except Exception as e:  # the baseline is reported, not required
+            line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                    "sample": f"failed: {str(e)[-200:]}"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

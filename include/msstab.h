@@ -70,8 +70,10 @@ typedef struct msstab_options {
                               for every system */
   double fetch_threshold;  /* fetch at the first cycle end with relres <= this; <= 0: sqrt(tol) */
   int32_t fetch_cycle;     /* > 0: fetch at the end of this cycle instead of by threshold */
-  int32_t orth_recycle;    /* 1 (default): orthonormalise the fetched V (and U alongside) by
-                              Cholesky QR twice; 0: keep them as fetched */
+  int32_t orth_recycle;    /* 1 (default): condition the fetched basis -- V := A U (s products
+                              with A, counted in the fetching solve), then Cholesky QR twice of
+                              V with U carried along; 0: keep U, V exactly as fetched (the
+                              paper's plain hand-over) */
   int64_t max_mvs;         /* products with A per solve; <= 0: min(100000, 20 sqrt(n) + 1 + s + 2l(s+1)) */
   double inner_tol;        /* FP32 inner: relative tolerance of each inner solve (tested on its
                               recursive residual); <= 0: max(1e-4, 0.5 tol ||b|| / ||r_outer||) */
@@ -231,8 +233,9 @@ msstab_status msstab_op_tau_update(msstab_t h, int32_t prec, void* d_R, void* d_
                                    const double* d_tau);
 
 /* Solve the n x n system d_M z = d_rhs (d_M row-major, n <= 16) on the device by
- * Gaussian elimination with partial pivoting; *d_flag = 1 if a pivot fell
- * below 1e-14 max|M| (z is then zero).  The small solves of Algorithm 1. */
+ * Gaussian elimination with partial pivoting; *d_flag = 1 if the pivot of a
+ * column fell below 1e-14 times the largest magnitude in that column of M
+ * (z is then zero).  The small solves of Algorithm 1. */
 msstab_status msstab_op_small_solve(msstab_t h, int32_t n, const double* d_M, const double* d_rhs,
                                     double* d_z, int32_t* d_flag);
 

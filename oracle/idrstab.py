@@ -24,7 +24,8 @@ Readings of points the paper leaves open (the same on the CUDA side):
   * the garbled recapture of the solution after the residual minimisation is
     read as x = x^(0) + sum_{i=1..l} tau_i r^(i-1);
   * s x s solves: Gaussian elimination with partial pivoting; a pivot below
-    1e-14 * max|entry| is a breakdown;
+    1e-14 * (largest magnitude in its column of the projected matrix) is a
+    breakdown (a per-column test: the columns differ in scale by orders);
   * tau = Z^+ r^(0) through the normal equations of the Gram matrix of
     [r^(0..l)], diagonally scaled, by Cholesky with LU as the fallback;
   * fetching point: the first cycle end whose recursive relative residual is
@@ -59,17 +60,21 @@ class Breakdown(Exception):
 def lu_solve_pp(M: np.ndarray, rhs: np.ndarray) -> np.ndarray:
     """Solve M z = rhs by Gaussian elimination with row (partial) pivoting.
 
-    Raises Breakdown if a pivot's magnitude is below 1e-14 times the largest
-    entry of M (or if M is zero or not finite)."""
+    Raises Breakdown if the pivot of column k falls below 1e-14 times the
+    largest magnitude in column k of M (a zero column included).  The test is
+    per column because the columns of a projected matrix P^T W can differ in
+    scale by many orders (P^T of an orthonormal column is O(sqrt(s/N)), P^T of
+    a product with A is O(||A||)); scaling a column changes neither
+    solvability nor the pivot rows that partial pivoting picks."""
     a = np.array(M, dtype=np.float64, copy=True)
     z = np.array(rhs, dtype=np.float64, copy=True)
     n = z.shape[0]
-    scale = float(np.max(np.abs(a))) if n else 0.0
-    if not (scale > 0.0 and math.isfinite(scale)):
-        raise Breakdown("projected matrix is zero or not finite")
+    colmax = np.max(np.abs(a), axis=0) if n else np.zeros(0)
+    if not (np.all(colmax > 0.0) and np.all(np.isfinite(colmax))):
+        raise Breakdown("projected matrix has a zero or non-finite column")
     for k in range(n):
         p = k + int(np.argmax(np.abs(a[k:, k])))
-        if abs(a[p, k]) < PIVOT_REL_TOL * scale:
+        if abs(a[p, k]) < PIVOT_REL_TOL * colmax[k]:
             raise Breakdown(f"pivot {a[p, k]:.3e} at step {k}")
         if p != k:
             a[[k, p], :] = a[[p, k], :]
@@ -307,7 +312,7 @@ class SolveResult:
 
 
 def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
-            fetch_threshold=None, fetch_cycle=None, inspect: Optional[Callable] = None,
+            fetch_threshold=None, fetch_cycle=None, fetch_refresh=False, inspect: Optional[Callable] = None,
             mv: Optional[MatVec] = None) -> SolveResult:
     """IDR(s)stab(l), Algorithm 1, with inputs A, b, x, s, l, P, U, V.
 
@@ -318,7 +323,10 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
 
     ``fetch_threshold`` / ``fetch_cycle`` write out (U, V) at the fetching point
     (Section 5): the first cycle end with relative recursive residual at most
-    the threshold, or the end of cycle number ``fetch_cycle``.
+    the threshold, or the end of cycle number ``fetch_cycle``.  With
+    ``fetch_refresh`` the written V is recomputed as A U (s counted MVs): the
+    recursions keep V = A U only up to a drift (about 1e-6 relative here), and
+    Algorithm 1 requires V = A U of its inputs.
     ``inspect(stage, state)`` is called after the level loop ("levels") and at
     each cycle end ("cycle") for the invariant tests."""
     mv = mv or MatVec(A)
@@ -401,7 +409,8 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
         if fetched is None:
             if (fetch_cycle is not None and cycles == fetch_cycle) or \
                (fetch_cycle is None and fetch_threshold is not None and relres <= fetch_threshold):
-                fetched = (U.copy(), V.copy())
+                Vf = np.stack([mv(u) for u in U]) if fetch_refresh else V.copy()
+                fetched = (U.copy(), Vf)
                 fetch_at = cycles
 
     relres_rec = float(np.linalg.norm(r)) / nb
@@ -442,6 +451,8 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
                     (the IDRstab baseline).
     policy "every": the final U, V of each solve are passed to the next
                     (Miltenberger's chaining, Section 3.1).
+    With ``orth_recycle`` (default) the passed basis is conditioned: V := A U
+    (s MVs, counted in the solve that wrote it), then Cholesky QR twice.
     ``first_step``/``steps`` select the slice of the sequence that is solved;
     x0 is then the solution of the step before the slice."""
     mv = MatVec(A)
@@ -458,11 +469,16 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
             U, V = rec
         want_fetch = policy == "once" and rec is None
         res = idrstab(mv.A, b, x, s, ell, P, U, V, tol, max_mvs=max_mvs,
-                      fetch_threshold=thr if want_fetch else None, mv=mv)
+                      fetch_threshold=thr if want_fetch else None, fetch_refresh=orth_recycle, mv=mv)
         if want_fetch and res.fetched is not None:
             rec = _orth_or_none(res.fetched) if orth_recycle else res.fetched
         elif policy == "every" and res.U is not None and res.cycles > 0 and res.status == OK:
-            rec = _orth_or_none((res.U, res.V)) if orth_recycle else (res.U, res.V)
+            if orth_recycle:
+                Vf = np.stack([mv(u) for u in res.U])
+                res.mvs += s
+                rec = _orth_or_none((res.U, Vf))
+            else:
+                rec = (res.U, res.V)
         solves.append(res)
         if on_solve is not None:
             on_solve(res)

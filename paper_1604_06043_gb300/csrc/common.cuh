@@ -166,12 +166,20 @@ __device__ __forceinline__ bool groups_done(RedScratch rs, int grp, int ngrp, in
 // ---------------------------------------------------------------------------
 
 // Gaussian elimination with partial pivoting on a (n x n, row-major, modified)
-// and z (rhs in, solution out).  Returns false on a pivot below
-// PIVOT_REL_TOL * max|a| (z is then zeroed).
+// and z (rhs in, solution out).  Returns false (z zeroed) when the pivot of
+// column k is below PIVOT_REL_TOL times the largest magnitude in column k of
+// the input (a zero column included).  The test is per column: the columns of
+// a projected matrix P^T W differ in scale by orders of magnitude, and column
+// scaling changes neither solvability nor the pivot rows chosen.
 __device__ inline bool lu_solve_pp(double* a, double* z, int n) {
-  double scale = 0.0;
-  for (int i = 0; i < n * n; ++i) scale = fmax(scale, fabs(a[i]));
-  bool ok = scale > 0.0 && isfinite(scale);
+  double colmax[SMAX];
+  bool ok = true;
+  for (int j = 0; j < n; ++j) {
+    double m = 0.0;
+    for (int i = 0; i < n; ++i) m = fmax(m, fabs(a[i * n + j]));
+    colmax[j] = m;
+    if (!(m > 0.0 && isfinite(m))) ok = false;
+  }
   for (int k = 0; ok && k < n; ++k) {
     int p = k;
     double best = fabs(a[k * n + k]);
@@ -179,7 +187,7 @@ __device__ inline bool lu_solve_pp(double* a, double* z, int n) {
       double v = fabs(a[i * n + k]);
       if (v > best) { best = v; p = i; }
     }
-    if (!(best >= PIVOT_REL_TOL * scale)) { ok = false; break; }
+    if (!(best >= PIVOT_REL_TOL * colmax[k])) { ok = false; break; }
     if (p != k) {
       for (int j = 0; j < n; ++j) { double t = a[k * n + j]; a[k * n + j] = a[p * n + j]; a[p * n + j] = t; }
       double t = z[k]; z[k] = z[p]; z[p] = t;

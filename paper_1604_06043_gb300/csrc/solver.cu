@@ -237,6 +237,19 @@ msstab_status cholqr2(msstab_t h, T* V, T* U, int64_t ld, bool* ok) {
   return MSSTAB_OK;
 }
 
+// V_rec := A U_rec (s products with A): the recursions keep V = A U only up to
+// a drift, and Algorithm 1 requires V = A U of its input basis.
+template <typename T>
+msstab_status refresh_v(msstab_t h, Work<T>& w, int prec, SolveOut& out) {
+  const Ctx c = h->ctx();
+  for (int q = 0; q < h->s; ++q)
+    LAUNCH(MSSTAB_K_SPMV, spmv<T>(c, h->A, w.Urec + (int64_t)q * w.ld, w.Vrec + (int64_t)q * w.ld, nullptr, nullptr,
+                                  0, 0, 0, 0, nullptr, epi_none(h)));
+  out.mvs += h->s;
+  if (prec) h->mvs32 += h->s;
+  return MSSTAB_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Arnoldi start of level s: U = first s Arnoldi vectors of K(A; r0), V = A U
 // (classical Gram-Schmidt applied twice; s products with A)
@@ -442,9 +455,13 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
         ((ctl.fetch_cycle > 0 && out.cycles == ctl.fetch_cycle) ||
          (ctl.fetch_cycle <= 0 && relres <= ctl.fetch_threshold))) {
       CK(cudaMemcpyAsync(w.Urec, Vq(-1, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
-      CK(cudaMemcpyAsync(w.Vrec, Vq(0, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
       bool ok = true;
-      if (h->opt.orth_recycle) CKS(cholqr2<T>(h, w.Vrec, w.Urec, ld, &ok));
+      if (h->opt.orth_recycle) {
+        CKS(refresh_v<T>(h, w, prec, out));
+        CKS(cholqr2<T>(h, w.Vrec, w.Urec, ld, &ok));
+      } else {
+        CK(cudaMemcpyAsync(w.Vrec, Vq(0, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+      }
       if (ok) {
         w.has_rec = true;
         out.fetched = 1;
@@ -468,14 +485,18 @@ int64_t default_max_mvs(msstab_t h) {
 
 // After a successful solve with policy EVERY, the final U, V become the store.
 template <typename T>
-msstab_status chain_recycle(msstab_t h, Work<T>& w, const SolveOut& o) {
+msstab_status chain_recycle(msstab_t h, Work<T>& w, int prec, SolveOut& o) {
   if (h->opt.fetch_policy != MSSTAB_FETCH_EVERY || o.status != MSSTAB_OK || o.cycles == 0) return MSSTAB_OK;
   const int64_t ld = w.ld;
   const int s = h->s;
   CK(cudaMemcpyAsync(w.Urec, w.V, sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
-  CK(cudaMemcpyAsync(w.Vrec, w.V + (int64_t)s * ld, sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
   bool ok = true;
-  if (h->opt.orth_recycle) CKS(cholqr2<T>(h, w.Vrec, w.Urec, ld, &ok));
+  if (h->opt.orth_recycle) {
+    CKS(refresh_v<T>(h, w, prec, o));
+    CKS(cholqr2<T>(h, w.Vrec, w.Urec, ld, &ok));
+  } else {
+    CK(cudaMemcpyAsync(w.Vrec, w.V + (int64_t)s * ld, sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+  }
   w.has_rec = ok;
   return MSSTAB_OK;
 }
@@ -498,7 +519,7 @@ SolveCtl make_ctl(msstab_t h, double tol, bool first_has_rec) {
 msstab_status solve_fp64(msstab_t h, double tol, SolveOut& o) {
   SolveCtl ctl = make_ctl(h, tol, h->w64.has_rec);
   CKS(idrstab<double>(h, h->w64, 0, ctl, o));
-  CKS(chain_recycle<double>(h, h->w64, o));
+  CKS(chain_recycle<double>(h, h->w64, 0, o));
   return MSSTAB_OK;
 }
 
@@ -559,7 +580,7 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     ctl.true_check = false;
     SolveOut io;
     CKS(idrstab<float>(h, v, 1, ctl, io));
-    CKS(chain_recycle<float>(h, v, io));
+    CKS(chain_recycle<float>(h, v, 1, io));
     o.mvs += io.mvs;
     o.cycles += io.cycles;
     o.fetched |= io.fetched;
