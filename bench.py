@@ -423,6 +423,7 @@ def main(argv=None):
         variants = {}
         for name, opts in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER)),
                            ("msstab_fp32_inner", dict(precision=M.PREC_FP32_INNER))):
+          try:
             V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, **opts)
             xv = torch.tensor(x0_np, device=dev)
             run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W)
@@ -443,17 +444,20 @@ def main(argv=None):
                 variants[name]["outer_per_system"] = round(statistics.mean(t["outer"] for t in tv), 2)
                 variants[name]["_xs"] = xs_list
             V.close()
+          except Exception as e:  # a failing variant is reported, the main line still stands
+            variants[name] = {"error": str(e)[-300:]}
         # error of the FP32-inner solutions against the FP64 solutions of the same systems
         P64 = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev)
         x64 = torch.tensor(x0_np, device=dev)
         run_sequence(M, torch, P64, f, x64, b, w.tau, w.tol, W)
         errs = []
-        for xv32 in variants["msstab_fp32_inner"].pop("_xs"):
+        for xv32 in variants["msstab_fp32_inner"].pop("_xs", []):
             P64.op_axpby(1.0 / w.tau, x64, 1.0, f, b)
             P64.solve(b, x64, w.tol)
             errs.append(float(torch.linalg.norm(xv32 - x64) / torch.linalg.norm(x64)))
         P64.close()
-        variants["msstab_fp32_inner"]["rel_err_vs_fp64_max"] = max(errs)
+        if errs:
+            variants["msstab_fp32_inner"]["rel_err_vs_fp64_max"] = max(errs)
         line["variants"] = variants
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

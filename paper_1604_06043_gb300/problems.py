@@ -176,6 +176,31 @@ def lognormal_kappa(shape: Sequence[int], sigma: float = 1.0, corr: float = 8.0,
     return np.exp(sigma * g).reshape(-1)
 
 
+CNN_LAYERS = [(2, 16), (16, 16), (16, 16), (16, 1)]   # (C_in, C_out), 3x3x3 kernels
+
+
+def cnn_init_params(seed: int = SEED_CNN) -> np.ndarray:
+    """Initial parameters of the learned-guess CNN as one flat float64 vector:
+    per layer, weights (C_out, C_in, 3, 3, 3) He-uniform with bound
+    sqrt(6 / fan_in), then C_out zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for ci, co in CNN_LAYERS:
+        bound = (6.0 / (ci * 27)) ** 0.5
+        parts.append(rng.uniform(-bound, bound, size=co * ci * 27))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts)
+
+
+def crop_origins(shape, crop: int, count: int, seed: int) -> np.ndarray:
+    """count random crop origins (z, y, x) of a crop^3 box inside a grid of the
+    given (x, y, z) shape, as an int32 array (count, 3)."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    return np.stack([rng.integers(0, nz - crop + 1, count), rng.integers(0, ny - crop + 1, count),
+                     rng.integers(0, nx - crop + 1, count)], axis=1).astype(np.int32)
+
+
 @dataclasses.dataclass
 class Workload:
     """One implicit-Euler sequence: A = I/tau + L_h, b^(i+1) = x^(i)/tau + f."""
