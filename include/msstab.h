@@ -244,6 +244,35 @@ msstab_status msstab_op_small_solve(msstab_t h, int32_t n, const double* d_M, co
  * that fails); tau = 0 if a level vector is zero. */
 msstab_status msstab_op_tau_solve(msstab_t h, int32_t ell, const double* d_gram, double* d_tau);
 
+/* ---------------------------------------------------------------------------
+ * Allocation-free entry point (the paper has no counterpart: it is a service
+ * for callers that may not allocate device memory themselves -- for example a
+ * solver embedded in a host application that owns all device memory through
+ * its own pool, or a time-critical loop in which an allocation, which can
+ * synchronise the device or fail at run time, is not allowed).
+ *
+ * y = A x for the CSR matrix (d_row_ptr[n+1], d_col[nnz], d_val[nnz], int32
+ * indices, FP64 values) fused with d_dots[c] = P_c . y for c < s (P columns at
+ * d_P + c*ldp, ldp >= n) and d_dots[s] = y . y -- the same kernel and results
+ * as msstab_op_spmv_dot on a CSR handle, without a handle.  The caller passes
+ * all inputs and outputs; the reduction scratch is a fixed device array inside
+ * the library (about 160 KB, one per GPU that loads the library, held until the
+ * process exits).  Limits: 1 <= n < 2^31 - 64, 0 <= nnz < 2^31, 0 <= s <= 16;
+ * other sizes are rejected with MSSTAB_ERR_INVALID_ARG and a message in
+ * msstab_last_error(NULL).  The call allocates nothing (no cudaMalloc, no
+ * cudaFree, no allocating library routine); it is asynchronous on `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  The first call on a
+ * device looks up the device address of the scratch array (once per device,
+ * with that device current); make that first call before any stream capture.
+ * Every call shares the one scratch array, which keeps the last call's
+ * contents (the call clears what must start at zero): calls that overlap on
+ * the GPU -- concurrent streams, or several host threads -- race and must be
+ * serialised by the caller.
+ */
+msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const int32_t* d_row_ptr, const int32_t* d_col,
+                                      const double* d_val, const double* d_x, double* d_y, const double* d_P,
+                                      int64_t ldp, int32_t s, double* d_dots, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,9 +5,14 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
+
 #include "common.cuh"
 
 namespace msk {
+
+// Text returned by msstab_last_error(NULL) (entry points without a handle).
+void set_global_error(const std::string& what);
 
 struct Ctx {
   cudaStream_t stream;

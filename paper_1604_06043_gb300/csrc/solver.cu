@@ -661,6 +661,8 @@ msstab_status solve_common(msstab_t h, double tol, msstab_stats* st) {
 
 }  // namespace
 
+void msk::set_global_error(const std::string& what) { g_create_error = what; }
+
 // ===========================================================================
 // C ABI
 // ===========================================================================

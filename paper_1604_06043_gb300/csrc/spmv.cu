@@ -9,7 +9,10 @@
 // column -1 and are skipped.  CSR: one thread per row (the baseline format).
 // All loads of matrix data are single-use and go through the read-only path.
 
+#include <mutex>
+
 #include "launch.h"
+#include "msstab.h"
 
 namespace msk {
 
@@ -290,3 +293,95 @@ cudaError_t sell_fill(const Ctx& c, int n, int nslices, const int* row_ptr, cons
 }
 
 }  // namespace msk
+
+// ===========================================================================
+// Allocation-free form of the fused product y = A x, P^T y (CSR).
+//
+// For callers that may not allocate device memory themselves -- code embedded
+// in a host application that owns all device memory through its own pool, or
+// time-critical loops where an allocation (which can synchronise the device or
+// fail at run time) is not allowed.  The reduction scratch (one partial sum per
+// thread block plus the ticket of the last-block combine) lives in this
+// file-scope device array instead of in memory the caller provides.  Every GPU
+// that loads the library holds one copy of it until the process exits.
+// ===========================================================================
+namespace msk {
+constexpr int NOALLOC_MAX_BLOCKS = 1024;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+constexpr size_t NOALLOC_DOUBLES = (size_t)NOALLOC_MAX_BLOCKS * MAXRED + 32;
+static __device__ __align__(256) double g_noalloc_scratch[NOALLOC_DOUBLES];
+}  // namespace msk
+
+extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const int32_t* d_row_ptr,
+                                                 const int32_t* d_col, const double* d_val, const double* d_x,
+                                                 double* d_y, const double* d_P, int64_t ldp, int32_t s,
+                                                 double* d_dots, void* stream) {
+  using namespace msk;
+  if (n < 1 || n >= (1LL << 31) - 64 || nnz < 0 || nnz >= (1LL << 31)) {
+    set_global_error("msstab_spmv_dot_noalloc: n must be in [1, 2^31 - 64) and nnz in [0, 2^31)");
+    return MSSTAB_ERR_INVALID_ARG;
+  }
+  if (s < 0 || s > SMAX) {
+    set_global_error("msstab_spmv_dot_noalloc: s must be in [0, 16] (the scratch holds 17 sums per block)");
+    return MSSTAB_ERR_INVALID_ARG;
+  }
+  if (!d_row_ptr || !d_x || !d_y || !d_dots || (nnz > 0 && (!d_col || !d_val)) || (s > 0 && (!d_P || ldp < n))) {
+    set_global_error("msstab_spmv_dot_noalloc: NULL pointer or ldp < n");
+    return MSSTAB_ERR_INVALID_ARG;
+  }
+  // Set-up, once per device and with that device current: the device address
+  // of the scratch array (its name is only a stand-in in host code).
+  static std::mutex mu;
+  static void* addr[NOALLOC_MAX_DEVICES] = {};
+  static int sms[NOALLOC_MAX_DEVICES] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+    set_global_error("msstab_spmv_dot_noalloc: no usable current device");
+    return MSSTAB_ERR_CUDA;
+  }
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        set_global_error(std::string("msstab_spmv_dot_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+        return MSSTAB_ERR_CUDA;
+      }
+      int m = 0;
+      e = cudaDeviceGetAttribute(&m, cudaDevAttrMultiProcessorCount, dev);
+      if (e != cudaSuccess) {
+        set_global_error(std::string("msstab_spmv_dot_noalloc: ") + cudaGetErrorString(e));
+        return MSSTAB_ERR_CUDA;
+      }
+      sms[dev] = m;
+      addr[dev] = ptr;
+    }
+  }
+  double* base = (double*)addr[dev];
+  RedScratch rs{base, nullptr, (unsigned int*)(base + (size_t)NOALLOC_MAX_BLOCKS * MAXRED), NOALLOC_MAX_BLOCKS};
+  cudaStream_t st = (cudaStream_t)stream;
+  // the ticket must start at zero (the array keeps the last call's contents)
+  e = cudaMemsetAsync(rs.tickets, 0, sizeof(unsigned int), st);
+  if (e != cudaSuccess) {
+    set_global_error(std::string("msstab_spmv_dot_noalloc: ") + cudaGetErrorString(e));
+    return MSSTAB_ERR_CUDA;
+  }
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_csr_kernel<double, true>, NT, 0) != cudaSuccess ||
+      nb < 1)
+    nb = 1;
+  int64_t g = ((int64_t)n + NT - 1) / NT;
+  if (g > (int64_t)nb * sms[dev]) g = (int64_t)nb * sms[dev];
+  if (g > NOALLOC_MAX_BLOCKS) g = NOALLOC_MAX_BLOCKS;
+  CsrMat<double> M{(int)n, d_row_ptr, d_col, d_val};
+  SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs};
+  spmv_csr_kernel<double, true><<<(int)g, NT, 0, st>>>(M, a);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_global_error(std::string("msstab_spmv_dot_noalloc: launch: ") + cudaGetErrorString(e));
+    return MSSTAB_ERR_CUDA;
+  }
+  return MSSTAB_OK;
+}

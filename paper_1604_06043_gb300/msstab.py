@@ -102,6 +102,7 @@ _SIGS = {
     "msstab_op_tau_update": (_I32, [_P, _I32, _P, _P, _P, _I64, _P]),
     "msstab_op_small_solve": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "msstab_op_tau_solve": (_I32, [_P, _I32, _P, _P]),
+    "msstab_spmv_dot_noalloc": (_I32, [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I32, _P, _P]),
 }
 
 _lib = None
