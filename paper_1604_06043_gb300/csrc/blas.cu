@@ -256,10 +256,10 @@ __global__ void __launch_bounds__(NT) tau_kernel(TauArgs<T> a) {
   }
   if (!a.proj) return;
   const int m = a.s + (t == 0 ? 1 : 0);
-  double fin[MAXRED];
+  double fin[32];
 #pragma unroll
-  for (int i = 0; i < MAXRED; ++i) fin[i] = i < SMAX && i < a.s ? acc[i < SMAX ? i : 0] : (i == a.s ? accr : 0.0);
-  block_reduce<MAXRED>(fin, m, smem_w, red);
+  for (int i = 0; i < 32; ++i) fin[i] = i < SMAX && i < a.s ? acc[i < SMAX ? i : 0] : (i == a.s ? accr : 0.0);
+  block_reduce<32>(fin, m, smem_w, red);
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
   if (!groups_done(a.rs, t, nt, m, red, &s_last)) return;
   // very last block: scatter all groups' sums into the device state
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(NT) tau_kernel(TauArgs<T> a) {
   if (threadIdx.x == 0) st->rr = __ldcg(a.rs.group_out + a.s);
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) run_epilogue(a.epi, ew);
+  if (threadIdx.x < 32) run_epilogue(a.epi, ew);
 }
 
 template <typename T>
@@ -329,10 +329,10 @@ __global__ void __launch_bounds__(NT) multidot_kernel(MdArgs<T> a) {
     accs = fma(xv, xv, accs);
   }
   const int m = a.ny + a.self;
-  double fin[MAXRED];
+  double fin[32];
 #pragma unroll
-  for (int i = 0; i < MAXRED; ++i) fin[i] = i < MD_MAXC && i < a.ny ? acc[i < MD_MAXC ? i : 0] : (i == a.ny ? accs : 0.0);
-  block_reduce<MAXRED>(fin, m, smem_w, red);
+  for (int i = 0; i < 32; ++i) fin[i] = i < MD_MAXC && i < a.ny ? acc[i < MD_MAXC ? i : 0] : (i == a.ny ? accs : 0.0);
+  block_reduce<32>(fin, m, smem_w, red);
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
   if (!groups_done(a.rs, t, a.nt, m, red, &s_last)) return;
   for (int i = threadIdx.x; i < a.nt * m; i += NT) {
@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(NT) multidot_kernel(MdArgs<T> a) {
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) run_epilogue(a.epi, ew);
+  if (threadIdx.x < 32) run_epilogue(a.epi, ew);
 }
 
 template <typename T>
@@ -448,17 +448,19 @@ cudaError_t small_cholesky(const Ctx& c, int s, const double* G, double* R, int*
   return cudaGetLastError();
 }
 
+// The warp-parallel elimination that the reduction epilogues use.
 __global__ void small_lu_kernel(int n, const double* M, const double* rhs, double* z, int* flag) {
-  double a[SMAX * SMAX], y[SMAX];
-  for (int i = 0; i < n * n; ++i) a[i] = M[i];
-  for (int i = 0; i < n; ++i) y[i] = rhs[i];
-  const bool ok = lu_solve_pp(a, y, n);
-  for (int i = 0; i < n; ++i) z[i] = y[i];
-  *flag = ok ? 0 : 1;
+  __shared__ double a[SMAX * SMAX], y[SMAX], l[SMAX];
+  for (int i = threadIdx.x; i < n * n; i += 32) a[i] = M[i];
+  if (threadIdx.x < n) y[threadIdx.x] = rhs[threadIdx.x];
+  __syncwarp();
+  const bool ok = warp_lu_solve(a, y, n, l);
+  if (threadIdx.x < n) z[threadIdx.x] = y[threadIdx.x];
+  if (threadIdx.x == 0) *flag = ok ? 0 : 1;
 }
 
 cudaError_t small_lu(const Ctx& c, int n, const double* M, const double* rhs, double* z, int* flag) {
-  small_lu_kernel<<<1, 1, 0, c.stream>>>(n, M, rhs, z, flag);
+  small_lu_kernel<<<1, 32, 0, c.stream>>>(n, M, rhs, z, flag);
   return cudaGetLastError();
 }
 

@@ -91,23 +91,63 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Reduce acc[0..m) of all threads of the block into red[0..m) (shared).
-// Uses smem_w[NWARP * MAXRED].  Ends with a __syncthreads().
-template <int MAXM>
-__device__ __forceinline__ void block_reduce(const double (&acc)[MAXM], int m, double* smem_w, double* red) {
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+// Reduce-scatter inside a warp: CNT values per lane, exchanged over xor
+// distance O, O/2, ..., 1.  While more than one value is left, each lane keeps
+// half of them (the upper half if bit O of its lane id is set) and adds the
+// partner's copy of that half, so a lane spends CNT/2 + CNT/4 + ... additions
+// instead of 5 per value.  Afterwards v[0] of lane L holds the warp sum of
+// value index rs_index<CNT>(L).
+template <int CNT, int O, int M>
+struct RedScatter {
+  static __device__ __forceinline__ void run(double (&v)[M], int lane) {
+    if constexpr (CNT > 1) {
+      constexpr int H = CNT / 2;
+      const bool up = (lane & O) != 0;
 #pragma unroll
-  for (int i = 0; i < MAXM; ++i) {
-    if (i < m) {
-      double v = warp_sum(acc[i]);
-      if (lane == 0) smem_w[w * MAXRED + i] = v;
+      for (int i = 0; i < H; ++i) {
+        const double send = up ? v[i] : v[i + H];
+        const double keep = up ? v[i + H] : v[i];
+        v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
+      }
+      if constexpr (O > 1) RedScatter<H, O / 2, M>::run(v, lane);
+    } else {
+      v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
+      if constexpr (O > 1) RedScatter<1, O / 2, M>::run(v, lane);
     }
   }
+};
+
+template <int M>
+__device__ __forceinline__ int rs_index(int lane) {
+  int idx = 0, cnt = M;
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    if (cnt > 1) {
+      cnt >>= 1;
+      if (lane & o) idx += cnt;
+    }
+  }
+  return idx;
+}
+
+// Reduce v[0..m) (m <= M, M a power of two <= 32) of all threads of the block
+// into red[0..m) (shared), in a fixed order.  Uses smem_w[NWARP * MAXRED].
+// Ends with a __syncthreads().
+template <int M>
+__device__ __forceinline__ void block_reduce(double (&v)[M], int m, double* smem_w, double* red) {
+  static_assert(M >= 1 && M <= 32 && (M & (M - 1)) == 0, "M must be a power of two <= 32");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  RedScatter<M, 16, M>::run(v, lane);
+  // lanes whose low bits (those not used to split values) are zero publish
+  constexpr int SPLIT_BITS = M >= 32 ? 5 : (M >= 16 ? 4 : (M >= 8 ? 3 : (M >= 4 ? 2 : (M >= 2 ? 1 : 0))));
+  constexpr int LOW_MASK = (1 << (5 - SPLIT_BITS)) - 1;
+  const int idx = rs_index<M>(lane);
+  if ((lane & LOW_MASK) == 0 && idx < m) smem_w[w * MAXRED + idx] = v[0];
   __syncthreads();
   if (threadIdx.x < m) {
-    double v = 0.0;
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) v += smem_w[j * MAXRED + threadIdx.x];
-    red[threadIdx.x] = v;
+    double s = 0.0;
+    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += smem_w[j * MAXRED + threadIdx.x];
+    red[threadIdx.x] = s;
   }
   __syncthreads();
 }
@@ -211,6 +251,76 @@ __device__ inline bool lu_solve_pp(double* a, double* z, int n) {
   return true;
 }
 
+// The same elimination by one warp (all 32 lanes call it): lane j < n owns
+// column j and lane n the right-hand side; a (n x n, row-major) and z live in
+// shared memory, lbuf holds n multipliers.  Same pivot rows (first maximum),
+// same per-column breakdown test and the same formulas as lu_solve_pp; only
+// the summation order of the back substitution differs.  Returns the same
+// (warp-uniform) result; z is zeroed on breakdown.
+__device__ inline bool warp_lu_solve(double* a, double* z, int n, double* lbuf) {
+  const unsigned FULL = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  double cm = 0.0;
+  if (lane < n)
+    for (int i = 0; i < n; ++i) cm = fmax(cm, fabs(a[i * n + lane]));
+  bool ok = !__any_sync(FULL, lane < n && !(cm > 0.0 && isfinite(cm)));
+  for (int k = 0; ok && k < n; ++k) {
+    double v = (lane >= k && lane < n) ? fabs(a[lane * n + k]) : -1.0;
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      const double ov = __shfl_xor_sync(FULL, v, o);
+      const int oi = __shfl_xor_sync(FULL, idx, o);
+      if (ov > v || (ov == v && oi < idx)) {
+        v = ov;
+        idx = oi;
+      }
+    }
+    const double ck = __shfl_sync(FULL, cm, k);
+    if (!(v >= PIVOT_REL_TOL * ck)) {
+      ok = false;
+      break;
+    }
+    const int p = idx;
+    if (p != k) {
+      if (lane < n) {
+        const double tmp = a[k * n + lane];
+        a[k * n + lane] = a[p * n + lane];
+        a[p * n + lane] = tmp;
+      } else if (lane == n) {
+        const double tmp = z[k];
+        z[k] = z[p];
+        z[p] = tmp;
+      }
+    }
+    __syncwarp();
+    const double piv = a[k * n + k];
+    if (lane > k && lane < n) lbuf[lane] = a[lane * n + k] / piv;
+    __syncwarp();
+    if (lane >= k && lane < n) {
+      const double akj = a[k * n + lane];
+      for (int i = k + 1; i < n; ++i) a[i * n + lane] -= lbuf[i] * akj;
+    } else if (lane == n) {
+      const double zk = z[k];
+      for (int i = k + 1; i < n; ++i) z[i] -= lbuf[i] * zk;
+    }
+    __syncwarp();
+  }
+  if (!ok) {
+    if (lane < n) z[lane] = 0.0;
+    __syncwarp();
+    return false;
+  }
+  for (int k = n - 1; k >= 0; --k) {
+    double t = (lane > k && lane < n) ? a[k * n + lane] * z[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
+    if (lane == 0) z[k] = (z[k] - t) / a[k * n + k];
+    __syncwarp();
+  }
+  return true;
+}
+
 // Upper Cholesky factor R (row-major, R^T R = G) of the n x n matrix G.
 // Returns false if a pivot d_j is not above rel_tol * G_jj (rel_tol = 0: not
 // positive; a positive rel_tol detects numerically rank-deficient bases).
@@ -277,40 +387,38 @@ __device__ inline void tau_from_gram(const double* G, int ell, double* tau, doub
 struct EpiScratch {
   double a[SMAX * SMAX];
   double z[SMAX];
+  double l[SMAX];
   double g[(LMAX + 1) * (LMAX + 1)];
   double wk[2 * LMAX * LMAX + 2 * LMAX];
 };
 
-// The small solve that follows a reduction (run by thread 0 of the last block).
+// The small solve that follows a reduction, run by warp 0 of the last block
+// (all 32 lanes call it; the coefficient solves are warp-parallel).
 __device__ inline void run_epilogue(const Epi& e, EpiScratch& w) {
   if (e.kind == EPI_NONE) return;
+  const int lane = threadIdx.x & 31;
   DevState* st = e.st;
   const int s = e.s;
-  double* a = w.a;
-  double* z = w.z;
-  if (e.kind == EPI_GAMMA) {
-    // (P^T V^(k)) gamma = P^T r^(k)
-    for (int c = 0; c < s; ++c) {
-      for (int j = 0; j < s; ++j) a[c * s + j] = __ldcg(&st->projV[(e.k * SMAX + j) * SMAX + c]);
-      z[c] = __ldcg(&st->projR[e.k * SMAX + c]);
+  if (e.kind == EPI_GAMMA || e.kind == EPI_ETA) {
+    // GAMMA: (P^T V^(k)) gamma = P^T r^(k);  ETA: (P^T W^(k)) eta_q = P^T r^(k+1)
+    // with W^(k) = [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}]
+    const int rlev = e.kind == EPI_GAMMA ? e.k : e.k + 1;
+    for (int i = lane; i < s * s; i += 32) {
+      const int c = i / s, j = i % s;
+      const int lev = (e.kind == EPI_ETA && j < e.q) ? e.k + 1 : e.k;
+      w.a[i] = __ldcg(&st->projV[(lev * SMAX + j) * SMAX + c]);
     }
-    if (!lu_solve_pp(a, z, s)) st->flag |= FLAG_BREAKDOWN;
-    for (int j = 0; j < s; ++j) st->gamma[e.k * SMAX + j] = z[j];
-  } else if (e.kind == EPI_ETA) {
-    // (P^T W^(k)) eta_q = P^T r^(k+1), W^(k) = [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}]
-    for (int c = 0; c < s; ++c) {
-      for (int j = 0; j < s; ++j) {
-        const int lev = j < e.q ? e.k + 1 : e.k;
-        a[c * s + j] = __ldcg(&st->projV[(lev * SMAX + j) * SMAX + c]);
-      }
-      z[c] = __ldcg(&st->projR[(e.k + 1) * SMAX + c]);
-    }
-    if (!lu_solve_pp(a, z, s)) st->flag |= FLAG_BREAKDOWN;
-    for (int j = 0; j < s; ++j) st->eta[(e.k * SMAX + e.q) * SMAX + j] = z[j];
+    if (lane < s) w.z[lane] = __ldcg(&st->projR[rlev * SMAX + lane]);
+    __syncwarp();
+    const bool ok = warp_lu_solve(w.a, w.z, s, w.l);
+    if (lane == 0 && !ok) st->flag |= FLAG_BREAKDOWN;
+    double* out = e.kind == EPI_GAMMA ? &st->gamma[e.k * SMAX] : &st->eta[(e.k * SMAX + e.q) * SMAX];
+    if (lane < s) out[lane] = w.z[lane];
   } else if (e.kind == EPI_TAU) {
     const int L = e.ell + 1;
-    for (int i = 0; i < L * L; ++i) w.g[i] = __ldcg(&st->gram[i]);
-    tau_from_gram(w.g, e.ell, st->tau, w.wk);
+    for (int i = lane; i < L * L; i += 32) w.g[i] = __ldcg(&st->gram[i]);
+    __syncwarp();
+    if (lane == 0) tau_from_gram(w.g, e.ell, st->tau, w.wk);
   }
 }
 

@@ -5,8 +5,11 @@
 //
 // Formats.  SELL-32-sigma: rows in slices of 32 (one warp per slice, one row
 // per lane), entries stored column-major within the slice so that every load of
-// the warp is one contiguous 128/256-byte segment; padding entries carry
-// column -1 and are skipped.  CSR: one thread per row (the baseline format).
+// the warp is one contiguous 128/256-byte segment; padding entries are zero
+// coefficients on the row's own index (they add an exact 0 for finite x, so the
+// sum equals the CSR sum bit for bit), and the row loop runs exactly the slice
+// width (chunks of 8 plus an exact tail: no predicated multiply-adds).
+// CSR: one thread per row (the baseline format).
 // All loads of matrix data are single-use and go through the read-only path.
 
 #include <mutex>
@@ -35,107 +38,124 @@ struct SpmvArgs {
   RedScratch rs;
 };
 
-// Per-thread accumulators of the fused dot products (P^T y, y.y, b.b).
+// Smallest power of two >= v (v <= 32).
+__host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : (v <= 2 ? 2 : (v <= 4 ? 4 : (v <= 8 ? 8 : (v <= 16 ? 16 : 32)))); }
+
+// Per-thread accumulators of the fused dot products: NP slots for P^T y (np <=
+// NP used), then y.y and b.b in fixed slots.
+template <int NP>
 struct DotAcc {
-  double p[SMAX];
-  double self, bb;
+  double v[NP + 2];
 };
 
-template <typename T>
-__device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc& acc) {
+template <typename T, int NP>
+__device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc<NP>& acc) {
   const double yd = (double)yv;
 #pragma unroll
-  for (int c = 0; c < SMAX; ++c)
-    if (c < a.np) acc.p[c] = fma(yd, (double)ro(a.P + (int64_t)c * a.ldp + row), acc.p[c]);
-  acc.self = fma(yd, yd, acc.self);
+  for (int c = 0; c < NP; ++c)
+    if (c < a.np) acc.v[c] = fma(yd, (double)ro(a.P + (int64_t)c * a.ldp + row), acc.v[c]);
+  if (a.self) acc.v[NP] = fma(yd, yd, acc.v[NP]);
   if (a.bdot) {
     const double bd = (double)a.b[row];
-    acc.bb = fma(bd, bd, acc.bb);
+    acc.v[NP + 1] = fma(bd, bd, acc.v[NP + 1]);
   }
 }
 
-template <typename T, bool DOT>
-__device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc& acc) {
-  if (!DOT) return;
+template <typename T, int NP>
+__device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<NP>& acc) {
+  constexpr int M = pow2_at_least(NP + 2);
   __shared__ double smem_w[NWARP * MAXRED];
   __shared__ double red[MAXRED];
   __shared__ int s_last;
   __shared__ EpiScratch ew;
   const int m = a.np + a.self + a.bdot;
-  double fin[MAXRED];
+  // compact (P^T y [np], y.y?, b.b?) into the first m slots
+  double fin[M];
 #pragma unroll
-  for (int i = 0; i < MAXRED; ++i) {
-    fin[i] = (i < SMAX && i < a.np) ? acc.p[i < SMAX ? i : 0] : 0.0;
-    if (a.self && i == a.np) fin[i] = acc.self;
-    if (a.bdot && i == a.np + a.self) fin[i] = acc.bb;
+  for (int i = 0; i < M; ++i) {
+    double v = 0.0;
+    if (i < NP && i < a.np) v = acc.v[i < NP ? i : 0];
+    if (a.self && i == a.np) v = acc.v[NP];
+    if (a.bdot && i == a.np + a.self) v = acc.v[NP + 1];
+    fin[i] = v;
   }
-  block_reduce<MAXRED>(fin, m, smem_w, red);
+  block_reduce<M>(fin, m, smem_w, red);
   if (grid_reduce(a.rs, 0, blockIdx.x, gridDim.x, m, red, &s_last)) {
     if (threadIdx.x < m) a.out[threadIdx.x] = red[threadIdx.x];
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) run_epilogue(a.epi, ew);
+    if (threadIdx.x < 32) run_epilogue(a.epi, ew);
   }
 }
 
-template <typename T, bool DOT>
-__global__ void __launch_bounds__(NT) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
-  DotAcc acc;
+// K consecutive entries of a SELL row (stride 32), continuing the row's
+// multiply-add chain in column order (as CSR does).
+template <typename T, int K>
+__device__ __forceinline__ T sell_chunk(const int* __restrict__ col, const T* __restrict__ val,
+                                        const T* __restrict__ x, int64_t base, T sum) {
+  int c[K];
+  T v[K];
 #pragma unroll
-  for (int i = 0; i < SMAX; ++i) acc.p[i] = 0.0;
-  acc.self = acc.bb = 0.0;
+  for (int u = 0; u < K; ++u) {
+    c[u] = ro(col + base + (int64_t)u * 32);
+    v[u] = ro(val + base + (int64_t)u * 32);
+  }
+#pragma unroll
+  for (int u = 0; u < K; ++u) sum = fma_t(v[u], ro(x + c[u]), sum);
+  return sum;
+}
+
+// One row of width w: chunks of 8, then an exact tail (no predicated slots).
+template <typename T>
+__device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __restrict__ val,
+                                      const T* __restrict__ x, int64_t base, int w) {
+  T sum = T(0);
+  int j = 0;
+  for (; j + 8 <= w; j += 8) sum = sell_chunk<T, 8>(col, val, x, base + (int64_t)j * 32, sum);
+  const int64_t b = base + (int64_t)j * 32;
+  switch (w - j) {
+    case 1: return sell_chunk<T, 1>(col, val, x, b, sum);
+    case 2: return sell_chunk<T, 2>(col, val, x, b, sum);
+    case 3: return sell_chunk<T, 3>(col, val, x, b, sum);
+    case 4: return sell_chunk<T, 4>(col, val, x, b, sum);
+    case 5: return sell_chunk<T, 5>(col, val, x, b, sum);
+    case 6: return sell_chunk<T, 6>(col, val, x, b, sum);
+    case 7: return sell_chunk<T, 7>(col, val, x, b, sum);
+    default: return sum;
+  }
+}
+
+// NP < 0: plain product; NP >= 0: also the reduction of up to NP dots with P,
+// y.y and b.b, and the epilogue.
+template <typename T, int NP>
+__global__ void __launch_bounds__(NT, 4) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
+  constexpr int NA = NP < 0 ? 0 : NP;
+  DotAcc<NA> acc;
+#pragma unroll
+  for (int i = 0; i < NA + 2; ++i) acc.v[i] = 0.0;
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * NWARP;
   for (int sl = (blockIdx.x * NT + threadIdx.x) >> 5; sl < A.nslices; sl += nwarps) {
     const int w = ro(A.slice_w + sl);
     const int64_t base = (int64_t)ro(A.slice_ptr + sl) + lane;
-    T sum = T(0);
-    int j = 0;
-    for (; j + 8 <= w; j += 8) {
-      int cc[8];
-      T vv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        cc[u] = ro(A.col + base + (int64_t)(j + u) * 32);
-        vv[u] = ro(A.val + base + (int64_t)(j + u) * 32);
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (cc[u] >= 0) sum = fma_t(vv[u], ro(a.x + cc[u]), sum);
-    }
-    if (j < w) {
-      int cc[8];
-      T vv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        cc[u] = -1;
-        vv[u] = T(0);
-        if (j + u < w) {
-          cc[u] = ro(A.col + base + (int64_t)(j + u) * 32);
-          vv[u] = ro(A.val + base + (int64_t)(j + u) * 32);
-        }
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u)
-        if (cc[u] >= 0) sum = fma_t(vv[u], ro(a.x + cc[u]), sum);
-    }
+    const T sum = sell_row<T>(A.col, A.val, a.x, base, w);
     const int pos = sl * 32 + lane;
     if (pos < A.n) {
       const int row = A.perm ? ro(A.perm + pos) : pos;
       const T yv = a.b ? (T)(a.b[row] - sum) : sum;
       a.y[row] = yv;
-      if (DOT) acc_row(a, row, yv, acc);
+      if (NP >= 0) acc_row<T, NA>(a, row, yv, acc);
     }
   }
-  finish<T, DOT>(a, acc);
+  if constexpr (NP >= 0) finish<T, NA>(a, acc);
 }
 
-template <typename T, bool DOT>
-__global__ void __launch_bounds__(NT) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a) {
-  DotAcc acc;
+template <typename T, int NP>
+__global__ void __launch_bounds__(NT, 4) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a) {
+  constexpr int NA = NP < 0 ? 0 : NP;
+  DotAcc<NA> acc;
 #pragma unroll
-  for (int i = 0; i < SMAX; ++i) acc.p[i] = 0.0;
-  acc.self = acc.bb = 0.0;
+  for (int i = 0; i < NA + 2; ++i) acc.v[i] = 0.0;
   const int stride = gridDim.x * NT;
   for (int row = blockIdx.x * NT + threadIdx.x; row < A.n; row += stride) {
     const int beg = ro(A.row_ptr + row), end = ro(A.row_ptr + row + 1);
@@ -143,9 +163,9 @@ __global__ void __launch_bounds__(NT) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a
     for (int p = beg; p < end; ++p) sum = fma_t(ro(A.val + p), ro(a.x + ro(A.col + p)), sum);
     const T yv = a.b ? (T)(a.b[row] - sum) : sum;
     a.y[row] = yv;
-    if (DOT) acc_row(a, row, yv, acc);
+    if (NP >= 0) acc_row<T, NA>(a, row, yv, acc);
   }
-  finish<T, DOT>(a, acc);
+  if constexpr (NP >= 0) finish<T, NA>(a, acc);
 }
 
 template <typename K>
@@ -163,35 +183,50 @@ const double* pick_val<double>(const MatDesc& A, bool sell) { return sell ? A.sv
 template <>
 const float* pick_val<float>(const MatDesc& A, bool sell) { return sell ? A.sval32 : A.val32; }
 
+template <typename T, int NP>
+static void launch_sell(const Ctx& c, const SellMat<T>& M, const SpmvArgs<T>& a) {
+  static int cap = max_grid(spmv_sell_kernel<T, NP>, c);
+  const int64_t need = ((int64_t)M.nslices * 32 + NT - 1) / NT;
+  spmv_sell_kernel<T, NP><<<(int)(need < cap ? need : cap), NT, 0, c.stream>>>(M, a);
+}
+
+template <typename T, int NP>
+static void launch_csr(const Ctx& c, const CsrMat<T>& M, const SpmvArgs<T>& a) {
+  static int cap = max_grid(spmv_csr_kernel<T, NP>, c);
+  const int64_t need = ((int64_t)M.n + NT - 1) / NT;
+  spmv_csr_kernel<T, NP><<<(int)(need < cap ? need : cap), NT, 0, c.stream>>>(M, a);
+}
+
 template <typename T>
 cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
                  int np, int self, int bdot, double* out, Epi epi) {
+  if (np < 0 || np > SMAX) return cudaErrorInvalidValue;
   SpmvArgs<T> a{x, y, b, P, ldp, np, self, bdot, out, epi, c.rs};
   const bool dot = (np + self + bdot) > 0;
   if (A.format == 0) {
     SellMat<T> M{A.n, A.nslices, A.slice_ptr, A.slice_w, A.perm, A.scol, pick_val<T>(A, true)};
-    const int64_t need = ((int64_t)A.nslices * 32 + NT - 1) / NT;
-    if (dot) {
-      static int cap = max_grid(spmv_sell_kernel<T, true>, c);
-      int g = (int)(need < cap ? need : cap);
-      spmv_sell_kernel<T, true><<<g, NT, 0, c.stream>>>(M, a);
-    } else {
-      static int cap = max_grid(spmv_sell_kernel<T, false>, c);
-      int g = (int)(need < cap ? need : cap);
-      spmv_sell_kernel<T, false><<<g, NT, 0, c.stream>>>(M, a);
-    }
+    if (!dot)
+      launch_sell<T, -1>(c, M, a);
+    else if (np == 0)
+      launch_sell<T, 0>(c, M, a);
+    else if (np <= 4)
+      launch_sell<T, 4>(c, M, a);
+    else if (np <= 8)
+      launch_sell<T, 8>(c, M, a);
+    else
+      launch_sell<T, 16>(c, M, a);
   } else {
     CsrMat<T> M{A.n, A.row_ptr, A.col, pick_val<T>(A, false)};
-    const int64_t need = ((int64_t)A.n + NT - 1) / NT;
-    if (dot) {
-      static int cap = max_grid(spmv_csr_kernel<T, true>, c);
-      int g = (int)(need < cap ? need : cap);
-      spmv_csr_kernel<T, true><<<g, NT, 0, c.stream>>>(M, a);
-    } else {
-      static int cap = max_grid(spmv_csr_kernel<T, false>, c);
-      int g = (int)(need < cap ? need : cap);
-      spmv_csr_kernel<T, false><<<g, NT, 0, c.stream>>>(M, a);
-    }
+    if (!dot)
+      launch_csr<T, -1>(c, M, a);
+    else if (np == 0)
+      launch_csr<T, 0>(c, M, a);
+    else if (np <= 4)
+      launch_csr<T, 4>(c, M, a);
+    else if (np <= 8)
+      launch_csr<T, 8>(c, M, a);
+    else
+      launch_csr<T, 16>(c, M, a);
   }
   return cudaGetLastError();
 }
@@ -265,9 +300,9 @@ __global__ void sell_fill_kernel(int n, int nslices, const int* row_ptr, const i
     const int sl = (int)(pos >> 5), lane = (int)(pos & 31);
     const int w = slice_w[sl];
     const int64_t base = (int64_t)slice_ptr[sl] + lane;
-    int b = 0, len = 0;
+    int b = 0, len = 0, row = 0;
     if (pos < n) {
-      const int row = perm ? perm[pos] : (int)pos;
+      row = perm ? perm[pos] : (int)pos;
       b = row_ptr[row];
       len = row_ptr[row + 1] - b;
     }
@@ -276,8 +311,8 @@ __global__ void sell_fill_kernel(int n, int nslices, const int* row_ptr, const i
       if (j < len) {
         scol[o] = col[b + j];
         sval[o] = val[b + j];
-      } else {
-        scol[o] = -1;
+      } else {  // padding: a zero coefficient on the row's own index
+        scol[o] = row;
         sval[o] = 0.0;
       }
     }
@@ -369,7 +404,7 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
     return MSSTAB_ERR_CUDA;
   }
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_csr_kernel<double, true>, NT, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_csr_kernel<double, 16>, NT, 0) != cudaSuccess ||
       nb < 1)
     nb = 1;
   int64_t g = ((int64_t)n + NT - 1) / NT;
@@ -377,7 +412,7 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
   if (g > NOALLOC_MAX_BLOCKS) g = NOALLOC_MAX_BLOCKS;
   CsrMat<double> M{(int)n, d_row_ptr, d_col, d_val};
   SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs};
-  spmv_csr_kernel<double, true><<<(int)g, NT, 0, st>>>(M, a);
+  spmv_csr_kernel<double, 16><<<(int)g, NT, 0, st>>>(M, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_global_error(std::string("msstab_spmv_dot_noalloc: launch: ") + cudaGetErrorString(e));
