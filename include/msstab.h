@@ -76,13 +76,19 @@ typedef struct msstab_options {
                               paper's plain hand-over) */
   int64_t max_mvs;         /* products with A per solve; <= 0: min(100000, 20 sqrt(n) + 1 + s + 2l(s+1)) */
   double inner_tol;        /* FP32 inner: relative tolerance of each inner solve (tested on its
-                              recursive residual); <= 0: max(1e-4, 0.5 tol ||b|| / ||r_outer||) */
+                              recursive residual); <= 0: max(1e-5, 0.5 tol ||b|| / ||r_outer||).
+                              An inner solve also stops when its residual has not halved in 4
+                              cycles (the FP32 floor near kappa * 6e-8 is reached) */
   int32_t spmv_format;     /* MSSTAB_FORMAT_SELL (default, SELL-32-sigma) or MSSTAB_FORMAT_CSR */
   int32_t sell_sigma;      /* SELL sorting window in rows (1 = no sorting, default; else a
                               multiple of 32) */
   int32_t kernel_timing;   /* 1: time every launch with CUDA events (msstab_stats.t_ms) */
   int32_t max_outer;       /* FP32 inner: defect-correction iterations per solve; <= 0: 20 */
-  int32_t reserved[4];
+  int32_t inner_ell;       /* FP32 inner: stabilisation degree of the inner solves (1 <= . <= l);
+                              <= 0: 1.  In FP32 the degree-l polynomial step through the level
+                              vectors A^k r drifts from the true residual for l > 1 on stiff
+                              problems; l = 1 keeps the inner recursive residual honest */
+  int32_t reserved[3];
   void* stream;            /* cudaStream_t for all work of the handle; NULL = default stream */
 } msstab_options;
 

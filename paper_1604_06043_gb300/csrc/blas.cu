@@ -23,6 +23,33 @@ static int max_grid(K kernel, const Ctx& c, int cap_blocks = MAXBLK) {
 
 static inline int clamp_grid(int64_t need, int cap) { return (int)(need < 1 ? 1 : (need < cap ? need : cap)); }
 
+// Per-thread dot-product accumulators: FP64 for FP64 vectors, compensated FP32
+// pairs for FP32 vectors (read out as FP64).
+template <typename T, int N>
+struct Acc;
+
+template <int N>
+struct Acc<double, N> {
+  double v[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) v[i] = 0.0;
+  }
+  __device__ __forceinline__ void add(int i, double x, double y) { v[i] = fma(x, y, v[i]); }
+  __device__ __forceinline__ double get(int i) const { return v[i]; }
+};
+
+template <int N>
+struct Acc<float, N> {
+  float hi[N], lo[N];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < N; ++i) hi[i] = lo[i] = 0.f;
+  }
+  __device__ __forceinline__ void add(int i, float x, float y) { df_add_prod(hi[i], lo[i], x, y); }
+  __device__ __forceinline__ double get(int i) const { return (double)hi[i] + (double)lo[i]; }
+};
+
 // ---------------------------------------------------------------------------
 // gamma step on the top level:  r^(k) -= V^(k) gamma
 // ---------------------------------------------------------------------------
@@ -87,7 +114,7 @@ cudaError_t eta_eager(const Ctx& c, int n, int s, const T* R, T* V, int64_t ld, 
 // updates of level step k on the levels below k, applied once after the q loop
 // ---------------------------------------------------------------------------
 template <typename T, int S>
-__global__ void __launch_bounds__(NT) lazy_kernel(int n, int s, T* R, T* V, T* x, int64_t ld, int k,
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) lazy_kernel(int n, int s, T* R, T* V, T* x, int64_t ld, int k,
                                                   const double* __restrict__ gamma,
                                                   const double* __restrict__ eta, int eta_ld) {
   __shared__ T g[SMAX];
@@ -99,55 +126,67 @@ __global__ void __launch_bounds__(NT) lazy_kernel(int n, int s, T* R, T* V, T* x
   for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
     T above[S];
 #pragma unroll
-    for (int j = 0; j < S; ++j)
-      if (j < s) above[j] = V[((int64_t)(k + 1) * s + j) * ld + row];
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+      above[j] = V[((int64_t)(k + 1) * s + j) * ld + row];
+    }
     T rup = R[(int64_t)k * ld + row];
     for (int i = k - 1; i >= -1; --i) {
       T old[S];
 #pragma unroll
-      for (int j = 0; j < S; ++j)
-        if (j < s) old[j] = V[((int64_t)(i + 1) * s + j) * ld + row];
+      for (int j = 0; j < S; ++j) {
+        if (j >= s) break;
+        old[j] = V[((int64_t)(i + 1) * s + j) * ld + row];
+      }
       // gamma step of this level step, with V^(i) as it was at its start
       if (i >= 0) {
         T ri = R[(int64_t)i * ld + row];
 #pragma unroll
-        for (int j = 0; j < S; ++j)
-          if (j < s) ri -= g[j] * old[j];
+        for (int j = 0; j < S; ++j) {
+          if (j >= s) break;
+          ri -= g[j] * old[j];
+        }
         R[(int64_t)i * ld + row] = ri;
         // eta steps of this level: new columns from r^(i+1), new V^(i+1), old V^(i)
 #pragma unroll
         for (int q = 0; q < S; ++q) {
-          if (q < s) {
-            T v = rup;
+          if (q >= s) break;
+          T v = rup;
 #pragma unroll
-            for (int j = 0; j < S; ++j)
-              if (j < s) v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
-            V[((int64_t)(i + 1) * s + q) * ld + row] = v;
-            old[q] = v;  // later columns q' > q read old[j] only for j >= q' > q
+          for (int j = 0; j < S; ++j) {
+            if (j >= s) break;
+            v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
           }
+          V[((int64_t)(i + 1) * s + q) * ld + row] = v;
+          old[q] = v;  // later columns q' > q read old[j] only for j >= q' > q
         }
         rup = ri;
       } else {
         T xv = x[row];
 #pragma unroll
-        for (int j = 0; j < S; ++j)
-          if (j < s) xv += g[j] * old[j];
+        for (int j = 0; j < S; ++j) {
+          if (j >= s) break;
+          xv += g[j] * old[j];
+        }
         x[row] = xv;
 #pragma unroll
         for (int q = 0; q < S; ++q) {
-          if (q < s) {
-            T v = rup;
+          if (q >= s) break;
+          T v = rup;
 #pragma unroll
-            for (int j = 0; j < S; ++j)
-              if (j < s) v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
-            V[(int64_t)q * ld + row] = v;
-            old[q] = v;
+          for (int j = 0; j < S; ++j) {
+            if (j >= s) break;
+            v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
           }
+          V[(int64_t)q * ld + row] = v;
+          old[q] = v;
         }
       }
 #pragma unroll
-      for (int j = 0; j < S; ++j)
-        if (j < s) above[j] = old[j];
+      for (int j = 0; j < S; ++j) {
+        if (j >= s) break;
+        above[j] = old[j];
+      }
     }
   }
 }
@@ -190,7 +229,7 @@ struct TauArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT) tau_kernel(TauArgs<T> a) {
+__global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
   __shared__ T tau[LMAX];
   __shared__ EpiScratch ew;
   __shared__ double smem_w[NWARP * MAXRED];
@@ -202,25 +241,54 @@ __global__ void __launch_bounds__(NT) tau_kernel(TauArgs<T> a) {
   const int nchunks = gridDim.x / nt;
   if (threadIdx.x < a.ell) tau[threadIdx.x] = (T)(a.do_update ? a.tau[threadIdx.x] : 0.0);
   __syncthreads();
-  double acc[SMAX];
-#pragma unroll
-  for (int i = 0; i < SMAX; ++i) acc[i] = 0.0;
-  double accr = 0.0;
+  Acc<T, SMAX + 1> acc;   // P^T out in slots 0..s-1, out.out in slot SMAX
+  acc.zero();
   const int64_t ld = a.ld;
   const int stride = nchunks * NT;
-  for (int row = chunk * NT + threadIdx.x; row < a.n; row += stride) {
+  // Two rows per iteration; every load of both rows (levels, x, and the P
+  // entries of the projection) is issued before any arithmetic, so that
+  // enough bytes are in flight per SM (this kernel runs 2 blocks per SM).
+  auto load_row = [&](int row, T (&lv)[LMAX + 2], T (&pv)[SMAX], T& xv) {
+    if (a.proj) {
+#pragma unroll
+      for (int c = 0; c < SMAX; ++c) {
+        if (c >= a.s) break;
+        pv[c] = __ldg(a.P + (int64_t)c * a.ldp + row);
+      }
+    }
+    if (t == 0) {
+      lv[0] = a.R[row];                                               // r^(0)
+      if (a.do_update) {
+        xv = a.x[row];
+#pragma unroll
+        for (int i = 1; i <= LMAX; ++i) {
+          if (i > a.ell) break;
+          lv[i] = a.R[(int64_t)i * ld + row];                         // r^(i)
+        }
+      }
+    } else {
+      const int q = t - 1;
+      lv[1] = a.V[((int64_t)a.s + q) * ld + row];                     // v_q^(0)
+      if (a.do_update) {
+        lv[0] = a.V[(int64_t)q * ld + row];                           // v_q^(-1)
+#pragma unroll
+        for (int i = 1; i <= LMAX; ++i) {
+          if (i > a.ell) break;
+          lv[i + 1] = a.V[((int64_t)(i + 1) * a.s + q) * ld + row];   // v_q^(i)
+        }
+      }
+    }
+  };
+  auto update_row = [&](int row, T (&lv)[LMAX + 2], const T (&pv)[SMAX], T xv) {
     T out;
     if (t == 0) {
-      T r = a.R[row];
+      T r = lv[0];
       if (a.do_update) {
-        const T r0 = r;
-        T xv = a.x[row];
-        T prev = r0;  // r^(i-1)
-        for (int i = 1; i <= a.ell; ++i) {
-          const T ri = a.R[(int64_t)i * ld + row];
-          r -= tau[i - 1] * ri;
-          xv += tau[i - 1] * prev;
-          prev = ri;
+#pragma unroll
+        for (int i = 1; i <= LMAX; ++i) {
+          if (i > a.ell) break;
+          r -= tau[i - 1] * lv[i];
+          xv += tau[i - 1] * lv[i - 1];
         }
         a.R[row] = r;
         a.x[row] = xv;
@@ -229,36 +297,51 @@ __global__ void __launch_bounds__(NT) tau_kernel(TauArgs<T> a) {
       out = r;
     } else {
       const int q = t - 1;
-      T v0 = a.V[((int64_t)a.s + q) * ld + row];     // v_q^(0)
       if (a.do_update) {
-        T um = a.V[(int64_t)q * ld + row];           // v_q^(-1)
-        T vnew = v0, unew = um;
-        T prev = v0;                                  // v_q^(i-1)
-        for (int i = 1; i <= a.ell; ++i) {
-          const T vi = a.V[((int64_t)(i + 1) * a.s + q) * ld + row];
-          vnew -= tau[i - 1] * vi;
-          unew -= tau[i - 1] * prev;
-          prev = vi;
+        T vnew = lv[1], unew = lv[0];
+#pragma unroll
+        for (int i = 1; i <= LMAX; ++i) {
+          if (i > a.ell) break;
+          vnew -= tau[i - 1] * lv[i + 1];
+          unew -= tau[i - 1] * lv[i];
         }
         a.V[((int64_t)a.s + q) * ld + row] = vnew;
         a.V[(int64_t)q * ld + row] = unew;
-        v0 = vnew;
+        lv[1] = vnew;
       }
-      out = v0;
+      out = lv[1];
     }
     if (a.proj) {
-      const double od = (double)out;
 #pragma unroll
-      for (int c = 0; c < SMAX; ++c)
-        if (c < a.s) acc[c] = fma(od, (double)__ldg(a.P + (int64_t)c * a.ldp + row), acc[c]);
-      accr = fma(od, od, accr);
+      for (int c = 0; c < SMAX; ++c) {
+        if (c >= a.s) break;
+        acc.add(c, out, pv[c]);
+      }
+      if (t == 0) acc.add(SMAX, out, out);
     }
+  };
+  int row = chunk * NT + threadIdx.x;
+  if constexpr (sizeof(T) == 4) {   // FP64 keeps one row: two would spill registers
+    for (; row + stride < a.n; row += 2 * stride) {
+      T lv0[LMAX + 2], lv1[LMAX + 2], pv0[SMAX], pv1[SMAX];
+      T x0 = T(0), x1 = T(0);
+      load_row(row, lv0, pv0, x0);
+      load_row(row + stride, lv1, pv1, x1);
+      update_row(row, lv0, pv0, x0);
+      update_row(row + stride, lv1, pv1, x1);
+    }
+  }
+  for (; row < a.n; row += stride) {
+    T lv0[LMAX + 2], pv0[SMAX];
+    T x0 = T(0);
+    load_row(row, lv0, pv0, x0);
+    update_row(row, lv0, pv0, x0);
   }
   if (!a.proj) return;
   const int m = a.s + (t == 0 ? 1 : 0);
   double fin[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) fin[i] = i < SMAX && i < a.s ? acc[i < SMAX ? i : 0] : (i == a.s ? accr : 0.0);
+  for (int i = 0; i < 32; ++i) fin[i] = i < SMAX && i < a.s ? acc.get(i < SMAX ? i : 0) : (i == a.s ? acc.get(SMAX) : 0.0);
   block_reduce<32>(fin, m, smem_w, red);
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
   if (!groups_done(a.rs, t, nt, m, red, &s_last)) return;
@@ -307,7 +390,7 @@ struct MdArgs {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(NT) multidot_kernel(MdArgs<T> a) {
+__global__ void __launch_bounds__(NT, 2) multidot_kernel(MdArgs<T> a) {
   __shared__ EpiScratch ew;
   __shared__ double smem_w[NWARP * MAXRED];
   __shared__ double red[MAXRED];
@@ -315,23 +398,30 @@ __global__ void __launch_bounds__(NT) multidot_kernel(MdArgs<T> a) {
   const int t = blockIdx.x % a.nt;
   const int chunk = blockIdx.x / a.nt;
   const int nchunks = gridDim.x / a.nt;
-  double acc[MD_MAXC];
-#pragma unroll
-  for (int i = 0; i < MD_MAXC; ++i) acc[i] = 0.0;
-  double accs = 0.0;
+  Acc<T, MD_MAXC + 1> acc;  // X_t . Y_c in slots 0..ny-1, X_t . X_t in slot MD_MAXC
+  acc.zero();
   const T* xt = a.cols.x[t];
   const int stride = nchunks * NT;
   for (int row = chunk * NT + threadIdx.x; row < a.n; row += stride) {
-    const double xv = (double)__ldg(xt + row);
+    const T xv = __ldg(xt + row);
+    T yv[MD_MAXC];
 #pragma unroll
-    for (int c = 0; c < MD_MAXC; ++c)
-      if (c < a.ny) acc[c] = fma(xv, (double)__ldg(a.cols.y[c] + row), acc[c]);
-    accs = fma(xv, xv, accs);
+    for (int c = 0; c < MD_MAXC; ++c) {
+      if (c >= a.ny) break;
+      yv[c] = __ldg(a.cols.y[c] + row);
+    }
+#pragma unroll
+    for (int c = 0; c < MD_MAXC; ++c) {
+      if (c >= a.ny) break;
+      acc.add(c, xv, yv[c]);
+    }
+    if (a.self) acc.add(MD_MAXC, xv, xv);
   }
   const int m = a.ny + a.self;
   double fin[32];
 #pragma unroll
-  for (int i = 0; i < 32; ++i) fin[i] = i < MD_MAXC && i < a.ny ? acc[i < MD_MAXC ? i : 0] : (i == a.ny ? accs : 0.0);
+  for (int i = 0; i < 32; ++i)
+    fin[i] = i < MD_MAXC && i < a.ny ? acc.get(i < MD_MAXC ? i : 0) : (i == a.ny ? acc.get(MD_MAXC) : 0.0);
   block_reduce<32>(fin, m, smem_w, red);
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
   if (!groups_done(a.rs, t, a.nt, m, red, &s_last)) return;

@@ -83,6 +83,23 @@ struct SellMat {           // SELL-32-sigma: slice k holds rows perm[32k .. 32k+
 };
 
 // ---------------------------------------------------------------------------
+// compensated FP32 accumulation (FP32 vectors): the product is split exactly
+// (FMA gives its rounding error) and summed with TwoSum, so a thread's partial
+// dot product carries about twice the FP32 precision without using the FP64
+// pipe, which on this GPU runs at 1/64 of the FP32 rate.  The rounded-mode
+// intrinsics keep the compiler from contracting the error terms away.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
+  const float p = __fmul_rn(a, b);
+  const float e = __fmaf_rn(a, b, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bp = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+// ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {
@@ -172,9 +189,17 @@ __device__ __forceinline__ bool grid_reduce(RedScratch rs, int grp, int blk, int
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const double* base = rs.partials + (size_t)grp * rs.max_blocks * MAXRED;
   for (int i = w; i < m; i += nw) {
-    double v = 0.0;
-    for (int b = lane; b < nblk; b += 32) v += __ldcg(base + (size_t)b * MAXRED + i);
-    v = warp_sum(v);
+    // four independent partial sums keep four loads in flight per lane
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {
+      v0 += __ldcg(base + (size_t)b * MAXRED + i);
+      v1 += __ldcg(base + (size_t)(b + 32) * MAXRED + i);
+      v2 += __ldcg(base + (size_t)(b + 64) * MAXRED + i);
+      v3 += __ldcg(base + (size_t)(b + 96) * MAXRED + i);
+    }
+    for (; b < nblk; b += 32) v0 += __ldcg(base + (size_t)b * MAXRED + i);
+    double v = warp_sum((v0 + v1) + (v2 + v3));
     if (lane == 0) red[i] = v;
   }
   __syncthreads();

@@ -210,7 +210,6 @@ msstab_status sync_read(msstab_t h, const void* dsrc, size_t bytes) {
 }
 
 Epi epi_none(msstab_t h) { return Epi{EPI_NONE, 0, 0, h->s, h->ell, h->st}; }
-Epi epi_of(msstab_t h, int kind, int k, int q) { return Epi{kind, k, q, h->s, h->ell, h->st}; }
 
 // ---------------------------------------------------------------------------
 // Cholesky QR (twice) of s columns V, applying the same R^-1 to U
@@ -311,12 +310,18 @@ struct SolveCtl {
   bool use_recycle;       // start from the recycle store if it holds data
   bool record_history;
   bool true_check;        // confirm convergence with the true residual b - A x
+  int ell;                // stabilisation degree of this solve (<= the handle's l)
+  bool stop_on_stagnation;  // stop when the residual has not halved in 4 cycles
+  bool continue_basis;    // start from the U, V left in the level slots by the previous solve
 };
 
 template <typename T>
 msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, SolveOut& out) {
   const Ctx c = h->ctx();
-  const int s = h->s, ell = h->ell, n = h->n;
+  const int s = h->s, ell = ctl.ell, n = h->n;
+  auto epi_of = [&](int kind, int k, int q) { return Epi{kind, k, q, s, ell, h->st}; };
+  double best = 1e300;
+  int64_t best_cycle = 0;
   const int64_t ld = w.ld;
   DevState* st = h->st;
   const T* P = w.P;
@@ -348,7 +353,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     h->hist.push_back(std::sqrt(rr) / nb);
     h->hist_mvs.push_back(out.mvs);
   }
-  bool r_is_true = true, have_basis = false, need_proj = true;
+  bool r_is_true = true, have_basis = ctl.continue_basis, need_proj = true;
   const int64_t cyc_mvs = (int64_t)ell * (s + 1);
   for (;;) {
     const double nr = std::sqrt(rr);
@@ -399,18 +404,18 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     }
     if (need_proj) {
       LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, nullptr, ld, nullptr, P, ld, 0, 1, st,
-                                         epi_of(h, EPI_GAMMA, 0, 0)));
+                                         epi_of(EPI_GAMMA, 0, 0)));
       need_proj = false;
     }
     // ---- one cycle: level steps k = 0..l-1 ----
     for (int k = 0; k < ell; ++k) {
       LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
       LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
-                                        &st->projR[(k + 1) * SMAX], epi_of(h, EPI_ETA, k, 0)));
+                                        &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0)));
       for (int q = 0; q < s; ++q) {
         LAUNCH(MSSTAB_K_ETA, eta_eager<T>(c, n, s, w.R, w.V, ld, k, q, &st->eta[(k * SMAX + q) * SMAX]));
-        Epi next = q + 1 < s ? epi_of(h, EPI_ETA, k, q + 1)
-                             : (k + 1 < ell ? epi_of(h, EPI_GAMMA, k + 1, 0) : epi_none(h));
+        Epi next = q + 1 < s ? epi_of(EPI_ETA, k, q + 1)
+                             : (k + 1 < ell ? epi_of(EPI_GAMMA, k + 1, 0) : epi_none(h));
         LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
                                           &st->projV[((k + 1) * SMAX + q) * SMAX], next));
       }
@@ -422,10 +427,10 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
       MdCols<T> cols{};
       for (int i = 0; i <= ell; ++i) cols.x[i] = cols.y[i] = Rk(i);
       LAUNCH(MSSTAB_K_TAU, multidot<T>(c, n, cols, ell + 1, ell + 1, 0, st->gram, ell + 1,
-                                       epi_of(h, EPI_TAU, 0, 0)));
+                                       epi_of(EPI_TAU, 0, 0)));
     }
     LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
-                                       epi_of(h, EPI_GAMMA, 0, 0)));
+                                       epi_of(EPI_GAMMA, 0, 0)));
     out.mvs += cyc_mvs;
     if (prec) h->mvs32 += cyc_mvs;
     out.cycles += 1;
@@ -451,6 +456,14 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     std::swap(w.XB, w.XB2);
     r_is_true = false;
     out.relres_rec = relres;
+    if (ctl.stop_on_stagnation) {
+      if (relres < 0.5 * best) {
+        best = relres;
+        best_cycle = out.cycles;
+      } else if (out.cycles - best_cycle >= 4) {
+        break;  // the FP32 floor is reached: the outer FP64 loop takes over
+      }
+    }
     if (ctl.want_fetch && !out.fetched &&
         ((ctl.fetch_cycle > 0 && out.cycles == ctl.fetch_cycle) ||
          (ctl.fetch_cycle <= 0 && relres <= ctl.fetch_threshold))) {
@@ -512,6 +525,9 @@ SolveCtl make_ctl(msstab_t h, double tol, bool first_has_rec) {
   ctl.fetch_cycle = h->opt.fetch_cycle;
   ctl.record_history = true;
   ctl.true_check = true;
+  ctl.ell = h->ell;
+  ctl.stop_on_stagnation = false;
+  ctl.continue_basis = false;
   return ctl;
 }
 
@@ -535,6 +551,7 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
   const int max_outer = h->opt.max_outer > 0 ? h->opt.max_outer : 20;
   int64_t outer = 0;
   double nb = -1.0;
+  bool cont = false;   // continue the inner basis (U, V) of the previous outer iteration
   o.status = MSSTAB_OK;
   for (;;) {
     // FP64 true residual
@@ -568,7 +585,7 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     CK(cudaMemsetAsync(v.X, 0, sizeof(float) * n, h->stream));
     // the FP32 true residual cannot go much below kappa * eps_32, so the inner
     // solves stop on their recursive residual; the FP64 loop checks the truth
-    const double itol = h->opt.inner_tol > 0 ? h->opt.inner_tol : std::max(1e-4, 0.5 * tol * nb / sigma);
+    const double itol = h->opt.inner_tol > 0 ? h->opt.inner_tol : std::max(1e-5, 0.5 * tol * nb / sigma);
     SolveCtl ctl{};
     ctl.tol = itol;
     ctl.max_mvs = default_max_mvs(h);
@@ -578,8 +595,14 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     ctl.fetch_cycle = h->opt.fetch_cycle;
     ctl.record_history = false;
     ctl.true_check = false;
+    ctl.ell = std::min(h->ell, h->opt.inner_ell > 0 ? h->opt.inner_ell : 1);
+    ctl.stop_on_stagnation = true;
+    ctl.continue_basis = cont;
     SolveOut io;
     CKS(idrstab<float>(h, v, 1, ctl, io));
+    // the next outer iteration hands this solve's final U, V on (as M(s)stab
+    // does between systems) instead of restarting from the recycle store
+    cont = (io.status == MSSTAB_OK || io.status == MSSTAB_ERR_MAXIT) && io.cycles > 0;
     CKS(chain_recycle<float>(h, v, 1, io));
     o.mvs += io.mvs;
     o.cycles += io.cycles;
@@ -682,6 +705,7 @@ void msstab_default_options(msstab_options* opt) {
   opt->sell_sigma = 1;
   opt->kernel_timing = 0;
   opt->max_outer = 0;
+  opt->inner_ell = 0;
   opt->stream = nullptr;
 }
 

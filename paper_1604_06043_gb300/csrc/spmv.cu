@@ -42,27 +42,48 @@ struct SpmvArgs {
 __host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : (v <= 2 ? 2 : (v <= 4 ? 4 : (v <= 8 ? 8 : (v <= 16 ? 16 : 32)))); }
 
 // Per-thread accumulators of the fused dot products: NP slots for P^T y (np <=
-// NP used), then y.y and b.b in fixed slots.
+// NP used), then y.y and b.b in fixed slots.  FP64 vectors accumulate in FP64;
+// FP32 vectors in compensated FP32 pairs (df_add_prod), read out as FP64.
+template <typename T, int NP>
+struct DotAcc;
+
 template <int NP>
-struct DotAcc {
+struct DotAcc<double, NP> {
   double v[NP + 2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NP + 2; ++i) v[i] = 0.0;
+  }
+  __device__ __forceinline__ void add(int i, double x, double y) { v[i] = fma(x, y, v[i]); }
+  __device__ __forceinline__ double get(int i) const { return v[i]; }
+};
+
+template <int NP>
+struct DotAcc<float, NP> {
+  float hi[NP + 2], lo[NP + 2];
+  __device__ __forceinline__ void zero() {
+#pragma unroll
+    for (int i = 0; i < NP + 2; ++i) hi[i] = lo[i] = 0.f;
+  }
+  __device__ __forceinline__ void add(int i, float x, float y) { df_add_prod(hi[i], lo[i], x, y); }
+  __device__ __forceinline__ double get(int i) const { return (double)hi[i] + (double)lo[i]; }
 };
 
 template <typename T, int NP>
-__device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc<NP>& acc) {
-  const double yd = (double)yv;
+__device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc<T, NP>& acc) {
+  // NP is the compile-time slot count chosen for np (np == NP in the cycle)
 #pragma unroll
   for (int c = 0; c < NP; ++c)
-    if (c < a.np) acc.v[c] = fma(yd, (double)ro(a.P + (int64_t)c * a.ldp + row), acc.v[c]);
-  if (a.self) acc.v[NP] = fma(yd, yd, acc.v[NP]);
+    if (c < a.np) acc.add(c, yv, ro(a.P + (int64_t)c * a.ldp + row));
+  if (a.self) acc.add(NP, yv, yv);
   if (a.bdot) {
-    const double bd = (double)a.b[row];
-    acc.v[NP + 1] = fma(bd, bd, acc.v[NP + 1]);
+    const T bd = a.b[row];
+    acc.add(NP + 1, bd, bd);
   }
 }
 
 template <typename T, int NP>
-__device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<NP>& acc) {
+__device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<T, NP>& acc) {
   constexpr int M = pow2_at_least(NP + 2);
   __shared__ double smem_w[NWARP * MAXRED];
   __shared__ double red[MAXRED];
@@ -74,9 +95,9 @@ __device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<NP>& a
 #pragma unroll
   for (int i = 0; i < M; ++i) {
     double v = 0.0;
-    if (i < NP && i < a.np) v = acc.v[i < NP ? i : 0];
-    if (a.self && i == a.np) v = acc.v[NP];
-    if (a.bdot && i == a.np + a.self) v = acc.v[NP + 1];
+    if (i < NP && i < a.np) v = acc.get(i < NP ? i : 0);
+    if (a.self && i == a.np) v = acc.get(NP);
+    if (a.bdot && i == a.np + a.self) v = acc.get(NP + 1);
     fin[i] = v;
   }
   block_reduce<M>(fin, m, smem_w, red);
@@ -130,9 +151,8 @@ __device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __re
 template <typename T, int NP>
 __global__ void __launch_bounds__(NT, 4) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
   constexpr int NA = NP < 0 ? 0 : NP;
-  DotAcc<NA> acc;
-#pragma unroll
-  for (int i = 0; i < NA + 2; ++i) acc.v[i] = 0.0;
+  DotAcc<T, NA> acc;
+  acc.zero();
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * NWARP;
   for (int sl = (blockIdx.x * NT + threadIdx.x) >> 5; sl < A.nslices; sl += nwarps) {
@@ -153,9 +173,8 @@ __global__ void __launch_bounds__(NT, 4) spmv_sell_kernel(SellMat<T> A, SpmvArgs
 template <typename T, int NP>
 __global__ void __launch_bounds__(NT, 4) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a) {
   constexpr int NA = NP < 0 ? 0 : NP;
-  DotAcc<NA> acc;
-#pragma unroll
-  for (int i = 0; i < NA + 2; ++i) acc.v[i] = 0.0;
+  DotAcc<T, NA> acc;
+  acc.zero();
   const int stride = gridDim.x * NT;
   for (int row = blockIdx.x * NT + threadIdx.x; row < A.n; row += stride) {
     const int beg = ro(A.row_ptr + row), end = ro(A.row_ptr + row + 1);

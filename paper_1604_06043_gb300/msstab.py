@@ -38,7 +38,8 @@ class Options(ctypes.Structure):
         ("sell_sigma", ctypes.c_int32),
         ("kernel_timing", ctypes.c_int32),
         ("max_outer", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 4),
+        ("inner_ell", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
         ("stream", ctypes.c_void_p),
     ]
 
