@@ -144,17 +144,21 @@ def sell_entries(A):
     return int(lens.max(axis=1).sum() * 32), lens.shape[0]
 
 
-def family_model(A, s, ell, cycles, solves, vb=8):
+def family_model(A, s, ell, cycles, solves, replaced=0, vb=8):
     """Algorithmic bytes and FP64 flops of the launches of one timed region.
 
     Every operand is counted once per launch: the matrix arrays, x read once,
-    y written once, each vector column read or written once."""
+    y written once, each vector column read or written once.  ``replaced``
+    true residuals r = b - A x at cycle ends are fused SpMV + P dots that also
+    read b."""
     n = A.n
     nnz_sell, nsl = sell_entries(A)
     v = vb * n
     spmv = nnz_sell * (4 + vb) + 8 * nsl + 2 * v
     m = {}
-    m["spmv_dot"] = dict(launches=cycles * ell * (s + 1), bytes=spmv + s * v, flops=2 * (A.nnz + s * n))
+    nd = cycles * ell * (s + 1)
+    m["spmv_dot"] = dict(launches=nd + replaced, bytes=spmv + s * v + v * replaced / max(1, nd + replaced),
+                         flops=2 * (A.nnz + s * n) + 2 * n * replaced / max(1, nd + replaced))
     m["eta"] = dict(launches=cycles * ell * s, bytes=(s + 2) * v, flops=2 * s * n)
     m["gamma"] = dict(launches=cycles * ell, bytes=(s + 2) * v, flops=2 * s * n)
     lazy_b = sum((s + 1) + (k + 1) * (2 * s + 2) for k in range(ell)) * v
@@ -186,6 +190,12 @@ def golden_cycles(first, count):
     if not sy:
         return None
     return (statistics.mean(x["cycles"] for x in sy), statistics.mean(x["mvs"] for x in sy), len(sy))
+
+
+def extra_mvs(w, cyc):
+    """Products with A per system outside the level steps: r0 = b - A x0, and
+    the true residuals (one per replace_every cycles, else one to confirm)."""
+    return 1 + (cyc / w.replace_every if w.replace_every > 0 else 1)
 
 
 def cpu_worker(args):
@@ -256,10 +266,11 @@ def reference_arm(args):
     timed = res["level_step_s"][args.warmup:]
     g = golden_cycles(args.warmup + 1, args.steps)
     cyc = g[0] if g else float("nan")
-    ms = statistics.mean(timed) * 1e3 * w.ell * cyc + 2 * res["mv_s"] * 1e3
+    em = extra_mvs(w, cyc)
+    ms = statistics.mean(timed) * 1e3 * w.ell * cyc + em * res["mv_s"] * 1e3
     sample = (f"{len(timed)} level steps of Algorithm 1 (s={w.s}, l={w.ell}) of the FP64 oracle on system 1 of "
               f"the 128^3 sequence, scaled by {cyc:.2f} cycles/system (oracle record, systems "
-              f"{args.warmup + 1}..{args.warmup + args.steps}) + 2 MVs")
+              f"{args.warmup + 1}..{args.warmup + args.steps}) + {em:.2f} MVs (r0 and true residuals)")
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(timed) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
@@ -273,6 +284,91 @@ def reference_arm(args):
 # ---------------------------------------------------------------------------
 # the GPU arm
 # ---------------------------------------------------------------------------
+
+def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300, batch=8, lr=2e-3):
+    """The learned initial guess: the plain FP64 solver produces the pairs of
+    systems 1..train_steps, the CNN is trained on them with the library's own
+    kernels, and systems train_steps+1..train_steps+K are solved (a) with the
+    guess under the keep-if-smaller-residual rule, (b) with the optimally
+    scaled guess, (c) as (a) on the FP32-inner solver, each against the plain
+    solver on the same systems."""
+    from paper_1604_06043_gb300 import problems as pb
+    import numpy as np
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
+    x = torch.tensor(w.x0(), device=dev)
+    b = torch.empty_like(x)
+    r0 = torch.empty_like(x)
+    nrm = torch.zeros(2, dtype=torch.float64, device=dev)
+    D = min(32, w.shape[0])
+    net = M.CNN(w.shape, pb.cnn_init_params(), max_pairs=train_steps, max_batch=batch, crop=D, device=dev)
+    for _ in range(train_steps):
+        S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
+        xp = x.clone()
+        S.op_residual(b, x, r0, nrm)
+        S.solve(b, x, w.tol)
+        net.add_pair(r0, xp, x)
+    net.fit_scales()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = net.train(pb.cnn_crop_batches(train_steps, w.shape, D, batch, iters), batch, D, lr)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    x_start = x.clone()
+    S.close()
+    out = {"train": {"pairs": train_steps, "iters": iters, "batch": batch, "crop": D, "seconds": round(train_s, 3),
+                     "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:]))},
+           "systems": f"{train_steps + 1}..{train_steps + K}"}
+
+    def run(precision, mode):
+        V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, precision=precision, replace_every=w.replace_every)
+        xs = torch.tensor(w.x0(), device=dev)
+        for _ in range(train_steps):             # the same history (and recycle store) as the plain run
+            V.op_axpby(1.0 / w.tau, xs, 1.0, f, b)
+            V.solve(b, xs, w.tol)
+        xg = torch.empty_like(xs)
+        delta = torch.empty_like(xs)
+        mv, used, red = [], 0, []
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(K):
+            V.op_axpby(1.0 / w.tau, xs, 1.0, f, b)
+            extra = 0
+            if mode != "plain":
+                V.op_residual(b, xs, r0, nrm)
+                net.infer(r0, xs, delta)
+                if mode == "rule":
+                    u = V.select_guess(b, xs, delta, xg)
+                else:
+                    u, a, rr = V.select_guess_scaled(b, xs, delta, xg)
+                    red.append(rr)
+                used += int(u)
+                xs.copy_(xg)
+                extra = 3
+            st = V.solve(b, xs, w.tol)
+            mv.append(st.mvs + extra)
+        e1.record()
+        torch.cuda.synchronize()
+        V.close()
+        d = {"ms_per_system": round(e0.elapsed_time(e1) / K, 3), "mvs_per_system": round(float(np.mean(mv)), 2)}
+        if mode != "plain":
+            d["guess_kept"] = used
+            d["fallback_rate"] = round(1.0 - used / K, 3)
+        if red:
+            d["residual_reduction_mean"] = round(float(np.mean(red)), 4)
+        return d
+
+    plain = run(M.PREC_FP64, "plain")
+    out["fp64_plain"] = plain
+    out["fp64_guess_rule"] = run(M.PREC_FP64, "rule")
+    out["fp64_guess_scaled"] = run(M.PREC_FP64, "scaled")
+    out["fp32_inner_guess_rule"] = run(M.PREC_FP32_INNER, "rule")
+    for k in ("fp64_guess_rule", "fp64_guess_scaled", "fp32_inner_guess_rule"):
+        out[k]["mvs_saved_per_system"] = round(plain["mvs_per_system"] - out[k]["mvs_per_system"], 2)
+    net.close()
+    return out
+
 
 def run_sequence(M, torch, S, f, x, b, tau, tol, count, collect=None):
     out = []
@@ -315,7 +411,7 @@ def main(argv=None):
     f_np, x0_np = w.f(), w.x0()
     K, W = args.steps, args.warmup
 
-    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, kernel_timing=1)
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, kernel_timing=1, replace_every=w.replace_every)
     stream = torch.cuda.current_stream()
     f = torch.tensor(f_np, device=dev)
     x = torch.tensor(x0_np, device=dev)
@@ -349,7 +445,9 @@ def main(argv=None):
     fam_ms = {f_: sum(t["t_ms"][f_] for t in timed) for f_ in FAMILIES}
     fam_n = {f_: sum(t["n_launch"][f_] for t in timed) for f_ in FAMILIES}
     launches = sum(t["launches"] for t in timed) + K          # + the right-hand-side launches
-    model, spmv_b = family_model(A, w.s, w.ell, cycles, K)
+    replaced = sum(t["cycles"] for t in timed) if w.replace_every == 1 else \
+        sum(t["cycles"] // w.replace_every for t in timed) if w.replace_every > 1 else 0
+    model, spmv_b = family_model(A, w.s, w.ell, cycles, K, replaced)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -402,7 +500,7 @@ def main(argv=None):
     # end to end through the public API with host buffers, on the same systems:
     # a fresh handle, the same warm-up, then the same K systems via msstab_solve_host
     if not args.no_e2e:
-        H = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev)
+        H = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
         xh = x0_np.copy()
         for _ in range(W):
             H.solve_host(xh / w.tau + f_np, xh, w.tol)
@@ -426,7 +524,7 @@ def main(argv=None):
         for name, opts in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER)),
                            ("msstab_fp32_inner", dict(precision=M.PREC_FP32_INNER))):
           try:
-            V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, **opts)
+            V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every, **opts)
             xv = torch.tensor(x0_np, device=dev)
             run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W)
             torch.cuda.synchronize()
@@ -449,7 +547,7 @@ def main(argv=None):
           except Exception as e:  # a failing variant is reported, the main line still stands
             variants[name] = {"error": str(e)[-300:]}
         # error of the FP32-inner solutions against the FP64 solutions of the same systems
-        P64 = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev)
+        P64 = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
         x64 = torch.tensor(x0_np, device=dev)
         run_sequence(M, torch, P64, f, x64, b, w.tau, w.tol, W)
         errs = []
@@ -460,17 +558,22 @@ def main(argv=None):
         P64.close()
         if errs:
             variants["msstab_fp32_inner"]["rel_err_vs_fp64_max"] = max(errs)
+        try:
+            variants["learned_guess"] = learned_guess_variants(M, torch, A, w, K, dev, f)
+        except Exception as e:
+            variants["learned_guess"] = {"error": str(e)[-300:]}
         line["variants"] = variants
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         try:
             res = run_cpu_sample(args, 4)
             cyc = cycles / K
-            ms = statistics.mean(res["level_step_s"]) * 1e3 * w.ell * cyc + 2 * res["mv_s"] * 1e3
+            em = extra_mvs(w, cyc)
+            ms = statistics.mean(res["level_step_s"]) * 1e3 * w.ell * cyc + em * res["mv_s"] * 1e3
             line["cpu_baseline"] = {"value": round(ms, 1), "unit": UNIT, "cores": res["threads"], "kind": "oracle",
                                     "sample": f"one cycle (4 level steps, 36 MVs) of Algorithm 1 of the FP64 oracle on "
                                               f"system 1 of the 128^3 sequence, scaled by the timed run's "
-                                              f"{cyc:.2f} cycles/system, + 2 MVs"}
+                                              f"{cyc:.2f} cycles/system, + {em:.2f} MVs (r0 and true residuals)"}
         except Exception as e:  # the baseline is reported, not required
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {str(e)[-200:]}"}

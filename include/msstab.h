@@ -88,7 +88,13 @@ typedef struct msstab_options {
                               <= 0: 1.  In FP32 the degree-l polynomial step through the level
                               vectors A^k r drifts from the true residual for l > 1 on stiff
                               problems; l = 1 keeps the inner recursive residual honest */
-  int32_t reserved[3];
+  int32_t replace_every;   /* > 0: replace the recursive residual by the true residual b - A x at
+                              the end of every replace_every-th cycle (one product with A, fused
+                              with the projections the next cycle needs), as the preconditioned
+                              experiment of Section 6 does after each cycle; bounds the gap that
+                              the drift of V from A U opens between the two.  0 (default):
+                              Algorithm 1 as printed, true residual only to confirm convergence */
+  int32_t reserved[2];
   void* stream;            /* cudaStream_t for all work of the handle; NULL = default stream */
 } msstab_options;
 
@@ -177,6 +183,15 @@ msstab_status msstab_import_recycle(msstab_t h, const double* d_U, const double*
 msstab_status msstab_select_guess(msstab_t h, const double* d_b, const double* d_xprev,
                                   const double* d_delta, double* d_x, int32_t* used);
 
+/* The same with the correction scaled optimally: d_x = d_xprev + alpha d_delta
+ * with alpha = (r0 . A delta) / ||A delta||^2 minimising ||b - A x|| (r0 =
+ * b - A x_prev; two products with A), which never increases the residual;
+ * falls back to d_xprev (used = 0) if alpha is 0 or not finite.  *alpha and
+ * *reduction (= ||b - A x|| / ||r0||) may be NULL. */
+msstab_status msstab_select_guess_scaled(msstab_t h, const double* d_b, const double* d_xprev,
+                                         const double* d_delta, double* d_x, int32_t* used, double* alpha,
+                                         double* reduction);
+
 /* ---------------------------------------------------------------------------
  * Kernel-level entry points on a handle (for testing and measuring single
  * kernels).  prec selects FP64 (0: double vectors, the matrix A) or FP32 (1:
@@ -249,6 +264,75 @@ msstab_status msstab_op_small_solve(msstab_t h, int32_t n, const double* d_M, co
  * equations of min ||r^(0) - Z tau||, diagonally scaled, by Cholesky (LU if
  * that fails); tau = 0 if a level vector is zero. */
 msstab_status msstab_op_tau_solve(msstab_t h, int32_t ell, const double* d_gram, double* d_tau);
+
+/* ---------------------------------------------------------------------------
+ * Learned initial guess (not in the paper; the workload's learned-x0 form).
+ * A 3D CNN -- 3x3x3 convolutions 2 -> 16 -> 16 -> 16 -> 1, zero "same"
+ * padding, bias, GELU (erf form) after the first three -- maps the normalised
+ * pair (b^(i+1), x^(i)), fed as the channels (r0, x^(i)) with r0 = b^(i+1) -
+ * A x^(i) (FP64, from msstab_op_residual), to the normalised x^(i+1) - x^(i).
+ * The residual channel carries the information of b in a form that survives
+ * bfloat16: tau b and x^(i) differ by tau f (about 0.5% of x for implicit
+ * Euler, below bfloat16's resolution), and A x^(i) for smooth x^(i) is a
+ * cancellation of terms 1e3-1e5 times larger than the result.  Weights, biases and
+ * all convolution operands are bfloat16, sums FP32, master weights and Adam
+ * state FP32.  Parameters: one flat FP32 vector of msstab_cnn_num_params()
+ * entries, per layer W[c_out][c_in][3][3][3] then b[c_out]; tap (dz, dy, dx)
+ * multiplies the input at offset (dz-1, dy-1, dx-1).  Volumes are
+ * [batch][channel][z][y][x], x fastest, like the solver's vectors.
+ * ------------------------------------------------------------------------- */
+typedef struct msstab_cnn_s* msstab_cnn_t;
+
+int32_t msstab_cnn_num_params(void);
+
+/* A network for an nx x ny x nz grid (x fastest), with initial parameters
+ * d_params (FP32, copied), room for max_pairs training pairs and for training
+ * batches of up to max_batch crops of edge up to crop.  stream: cudaStream_t. */
+msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float* d_params, int32_t max_pairs,
+                                int32_t max_batch, int32_t crop, void* stream, msstab_cnn_t* out);
+msstab_status msstab_cnn_destroy(msstab_cnn_t h);
+const char* msstab_cnn_last_error(msstab_cnn_t h);
+msstab_status msstab_cnn_get_params(msstab_cnn_t h, float* d_params);
+msstab_status msstab_cnn_set_params(msstab_cnn_t h, const float* d_params);
+
+/* Normalisation.  The map r0 -> x^(i+1) - x^(i) is linear in r0, so each
+ * instance is presented at unit residual scale: network input (s_r r0, s_x
+ * x^(i)) and target c s_r (x^(i+1) - x^(i)), with s_r = 1/RMS(r0) of that
+ * instance (computed in every add_pair and infer), s_x and c global.
+ * msstab_cnn_fit_scales sets s_x = 1/RMS(x^(i)) and c = 1/RMS(s_r delta) over
+ * the stored pairs; get/set exchange (s_x, c). */
+msstab_status msstab_cnn_set_scales(msstab_cnn_t h, float s_x, float c);
+msstab_status msstab_cnn_get_scales(msstab_cnn_t h, float* scales2);
+msstab_status msstab_cnn_fit_scales(msstab_cnn_t h);
+
+/* Store a training pair: r0 = b^(i+1) - A x^(i) and x^(i) -> x^(i+1) - x^(i)
+ * (FP64 device vectors of the grid). */
+msstab_status msstab_cnn_add_pair(msstab_cnn_t h, const double* d_r0, const double* d_x_prev,
+                                  const double* d_x_next);
+
+/* iters Adam steps (lr; beta 0.9, 0.999; eps 1e-8) on the mean squared error
+ * over batches of B crops of edge D cut from the stored pairs; h_origins holds
+ * iters x B x 4 int32 (pair index, z0, y0, x0) per crop.  loss_history (host,
+ * iters entries) may be NULL. */
+msstab_status msstab_cnn_train(msstab_cnn_t h, int32_t iters, int32_t B, int32_t D, const int32_t* h_origins,
+                               float lr, float* loss_history);
+
+/* Network output for B normalised input crops d_in [B][2][D^3] (FP32; rounded
+ * to bfloat16 inside) into d_out [B][D^3] (FP32). */
+msstab_status msstab_cnn_forward(msstab_cnn_t h, const float* d_in, int32_t B, int32_t D, float* d_out);
+
+/* Gradient (FP32, d_grad[num_params]) and value (*loss, host) of the mean
+ * squared error of the output for d_in against d_target [B][D^3]; no update. */
+msstab_status msstab_cnn_grad(msstab_cnn_t h, const float* d_in, const float* d_target, int32_t B, int32_t D,
+                              float* d_grad, double* loss);
+
+/* One Adam step with the given gradient. */
+msstab_status msstab_cnn_adam_step(msstab_cnn_t h, const float* d_grad, float lr);
+
+/* d_delta = the network's x^(i+1) - x^(i) for the whole grid from r0 = b^(i+1)
+ * - A x^(i) and x^(i) (FP64 vectors; asynchronous on the handle's stream).
+ * Use with msstab_select_guess / msstab_select_guess_scaled. */
+msstab_status msstab_cnn_infer(msstab_cnn_t h, const double* d_r0, const double* d_x_prev, double* d_delta);
 
 /* ---------------------------------------------------------------------------
  * Allocation-free entry point (the paper has no counterpart: it is a service

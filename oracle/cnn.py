@@ -3,9 +3,9 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).  The network is not part
 of the paper; it is the workload's learned-x0 form: four 3x3x3 convolutions
 2 -> 16 -> 16 -> 16 -> 1 with "same" zero padding and bias, the erf form of
-GELU after the first three, mapping the normalised (tau b^(i+1), x^(i)) to the
-normalised x^(i+1) - x^(i).  Training minimises the mean squared error with
-Adam.
+GELU after the first three, mapping the normalised input channels
+(r0, x^(i)), r0 = b^(i+1) - A x^(i), to the normalised x^(i+1) - x^(i).
+Training minimises the mean squared error with Adam.
 
 Arrays are channels-first, (C, Z, Y, X) for one volume and (B, C, Z, Y, X)
 for a batch; x is the fastest axis, as in the solver's vectors.  Weights are

@@ -312,8 +312,8 @@ class SolveResult:
 
 
 def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
-            fetch_threshold=None, fetch_cycle=None, fetch_refresh=False, inspect: Optional[Callable] = None,
-            mv: Optional[MatVec] = None) -> SolveResult:
+            fetch_threshold=None, fetch_cycle=None, fetch_refresh=False,
+            replace_every=0, inspect: Optional[Callable] = None, mv: Optional[MatVec] = None) -> SolveResult:
     """IDR(s)stab(l), Algorithm 1, with inputs A, b, x, s, l, P, U, V.
 
     Precondition V = A U, dim P = s (P orthonormal, (s, N) layout).  With
@@ -327,6 +327,10 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
     ``fetch_refresh`` the written V is recomputed as A U (s counted MVs): the
     recursions keep V = A U only up to a drift (about 1e-6 relative here), and
     Algorithm 1 requires V = A U of its inputs.
+    ``replace_every`` > 0 replaces the recursive residual by b - A x (one
+    counted MV) at the end of every replace_every-th cycle, as the
+    preconditioned experiment of Section 6 does after each cycle; the stopping
+    test then needs no confirming product.
     ``inspect(stage, state)`` is called after the level loop ("levels") and at
     each cycle end ("cycle") for the invariant tests."""
     mv = mv or MatVec(A)
@@ -401,6 +405,9 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
         r_is_true = False
         j += ell
         cycles += 1
+        if replace_every and cycles % replace_every == 0:
+            r = b - mv(x)
+            r_is_true = True
         relres = float(np.linalg.norm(r)) / nb
         history.append(relres)
         mv_history.append(mv.count - m0)
@@ -439,7 +446,7 @@ class SequenceResult:
 
 def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="once",
                     fetch_threshold=None, orth_recycle=True, first_step=0,
-                    max_mvs=None, on_solve: Optional[Callable] = None) -> SequenceResult:
+                    max_mvs=None, replace_every=0, on_solve: Optional[Callable] = None) -> SequenceResult:
     """Solve the implicit-Euler sequence A x^(i+1) = x^(i)/tau_t + f, one system
     after the other, from x^(0).
 
@@ -469,7 +476,8 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
             U, V = rec
         want_fetch = policy == "once" and rec is None
         res = idrstab(mv.A, b, x, s, ell, P, U, V, tol, max_mvs=max_mvs,
-                      fetch_threshold=thr if want_fetch else None, fetch_refresh=orth_recycle, mv=mv)
+                      fetch_threshold=thr if want_fetch else None, fetch_refresh=orth_recycle,
+                      replace_every=replace_every, mv=mv)
         if want_fetch and res.fetched is not None:
             rec = _orth_or_none(res.fetched) if orth_recycle else res.fetched
         elif policy == "every" and res.U is not None and res.cycles > 0 and res.status == OK:

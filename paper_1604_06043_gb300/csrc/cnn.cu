@@ -1,0 +1,770 @@
+// Learned initial guess: a small 3D CNN trained on the solver's own
+// (b^(i+1), x^(i)) -> x^(i+1) - x^(i) pairs (fed as the channels
+// r0 = b^(i+1) - A x^(i) and x^(i)), with hand-written bfloat16 kernels
+// that accumulate in FP32.  Not part of the paper: the workload's learned-x0
+// form.  The network: 3x3x3 convolutions 2 -> 16 -> 16 -> 16 -> 1, "same"
+// zero padding, bias, GELU (erf form) after the first three layers.
+//
+// Precision: weights, biases and every convolution operand (input volumes,
+// hidden activations, gradients fed to the next contraction) are rounded to
+// bfloat16 (round to nearest even); products are accumulated in FP32; the FP32
+// master weights, Adam moments, pre-activations and the network output stay
+// FP32.  Volumes are [batch][channel][z][y][x] with x fastest, as the solver's
+// vectors.  Weight tap (dz, dy, dx) multiplies the input voxel at offset
+// (dz-1, dy-1, dx-1) (cross-correlation).
+//
+// All reductions (weight gradients, loss, normalisation) are deterministic:
+// per-block partials summed in block order.
+
+#include <cuda_bf16.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "launch.h"
+#include "msstab.h"
+
+namespace mcnn {
+
+constexpr int NL = 4;
+constexpr int CI_[NL] = {2, 16, 16, 16};
+constexpr int CO_[NL] = {16, 16, 16, 1};
+constexpr int TX = 8, TY = 8, TZ = 4, TV = TX * TY * TZ;   // output tile, one voxel per thread
+constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HV = HX * HY * HZ;
+
+__host__ __device__ constexpr int n_params() {
+  return 2 * 16 * 27 + 16 + 16 * 16 * 27 + 16 + 16 * 16 * 27 + 16 + 16 * 1 * 27 + 1;
+}
+inline int w_offset(int l) {
+  int o = 0;
+  for (int i = 0; i < l; ++i) o += CO_[i] * CI_[i] * 27 + CO_[i];
+  return o;
+}
+
+enum Mode { FWD_HIDDEN = 0, FWD_LAST = 1, BWD_DATA = 2, INFER_HIDDEN = 3 };
+
+__device__ __forceinline__ float gelu(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
+__device__ __forceinline__ float gelu_grad(float z) {
+  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
+}
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+
+struct Dims {
+  int X, Y, Z;
+  __host__ __device__ int64_t vol() const { return (int64_t)X * Y * Z; }
+};
+
+// ---------------------------------------------------------------------------
+// 3x3x3 convolution of a CI-channel bf16 volume to CO channels, FP32 sums.
+// w: [CO][CI][27] bf16, bias: CO floats (bf16 values) or NULL.
+// MODE FWD_HIDDEN: z (FP32) and act = bf16(gelu(z)); FWD_LAST: z only;
+// INFER_HIDDEN: act only; BWD_DATA: act = bf16(sum * gelu'(zaux)) (the
+// gradient of the previous layer's pre-activation; w holds that layer's
+// weights transposed and flipped).
+// ---------------------------------------------------------------------------
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(TV) conv_kernel(const __nv_bfloat16* __restrict__ in, Dims d,
+                                                  const __nv_bfloat16* __restrict__ w,
+                                                  const float* __restrict__ bias, float* __restrict__ z,
+                                                  __nv_bfloat16* __restrict__ act,
+                                                  const float* __restrict__ zaux) {
+  extern __shared__ float smem[];
+  float* in_s = smem;                 // [CI][HV]
+  float* w_s = smem + CI * HV;        // [CI][27][CO]
+  const int tilesx = (d.X + TX - 1) / TX, tilesy = (d.Y + TY - 1) / TY;
+  const int tz0 = (blockIdx.x / (tilesx * tilesy)) * TZ;
+  const int ty0 = ((blockIdx.x / tilesx) % tilesy) * TY;
+  const int tx0 = (blockIdx.x % tilesx) * TX;
+  const int b = blockIdx.y;
+  const int64_t vol = d.vol();
+  const __nv_bfloat16* inb = in + (int64_t)b * CI * vol;
+  for (int i = threadIdx.x; i < CI * HV; i += TV) {
+    const int c = i / HV, h = i % HV;
+    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+    const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+    float v = 0.f;
+    if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z)
+      v = __bfloat162float(inb[(int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
+    in_s[i] = v;
+  }
+  for (int i = threadIdx.x; i < CO * CI * 27; i += TV) {
+    const int co = i / (CI * 27), r = i % (CI * 27);   // r = ci*27 + tap
+    w_s[r * CO + co] = __bfloat162float(w[i]);
+  }
+  __syncthreads();
+  const int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
+  const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
+  float acc[CO];
+#pragma unroll
+  for (int co = 0; co < CO; ++co) acc[co] = bias ? bias[co] : 0.f;
+  for (int ci = 0; ci < CI; ++ci) {
+    const float* src = in_s + ci * HV;
+    const float* wc = w_s + ci * 27 * CO;
+#pragma unroll
+    for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) {
+          const float v = src[((lz + dz) * HY + (ly + dy)) * HX + (lx + dx)];
+          const float* wt = wc + ((dz * 3 + dy) * 3 + dx) * CO;
+#pragma unroll
+          for (int co = 0; co < CO; ++co) acc[co] = fmaf(wt[co], v, acc[co]);
+        }
+  }
+  if (gx >= d.X || gy >= d.Y || gz >= d.Z) return;
+  const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
+  const int64_t ob = (int64_t)b * CO * vol;
+#pragma unroll
+  for (int co = 0; co < CO; ++co) {
+    const int64_t o = ob + (int64_t)co * vol + p;
+    if (MODE == FWD_HIDDEN) {
+      z[o] = acc[co];
+      act[o] = __float2bfloat16_rn(gelu(acc[co]));
+    } else if (MODE == FWD_LAST) {
+      z[o] = acc[co];
+    } else if (MODE == INFER_HIDDEN) {
+      act[o] = __float2bfloat16_rn(gelu(acc[co]));
+    } else {
+      act[o] = __float2bfloat16_rn(acc[co] * gelu_grad(zaux[o]));
+    }
+  }
+}
+
+template <int CI, int CO, int MODE>
+static cudaError_t conv(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
+                        const float* bias, float* z, __nv_bfloat16* act, const float* zaux) {
+  const size_t smem = sizeof(float) * (CI * HV + CO * CI * 27);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int tiles = ((d.X + TX - 1) / TX) * ((d.Y + TY - 1) / TY) * ((d.Z + TZ - 1) / TZ);
+  conv_kernel<CI, CO, MODE><<<dim3(tiles, B), TV, smem, st>>>(in, d, w, bias, z, act, zaux);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// weight and bias gradients: per-block partials of dW[co][ci][tap] =
+// sum_p g[co, p] a[ci, p + tap - 1] and db[co] = sum_p g[co, p]
+// ---------------------------------------------------------------------------
+template <int CI, int CO>
+__global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __restrict__ g,
+                                                   Dims d, float* __restrict__ partials) {
+  constexpr int PAIRS = CO * CI;
+  constexpr int GROUPS = TV / PAIRS >= 1 ? TV / PAIRS : 1;
+  constexpr int NV = PAIRS * 27 + CO;
+  extern __shared__ float smem[];
+  float* a_s = smem;                  // [CI][HV]
+  float* g_s = smem + CI * HV;        // [CO][TV]
+  float* r_s = g_s + CO * TV;         // [GROUPS][PAIRS][28]
+  const int tilesx = (d.X + TX - 1) / TX, tilesy = (d.Y + TY - 1) / TY;
+  const int tz0 = (blockIdx.x / (tilesx * tilesy)) * TZ;
+  const int ty0 = ((blockIdx.x / tilesx) % tilesy) * TY;
+  const int tx0 = (blockIdx.x % tilesx) * TX;
+  const int b = blockIdx.y;
+  const int64_t vol = d.vol();
+  for (int i = threadIdx.x; i < CI * HV; i += TV) {
+    const int c = i / HV, h = i % HV;
+    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
+    const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+    float v = 0.f;
+    if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z)
+      v = __bfloat162float(a[(int64_t)b * CI * vol + (int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
+    a_s[i] = v;
+  }
+  for (int i = threadIdx.x; i < CO * TV; i += TV) {
+    const int c = i / TV, t = i % TV;
+    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+    const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
+    float v = 0.f;
+    if (gx < d.X && gy < d.Y && gz < d.Z)
+      v = __bfloat162float(g[(int64_t)b * CO * vol + (int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
+    g_s[i] = v;
+  }
+  __syncthreads();
+  const int pair = threadIdx.x % PAIRS, grp = threadIdx.x / PAIRS;
+  const int co = pair / CI, ci = pair % CI;
+  float acc[27];
+#pragma unroll
+  for (int k = 0; k < 27; ++k) acc[k] = 0.f;
+  float db = 0.f;
+  if (grp < GROUPS) {
+    for (int t = grp; t < TV; t += GROUPS) {
+      const float gv = g_s[co * TV + t];
+      const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
+      const float* src = a_s + ci * HV;
+#pragma unroll
+      for (int dz = 0; dz < 3; ++dz)
+#pragma unroll
+        for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+          for (int dx = 0; dx < 3; ++dx)
+            acc[(dz * 3 + dy) * 3 + dx] = fmaf(gv, src[((lz + dz) * HY + (ly + dy)) * HX + (lx + dx)],
+                                               acc[(dz * 3 + dy) * 3 + dx]);
+      db += gv;
+    }
+    float* r = r_s + ((size_t)grp * PAIRS + pair) * 28;
+#pragma unroll
+    for (int k = 0; k < 27; ++k) r[k] = acc[k];
+    r[27] = db;
+  }
+  __syncthreads();
+  float* out = partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NV;
+  for (int i = threadIdx.x; i < PAIRS * 28; i += TV) {
+    const int pr = i / 28, k = i % 28;
+    float s = 0.f;
+    for (int gg = 0; gg < GROUPS; ++gg) s += r_s[((size_t)gg * PAIRS + pr) * 28 + k];
+    if (k < 27)
+      out[pr * 27 + k] = s;                        // [co][ci][tap] with pr = co*CI + ci
+    else if (pr % CI == 0)
+      out[PAIRS * 27 + pr / CI] = s;               // bias of co = pr / CI (ci == 0 carries it)
+  }
+}
+
+template <int CI, int CO>
+static cudaError_t wgrad(cudaStream_t st, const __nv_bfloat16* a, const __nv_bfloat16* g, Dims d, int B,
+                         float* partials, int* nblocks) {
+  constexpr int PAIRS = CO * CI;
+  constexpr int GROUPS = TV / PAIRS >= 1 ? TV / PAIRS : 1;
+  const size_t smem = sizeof(float) * (CI * HV + CO * TV + GROUPS * PAIRS * 28);
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const int tiles = ((d.X + TX - 1) / TX) * ((d.Y + TY - 1) / TY) * ((d.Z + TZ - 1) / TZ);
+  wgrad_kernel<CI, CO><<<dim3(tiles, B), TV, smem, st>>>(a, g, d, partials);
+  *nblocks = tiles * B;
+  return cudaGetLastError();
+}
+
+// grad[i] = sum over blocks of partials[blk][i], in block order (FP64 sum)
+__global__ void reduce_partials_kernel(const float* partials, int nblocks, int nv, float* grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  double s = 0.0;
+  for (int b = 0; b < nblocks; ++b) s += (double)partials[(size_t)b * nv + i];
+  grad[i] = (float)s;
+}
+
+// ---------------------------------------------------------------------------
+// loss, weight handling, data movement
+// ---------------------------------------------------------------------------
+
+// g = bf16(2 (out - t) / count); per-block partial sums of (out - t)^2
+__global__ void loss_kernel(const float* out, const float* t, int64_t n, double inv_count, __nv_bfloat16* g,
+                            double* partial) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float dlt = out[i] - t[i];
+    s += (double)dlt * dlt;
+    g[i] = __float2bfloat16_rn((float)(2.0 * (double)dlt * inv_count));
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    partial[blockIdx.x] = tot;
+  }
+}
+
+// bf16 copies of the weights (and transposed, flipped copies for the data
+// gradient: wt[ci][co][26 - tap] = w[co][ci][tap]) and bf16-rounded biases
+__global__ void quantize_kernel(const float* theta, __nv_bfloat16* wq, __nv_bfloat16* wt, float* bq, int ci, int co) {
+  const int nw = co * ci * 27;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < nw + co; i += gridDim.x * blockDim.x) {
+    if (i < nw) {
+      const __nv_bfloat16 v = __float2bfloat16_rn(theta[i]);
+      wq[i] = v;
+      const int o = i / (ci * 27), r = i % (ci * 27), c = r / 27, tap = r % 27;
+      wt[(c * co + o) * 27 + (26 - tap)] = v;
+    } else {
+      bq[i - nw] = bf(theta[i]);
+    }
+  }
+}
+
+__global__ void adam_kernel(float* theta, float* m, float* v, const float* grad, int n, float lr, float b1, float b2,
+                            float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = grad[i];
+  const float mi = b1 * m[i] + (1.f - b1) * g;
+  const float vi = b2 * v[i] + (1.f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  theta[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// batch of crops of pair k: in[b] = (bf16(sr_k r0), bf16(s_x x)), t[b] = c sr_k delta
+// (sr_k = 1 / RMS of pair k's residual: the map r0 -> delta is linear, so each
+// pair is presented at unit residual scale)
+__global__ void gather_kernel(const float* pin, const float* pt, int64_t N, Dims full, const int* origins, int D,
+                              const float* pair_sr, float s1, float c, __nv_bfloat16* in, float* t) {
+  const int b = blockIdx.y;
+  const int k = origins[4 * b], oz = origins[4 * b + 1], oy = origins[4 * b + 2], ox = origins[4 * b + 3];
+  const float s0 = pair_sr[k], st = c * pair_sr[k];
+  const int64_t v3 = (int64_t)D * D * D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v3; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), y = (int)((i / D) % D), z = (int)(i / ((int64_t)D * D));
+    const int64_t g = ((int64_t)(oz + z) * full.Y + (oy + y)) * full.X + (ox + x);
+    in[((int64_t)b * 2 + 0) * v3 + i] = __float2bfloat16_rn(s0 * pin[((int64_t)k * 2 + 0) * N + g]);
+    in[((int64_t)b * 2 + 1) * v3 + i] = __float2bfloat16_rn(s1 * pin[((int64_t)k * 2 + 1) * N + g]);
+    t[(int64_t)b * v3 + i] = st * pt[(int64_t)k * N + g];
+  }
+}
+
+// store a training pair: the input channels (r0, x_prev) and the target
+// x_next - x_prev, FP32
+__global__ void pair_kernel(const double* r0, const double* xp, const double* xn, int64_t N, float* pin, float* pt) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    pin[i] = (float)r0[i];
+    pin[N + i] = (float)xp[i];
+    pt[i] = (float)(xn[i] - xp[i]);
+  }
+}
+
+// inference input: bf16(s0 r0), bf16(s1 x_prev)
+__global__ void infer_in_kernel(const double* r0, const double* xp, int64_t N, float s0, float s1,
+                                __nv_bfloat16* in) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+    in[i] = __float2bfloat16_rn(s0 * (float)r0[i]);
+    in[N + i] = __float2bfloat16_rn(s1 * (float)xp[i]);
+  }
+}
+
+__global__ void infer_out_kernel(const float* out, int64_t N, double inv_st, double* delta) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x)
+    delta[i] = (double)out[i] * inv_st;
+}
+
+// per-block sums of squares (deterministic: fixed mapping)
+template <typename T>
+__global__ void sumsq_kernel(const T* x, int64_t n, double* partial) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    s += (double)x[i] * x[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    partial[blockIdx.x] = tot;
+  }
+}
+
+__global__ void bf16_from_float_kernel(const float* x, int64_t n, __nv_bfloat16* y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+}  // namespace mcnn
+
+// ===========================================================================
+// handle
+// ===========================================================================
+using namespace mcnn;
+
+struct msstab_cnn_s {
+  Dims full{};
+  std::vector<float> pair_sr;   // 1 / RMS of each stored pair's residual
+  float* d_pair_sr = nullptr;
+  int64_t N = 0;
+  int max_pairs = 0, n_pairs = 0, max_batch = 0, crop = 0;
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  float* theta = nullptr;
+  float* m = nullptr;
+  float* v = nullptr;
+  float* grad = nullptr;
+  __nv_bfloat16* wq[NL] = {};
+  __nv_bfloat16* wt[NL] = {};
+  float* bq[NL] = {};
+  float* pin = nullptr;   // [max_pairs][2][N]
+  float* pt = nullptr;    // [max_pairs][N]
+  // training buffers (batch of crops)
+  __nv_bfloat16* act[NL] = {};  // input of layer l
+  float* z[NL] = {};            // pre-activation of layer l
+  __nv_bfloat16* dz[NL] = {};   // gradient of the pre-activation of layer l (bf16)
+  float* tgt = nullptr;
+  float* partials = nullptr;
+  double* dpart = nullptr;
+  double* h_small = nullptr;
+  int* origins = nullptr;
+  // inference buffers (full grid)
+  __nv_bfloat16* iin = nullptr;
+  __nv_bfloat16* ia = nullptr;
+  __nv_bfloat16* ib = nullptr;
+  float* iout = nullptr;
+  float scale[2] = {1.f, 1.f};   // s_x (x channel), c (target factor)
+  int adam_t = 0;
+  std::string err;
+};
+
+namespace {
+
+thread_local std::string g_cnn_error;
+
+msstab_status cfail(msstab_cnn_t h, msstab_status code, const std::string& what) {
+  if (h) h->err = what;
+  g_cnn_error = what;
+  msk::set_global_error(what);
+  return code;
+}
+
+#define CCK(call)                                                                              \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return cfail(h, e_ == cudaErrorMemoryAllocation ? MSSTAB_ERR_OOM : MSSTAB_ERR_CUDA,      \
+                   std::string(#call) + ": " + cudaGetErrorString(e_));                        \
+  } while (0)
+
+template <typename T>
+msstab_status calloc_(msstab_cnn_t h, T** p, size_t count) {
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, count * sizeof(T) + 256);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return cfail(h, MSSTAB_ERR_OOM, "cudaMalloc failed in the CNN handle");
+  }
+  h->allocs.push_back(q);
+  *p = (T*)q;
+  return MSSTAB_OK;
+}
+
+#define CKA(expr)                      \
+  do {                                 \
+    msstab_status s_ = (expr);         \
+    if (s_ != MSSTAB_OK) return s_;    \
+  } while (0)
+
+int grid1(int64_t n) {
+  int64_t g = (n + 255) / 256;
+  return (int)(g < 4096 ? (g < 1 ? 1 : g) : 4096);
+}
+
+msstab_status quantize(msstab_cnn_t h) {
+  for (int l = 0; l < NL; ++l) {
+    const int o = w_offset(l);
+    quantize_kernel<<<grid1(CO_[l] * CI_[l] * 27 + CO_[l]), 256, 0, h->stream>>>(h->theta + o, h->wq[l], h->wt[l],
+                                                                                   h->bq[l], CI_[l], CO_[l]);
+    CCK(cudaGetLastError());
+  }
+  return MSSTAB_OK;
+}
+
+// forward of the batch in h->act[0] (B crops of D^3): z[l], act[l+1]
+msstab_status forward_batch(msstab_cnn_t h, int B, int D) {
+  const Dims d{D, D, D};
+  cudaStream_t st = h->stream;
+  CCK((conv<2, 16, FWD_HIDDEN>(st, h->act[0], d, B, h->wq[0], h->bq[0], h->z[0], h->act[1], nullptr)));
+  CCK((conv<16, 16, FWD_HIDDEN>(st, h->act[1], d, B, h->wq[1], h->bq[1], h->z[1], h->act[2], nullptr)));
+  CCK((conv<16, 16, FWD_HIDDEN>(st, h->act[2], d, B, h->wq[2], h->bq[2], h->z[2], h->act[3], nullptr)));
+  CCK((conv<16, 1, FWD_LAST>(st, h->act[3], d, B, h->wq[3], h->bq[3], h->z[3], nullptr, nullptr)));
+  return MSSTAB_OK;
+}
+
+// loss of z[3] against tgt, gradient into h->grad; *loss on the host
+msstab_status backward_batch(msstab_cnn_t h, int B, int D, double* loss) {
+  const Dims d{D, D, D};
+  cudaStream_t st = h->stream;
+  const int64_t n = (int64_t)B * D * D * D;
+  const int lg = grid1(n) < 1024 ? grid1(n) : 1024;
+  loss_kernel<<<lg, 256, 0, st>>>(h->z[3], h->tgt, n, 1.0 / (double)n, h->dz[3], h->dpart);
+  CCK(cudaGetLastError());
+  int nb = 0;
+  // layer 3 (16 -> 1)
+  CCK((wgrad<16, 1>(st, h->act[3], h->dz[3], d, B, h->partials, &nb)));
+  reduce_partials_kernel<<<grid1(16 * 27 + 1), 256, 0, st>>>(h->partials, nb, 16 * 27 + 1, h->grad + w_offset(3));
+  CCK((conv<1, 16, BWD_DATA>(st, h->dz[3], d, B, h->wt[3], nullptr, nullptr, h->dz[2], h->z[2])));
+  for (int l = 2; l >= 1; --l) {
+    CCK((wgrad<16, 16>(st, h->act[l], h->dz[l], d, B, h->partials, &nb)));
+    reduce_partials_kernel<<<grid1(16 * 16 * 27 + 16), 256, 0, st>>>(h->partials, nb, 16 * 16 * 27 + 16,
+                                                                     h->grad + w_offset(l));
+    CCK((conv<16, 16, BWD_DATA>(st, h->dz[l], d, B, h->wt[l], nullptr, nullptr, h->dz[l - 1], h->z[l - 1])));
+  }
+  CCK((wgrad<2, 16>(st, h->act[0], h->dz[0], d, B, h->partials, &nb)));
+  reduce_partials_kernel<<<grid1(2 * 16 * 27 + 16), 256, 0, st>>>(h->partials, nb, 2 * 16 * 27 + 16,
+                                                                  h->grad + w_offset(0));
+  CCK(cudaGetLastError());
+  if (loss) {
+    std::vector<double> part(lg);
+    CCK(cudaMemcpyAsync(part.data(), h->dpart, sizeof(double) * lg, cudaMemcpyDeviceToHost, st));
+    CCK(cudaStreamSynchronize(st));
+    double s = 0.0;
+    for (int i = 0; i < lg; ++i) s += part[i];
+    *loss = s / (double)n;
+  }
+  return MSSTAB_OK;
+}
+
+template <typename T>
+msstab_status sumsq(msstab_cnn_t h, const T* x, int64_t n, double* out) {
+  const int g = 1024;
+  sumsq_kernel<T><<<g, 256, 0, h->stream>>>(x, n, h->dpart);
+  CCK(cudaGetLastError());
+  std::vector<double> part(g);
+  CCK(cudaMemcpyAsync(part.data(), h->dpart, sizeof(double) * g, cudaMemcpyDeviceToHost, h->stream));
+  CCK(cudaStreamSynchronize(h->stream));
+  double s = 0.0;
+  for (int i = 0; i < g; ++i) s += part[i];
+  *out = s;
+  return MSSTAB_OK;
+}
+
+msstab_status check_batch(msstab_cnn_t h, int B, int D) {
+  if (B < 1 || B > h->max_batch || D < 1 || D > h->crop)
+    return cfail(h, MSSTAB_ERR_INVALID_ARG, "batch size or crop edge beyond the handle's capacity");
+  return MSSTAB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t msstab_cnn_num_params(void) { return n_params(); }
+
+msstab_status msstab_cnn_destroy(msstab_cnn_t h) {
+  if (!h) return MSSTAB_OK;
+  cudaStreamSynchronize(h->stream);
+  for (void* p : h->allocs) cudaFree(p);
+  if (h->h_small) cudaFreeHost(h->h_small);
+  delete h;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float* d_params, int32_t max_pairs,
+                                int32_t max_batch, int32_t crop, void* stream, msstab_cnn_t* out) {
+  if (!out) return cfail(nullptr, MSSTAB_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (nx < 1 || ny < 1 || nz < 1 || (int64_t)nx * ny * nz >= (1LL << 31) || max_pairs < 0 || max_batch < 1 ||
+      crop < 1 || crop > nx || crop > ny || crop > nz || !d_params)
+    return cfail(nullptr, MSSTAB_ERR_INVALID_ARG, "msstab_cnn_create: bad grid, capacity or NULL parameters");
+  msstab_cnn_t h = new msstab_cnn_s();
+  h->full = Dims{nx, ny, nz};
+  h->N = (int64_t)nx * ny * nz;
+  h->max_pairs = max_pairs;
+  h->max_batch = max_batch;
+  h->crop = crop;
+  h->stream = (cudaStream_t)stream;
+  auto fail_create = [&](msstab_status s) {
+    g_cnn_error = h->err;
+    msstab_cnn_destroy(h);
+    return s;
+  };
+  const int np = n_params();
+  const int64_t bv = (int64_t)max_batch * crop * crop * crop;
+  msstab_status s = MSSTAB_OK;
+#define CKC(expr)                      \
+  if ((s = (expr)) != MSSTAB_OK) return fail_create(s)
+  CKC(calloc_(h, &h->theta, np));
+  CKC(calloc_(h, &h->m, np));
+  CKC(calloc_(h, &h->v, np));
+  CKC(calloc_(h, &h->grad, np));
+  for (int l = 0; l < NL; ++l) {
+    CKC(calloc_(h, &h->wq[l], CO_[l] * CI_[l] * 27));
+    CKC(calloc_(h, &h->wt[l], CO_[l] * CI_[l] * 27));
+    CKC(calloc_(h, &h->bq[l], CO_[l]));
+    CKC(calloc_(h, &h->act[l], (size_t)CI_[l] * bv));
+    CKC(calloc_(h, &h->z[l], (size_t)CO_[l] * bv));
+    CKC(calloc_(h, &h->dz[l], (size_t)CO_[l] * bv));
+  }
+  CKC(calloc_(h, &h->tgt, bv));
+  const int64_t tiles = ((crop + TX - 1) / TX) * (int64_t)((crop + TY - 1) / TY) * ((crop + TZ - 1) / TZ) * max_batch;
+  CKC(calloc_(h, &h->partials, (size_t)tiles * (16 * 16 * 27 + 16)));
+  CKC(calloc_(h, &h->dpart, 4096));
+  CKC(calloc_(h, &h->origins, 4 * (size_t)max_batch));
+  if (max_pairs > 0) {
+    CKC(calloc_(h, &h->pin, (size_t)max_pairs * 2 * h->N));
+    CKC(calloc_(h, &h->pt, (size_t)max_pairs * h->N));
+    CKC(calloc_(h, &h->d_pair_sr, (size_t)max_pairs));
+  }
+  CKC(calloc_(h, &h->iin, 2 * (size_t)h->N));
+  CKC(calloc_(h, &h->ia, 16 * (size_t)h->N));
+  CKC(calloc_(h, &h->ib, 16 * (size_t)h->N));
+  CKC(calloc_(h, &h->iout, (size_t)h->N));
+#undef CKC
+  if (cudaMallocHost((void**)&h->h_small, 64 * sizeof(double)) != cudaSuccess) {
+    h->h_small = nullptr;
+    h->err = "cudaMallocHost failed";
+    return fail_create(MSSTAB_ERR_OOM);
+  }
+  if (cudaMemcpyAsync(h->theta, d_params, sizeof(float) * np, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->m, 0, sizeof(float) * np, h->stream) != cudaSuccess ||
+      cudaMemsetAsync(h->v, 0, sizeof(float) * np, h->stream) != cudaSuccess) {
+    h->err = "copying the initial parameters failed";
+    return fail_create(MSSTAB_ERR_CUDA);
+  }
+  if ((s = quantize(h)) != MSSTAB_OK) return fail_create(s);
+  if (cudaStreamSynchronize(h->stream) != cudaSuccess) {
+    h->err = "CNN set-up failed";
+    return fail_create(MSSTAB_ERR_CUDA);
+  }
+  *out = h;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_get_params(msstab_cnn_t h, float* d_params) {
+  if (!h || !d_params) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  CCK(cudaMemcpyAsync(d_params, h->theta, sizeof(float) * n_params(), cudaMemcpyDeviceToDevice, h->stream));
+  CCK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_set_params(msstab_cnn_t h, const float* d_params) {
+  if (!h || !d_params) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  CCK(cudaMemcpyAsync(h->theta, d_params, sizeof(float) * n_params(), cudaMemcpyDeviceToDevice, h->stream));
+  CKA(quantize(h));
+  CCK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_set_scales(msstab_cnn_t h, float s_x, float c) {
+  if (!h || !(s_x > 0.f) || !(c > 0.f)) return cfail(h, MSSTAB_ERR_INVALID_ARG, "scales must be positive");
+  h->scale[0] = s_x;
+  h->scale[1] = c;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_get_scales(msstab_cnn_t h, float* scales2) {
+  if (!h || !scales2) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  std::memcpy(scales2, h->scale, sizeof(h->scale));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_forward(msstab_cnn_t h, const float* d_in, int32_t B, int32_t D, float* d_out) {
+  if (!h || !d_in || !d_out) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  CKA(check_batch(h, B, D));
+  const int64_t n = (int64_t)B * 2 * D * D * D;
+  bf16_from_float_kernel<<<grid1(n), 256, 0, h->stream>>>(d_in, n, h->act[0]);
+  CCK(cudaGetLastError());
+  CKA(forward_batch(h, B, D));
+  CCK(cudaMemcpyAsync(d_out, h->z[3], sizeof(float) * B * D * D * D, cudaMemcpyDeviceToDevice, h->stream));
+  CCK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_grad(msstab_cnn_t h, const float* d_in, const float* d_target, int32_t B, int32_t D,
+                              float* d_grad, double* loss) {
+  if (!h || !d_in || !d_target || !d_grad) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  CKA(check_batch(h, B, D));
+  const int64_t n = (int64_t)B * 2 * D * D * D;
+  bf16_from_float_kernel<<<grid1(n), 256, 0, h->stream>>>(d_in, n, h->act[0]);
+  CCK(cudaGetLastError());
+  CCK(cudaMemcpyAsync(h->tgt, d_target, sizeof(float) * B * D * D * D, cudaMemcpyDeviceToDevice, h->stream));
+  CKA(forward_batch(h, B, D));
+  CKA(backward_batch(h, B, D, loss));
+  CCK(cudaMemcpyAsync(d_grad, h->grad, sizeof(float) * n_params(), cudaMemcpyDeviceToDevice, h->stream));
+  CCK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_adam_step(msstab_cnn_t h, const float* d_grad, float lr) {
+  if (!h || !d_grad || !(lr > 0.f)) return cfail(h, MSSTAB_ERR_INVALID_ARG, "bad Adam arguments");
+  h->adam_t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)h->adam_t), c2 = 1.f - powf(b2, (float)h->adam_t);
+  adam_kernel<<<grid1(n_params()), 256, 0, h->stream>>>(h->theta, h->m, h->v, d_grad, n_params(), lr, b1, b2, 1e-8f,
+                                                        c1, c2);
+  CCK(cudaGetLastError());
+  CKA(quantize(h));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_add_pair(msstab_cnn_t h, const double* d_r0, const double* d_x_prev,
+                                  const double* d_x_next) {
+  if (!h || !d_r0 || !d_x_prev || !d_x_next) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  if (h->n_pairs >= h->max_pairs) return cfail(h, MSSTAB_ERR_INVALID_ARG, "the pair store is full");
+  const int k = h->n_pairs;
+  pair_kernel<<<grid1(h->N), 256, 0, h->stream>>>(d_r0, d_x_prev, d_x_next, h->N, h->pin + (size_t)k * 2 * h->N,
+                                                  h->pt + (size_t)k * h->N);
+  CCK(cudaGetLastError());
+  double ss = 0.0;
+  CKA(sumsq<double>(h, d_r0, h->N, &ss));
+  const double rms = std::sqrt(ss / (double)h->N);
+  const float sr = rms > 0.0 && std::isfinite(rms) ? (float)(1.0 / rms) : 1.f;
+  h->pair_sr.push_back(sr);
+  CCK(cudaMemcpyAsync(h->d_pair_sr + k, &h->pair_sr.back(), sizeof(float), cudaMemcpyHostToDevice, h->stream));
+  CCK(cudaStreamSynchronize(h->stream));
+  h->n_pairs += 1;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_fit_scales(msstab_cnn_t h) {
+  if (!h || h->n_pairs < 1) return cfail(h, MSSTAB_ERR_INVALID_ARG, "no training pairs");
+  double sx = 0.0, sd = 0.0;
+  for (int k = 0; k < h->n_pairs; ++k) {
+    double a = 0.0, d = 0.0;
+    CKA(sumsq<float>(h, h->pin + ((size_t)k * 2 + 1) * h->N, h->N, &a));
+    CKA(sumsq<float>(h, h->pt + (size_t)k * h->N, h->N, &d));
+    sx += a;
+    sd += d * (double)h->pair_sr[k] * (double)h->pair_sr[k];
+  }
+  const double cnt = (double)h->n_pairs * (double)h->N;
+  const double rx = std::sqrt(sx / cnt), rd = std::sqrt(sd / cnt);
+  h->scale[0] = rx > 0.0 ? (float)(1.0 / rx) : 1.f;
+  h->scale[1] = rd > 0.0 ? (float)(1.0 / rd) : 1.f;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_train(msstab_cnn_t h, int32_t iters, int32_t B, int32_t D, const int32_t* origins,
+                               float lr, float* loss_history) {
+  if (!h || !origins || iters < 0 || !(lr > 0.f)) return cfail(h, MSSTAB_ERR_INVALID_ARG, "bad training arguments");
+  CKA(check_batch(h, B, D));
+  if (h->n_pairs < 1) return cfail(h, MSSTAB_ERR_INVALID_ARG, "no training pairs");
+  for (int it = 0; it < iters; ++it) {
+    const int32_t* o = origins + (size_t)it * 4 * B;
+    for (int b = 0; b < B; ++b)
+      if (o[4 * b] < 0 || o[4 * b] >= h->n_pairs || o[4 * b + 1] < 0 || o[4 * b + 1] + D > h->full.Z ||
+          o[4 * b + 2] < 0 || o[4 * b + 2] + D > h->full.Y || o[4 * b + 3] < 0 || o[4 * b + 3] + D > h->full.X)
+        return cfail(h, MSSTAB_ERR_INVALID_ARG, "crop origin out of range");
+    CCK(cudaMemcpyAsync(h->origins, o, sizeof(int32_t) * 4 * B, cudaMemcpyHostToDevice, h->stream));
+    const int64_t v3 = (int64_t)D * D * D;
+    gather_kernel<<<dim3(grid1(v3), B), 256, 0, h->stream>>>(h->pin, h->pt, h->N, h->full, h->origins, D,
+                                                             h->d_pair_sr, h->scale[0], h->scale[1], h->act[0],
+                                                             h->tgt);
+    CCK(cudaGetLastError());
+    CKA(forward_batch(h, B, D));
+    double loss = 0.0;
+    CKA(backward_batch(h, B, D, loss_history ? &loss : nullptr));
+    if (loss_history) loss_history[it] = (float)loss;
+    CKA(msstab_cnn_adam_step(h, h->grad, lr));
+  }
+  CCK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_infer(msstab_cnn_t h, const double* d_r0, const double* d_x_prev, double* d_delta) {
+  if (!h || !d_r0 || !d_x_prev || !d_delta) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t st = h->stream;
+  double ss = 0.0;
+  CKA(sumsq<double>(h, d_r0, h->N, &ss));
+  const double rms = std::sqrt(ss / (double)h->N);
+  const float sr = rms > 0.0 && std::isfinite(rms) ? (float)(1.0 / rms) : 1.f;
+  infer_in_kernel<<<grid1(h->N), 256, 0, st>>>(d_r0, d_x_prev, h->N, sr, h->scale[0], h->iin);
+  CCK(cudaGetLastError());
+  CCK((conv<2, 16, INFER_HIDDEN>(st, h->iin, h->full, 1, h->wq[0], h->bq[0], nullptr, h->ia, nullptr)));
+  CCK((conv<16, 16, INFER_HIDDEN>(st, h->ia, h->full, 1, h->wq[1], h->bq[1], nullptr, h->ib, nullptr)));
+  CCK((conv<16, 16, INFER_HIDDEN>(st, h->ib, h->full, 1, h->wq[2], h->bq[2], nullptr, h->ia, nullptr)));
+  CCK((conv<16, 1, FWD_LAST>(st, h->ia, h->full, 1, h->wq[3], h->bq[3], h->iout, nullptr, nullptr)));
+  infer_out_kernel<<<grid1(h->N), 256, 0, st>>>(h->iout, h->N, 1.0 / ((double)h->scale[1] * (double)sr), d_delta);
+  CCK(cudaGetLastError());
+  return MSSTAB_OK;
+}
+
+const char* msstab_cnn_last_error(msstab_cnn_t h) { return h ? h->err.c_str() : g_cnn_error.c_str(); }
+
+}  // extern "C"

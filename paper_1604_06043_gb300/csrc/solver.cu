@@ -313,6 +313,7 @@ struct SolveCtl {
   int ell;                // stabilisation degree of this solve (<= the handle's l)
   bool stop_on_stagnation;  // stop when the residual has not halved in 4 cycles
   bool continue_basis;    // start from the U, V left in the level slots by the previous solve
+  int replace_every;      // > 0: r := b - A x after every replace_every-th cycle
 };
 
 template <typename T>
@@ -434,8 +435,19 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     out.mvs += cyc_mvs;
     if (prec) h->mvs32 += cyc_mvs;
     out.cycles += 1;
+    // residual replacement at the cycle end: r = b - A x with P^T r and ||r||^2 in the same pass
+    // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
+    // level step from P^T V (left by tau_update) in the epilogue
+    const bool replaced = ctl.replace_every > 0 && out.cycles % ctl.replace_every == 0;
+    if (replaced) {
+      LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
+                                        epi_of(EPI_GAMMA, 0, 0)));
+      out.mvs += 1;
+      if (prec) h->mvs32 += 1;
+    }
     // ---- cycle end: the one host synchronisation ----
-    CK(cudaMemcpyAsync(h->h_small, &st->rr, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->h_small, replaced ? &st->projR[s] : &st->rr, sizeof(double), cudaMemcpyDeviceToHost,
+                       h->stream));
     CK(cudaMemcpyAsync(h->h_small + 1, &st->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
     CKS(timing_flush(h));
@@ -454,7 +466,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     }
     if (!std::isfinite(relres)) continue;  // handled (restore) at the top
     std::swap(w.XB, w.XB2);
-    r_is_true = false;
+    r_is_true = replaced;
     out.relres_rec = relres;
     if (ctl.stop_on_stagnation) {
       if (relres < 0.5 * best) {
@@ -528,6 +540,7 @@ SolveCtl make_ctl(msstab_t h, double tol, bool first_has_rec) {
   ctl.ell = h->ell;
   ctl.stop_on_stagnation = false;
   ctl.continue_basis = false;
+  ctl.replace_every = h->opt.replace_every > 0 ? h->opt.replace_every : 0;
   return ctl;
 }
 
@@ -706,6 +719,7 @@ void msstab_default_options(msstab_options* opt) {
   opt->kernel_timing = 0;
   opt->max_outer = 0;
   opt->inner_ell = 0;
+  opt->replace_every = 0;
   opt->stream = nullptr;
 }
 
@@ -1005,6 +1019,40 @@ msstab_status msstab_select_guess(msstab_t h, const double* d_b, const double* d
   CK(cudaMemcpyAsync(d_x, keep ? w.XB2 : d_xprev, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (used) *used = keep ? 1 : 0;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_select_guess_scaled(msstab_t h, const double* d_b, const double* d_xprev,
+                                         const double* d_delta, double* d_x, int32_t* used, double* alpha,
+                                         double* reduction) {
+  CKS(check_handle(h));
+  CKS(check_ptr(h, d_b, "b"));
+  CKS(check_ptr(h, d_xprev, "xprev"));
+  CKS(check_ptr(h, d_delta, "delta"));
+  CKS(check_ptr(h, d_x, "x"));
+  const Ctx c = h->ctx();
+  const int n = h->n;
+  DevState* st = h->st;
+  Work<double>& w = h->w64;
+  // r0 = b - A x_prev (||r0||^2), w = A delta, then w . r0 and w . w
+  LAUNCH(MSSTAB_K_SPMV, spmv<double>(c, h->A, d_xprev, w.Tm, d_b, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
+  LAUNCH(MSSTAB_K_SPMV, spmv<double>(c, h->A, d_delta, w.XB2, nullptr, nullptr, 0, 0, 0, 0, nullptr, epi_none(h)));
+  MdCols<double> cols{};
+  cols.x[0] = w.XB2;
+  cols.y[0] = w.Tm;
+  LAUNCH(MSSTAB_K_OTHER, multidot<double>(c, n, cols, 1, 1, 1, &st->scal[1], 2, epi_none(h)));
+  CKS(sync_read(h, &st->scal[0], 3 * sizeof(double)));
+  const double rr = h->h_small[0], wr = h->h_small[1], ww = h->h_small[2];
+  const double a = ww > 0.0 ? wr / ww : 0.0;
+  const bool keep = std::isfinite(a) && a != 0.0 && rr > 0.0;
+  if (keep)
+    LAUNCH(MSSTAB_K_OTHER, axpby_f64(c, n, 1.0, d_xprev, a, d_delta, d_x));
+  else
+    CK(cudaMemcpyAsync(d_x, d_xprev, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (used) *used = keep ? 1 : 0;
+  if (alpha) *alpha = keep ? a : 0.0;
+  if (reduction) *reduction = keep ? std::sqrt(std::max(0.0, 1.0 - (wr * wr) / (ww * rr))) : 1.0;
   return MSSTAB_OK;
 }
 

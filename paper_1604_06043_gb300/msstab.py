@@ -39,7 +39,8 @@ class Options(ctypes.Structure):
         ("kernel_timing", ctypes.c_int32),
         ("max_outer", ctypes.c_int32),
         ("inner_ell", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("replace_every", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -91,6 +92,8 @@ _SIGS = {
     "msstab_export_recycle": (_I32, [_P, _P, _P]),
     "msstab_import_recycle": (_I32, [_P, _P, _P]),
     "msstab_select_guess": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I32)]),
+    "msstab_select_guess_scaled": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_D),
+                                          ctypes.POINTER(_D)]),
     "msstab_op_spmv": (_I32, [_P, _I32, _P, _P]),
     "msstab_op_residual": (_I32, [_P, _P, _P, _P, _P]),
     "msstab_op_spmv_dot": (_I32, [_P, _I32, _P, _P, _P]),
@@ -104,6 +107,21 @@ _SIGS = {
     "msstab_op_small_solve": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "msstab_op_tau_solve": (_I32, [_P, _I32, _P, _P]),
     "msstab_spmv_dot_noalloc": (_I32, [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I32, _P, _P]),
+    "msstab_cnn_num_params": (_I32, []),
+    "msstab_cnn_create": (_I32, [_I32, _I32, _I32, _P, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
+    "msstab_cnn_destroy": (_I32, [_P]),
+    "msstab_cnn_last_error": (ctypes.c_char_p, [_P]),
+    "msstab_cnn_get_params": (_I32, [_P, _P]),
+    "msstab_cnn_set_params": (_I32, [_P, _P]),
+    "msstab_cnn_set_scales": (_I32, [_P, ctypes.c_float, ctypes.c_float]),
+    "msstab_cnn_get_scales": (_I32, [_P, _P]),
+    "msstab_cnn_fit_scales": (_I32, [_P]),
+    "msstab_cnn_add_pair": (_I32, [_P, _P, _P, _P]),
+    "msstab_cnn_train": (_I32, [_P, _I32, _I32, _I32, _P, ctypes.c_float, _P]),
+    "msstab_cnn_forward": (_I32, [_P, _P, _I32, _I32, _P]),
+    "msstab_cnn_grad": (_I32, [_P, _P, _P, _I32, _I32, _P, ctypes.POINTER(_D)]),
+    "msstab_cnn_adam_step": (_I32, [_P, _P, ctypes.c_float]),
+    "msstab_cnn_infer": (_I32, [_P, _P, _P, _P]),
 }
 
 _lib = None
@@ -265,6 +283,14 @@ class Solver:
                                           ctypes.byref(used)), self._h)
         return bool(used.value)
 
+    def select_guess_scaled(self, b, xprev, delta, x):
+        """x = xprev + alpha delta with the residual-minimising alpha; returns
+        (used, alpha, ||b - A x|| / ||b - A xprev||)."""
+        used, a, red = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+        _check(load().msstab_select_guess_scaled(self._h, _ptr(b), _ptr(xprev), _ptr(delta), _ptr(x),
+                                                 ctypes.byref(used), ctypes.byref(a), ctypes.byref(red)), self._h)
+        return bool(used.value), a.value, red.value
+
     # -- kernel-level entry points -----------------------------------------
     def op_spmv(self, x, y, prec: int = 0):
         _check(load().msstab_op_spmv(self._h, prec, _ptr(x), _ptr(y)), self._h)
@@ -307,6 +333,94 @@ class Solver:
 
     def op_tau_solve(self, gram, tau):
         _check(load().msstab_op_tau_solve(self._h, tau.numel(), _ptr(gram), _ptr(tau)), self._h)
+
+
+class CNN:
+    """The learned-initial-guess network of libmsstab (thin wrapper)."""
+
+    def __init__(self, shape, params, max_pairs=0, max_batch=8, crop=32, device="cuda", stream=None):
+        import torch
+        lib = load()
+        nx, ny, nz = shape
+        p = torch.as_tensor(np.ascontiguousarray(params), dtype=torch.float32, device=device)
+        if p.numel() != lib.msstab_cnn_num_params():
+            raise ValueError("wrong parameter count")
+        stream = stream or torch.cuda.current_stream()
+        self._stream = stream
+        h = ctypes.c_void_p()
+        rc = lib.msstab_cnn_create(nx, ny, nz, p.data_ptr(), max_pairs, max_batch, crop, stream.cuda_stream,
+                                   ctypes.byref(h))
+        if rc != OK:
+            raise MsstabError(rc, lib.msstab_cnn_last_error(None).decode())
+        self._h = h
+        self.device = device
+        self.shape = shape
+
+    def _chk(self, rc):
+        if rc != OK:
+            raise MsstabError(rc, load().msstab_cnn_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            load().msstab_cnn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import torch
+        out = torch.empty(load().msstab_cnn_num_params(), dtype=torch.float32, device=self.device)
+        self._chk(load().msstab_cnn_get_params(self._h, out.data_ptr()))
+        return out
+
+    def set_params(self, p):
+        self._chk(load().msstab_cnn_set_params(self._h, _ptr(p)))
+
+    def set_scales(self, s_x, c):
+        self._chk(load().msstab_cnn_set_scales(self._h, s_x, c))
+
+    def scales(self):
+        out = (ctypes.c_float * 2)()
+        self._chk(load().msstab_cnn_get_scales(self._h, out))
+        return list(out)
+
+    def fit_scales(self):
+        self._chk(load().msstab_cnn_fit_scales(self._h))
+
+    def add_pair(self, r0, x_prev, x_next):
+        """A training pair: r0 = b - A x_prev, x_prev -> x_next - x_prev."""
+        self._chk(load().msstab_cnn_add_pair(self._h, _ptr(r0), _ptr(x_prev), _ptr(x_next)))
+
+    def train(self, origins, B, D, lr):
+        o = np.ascontiguousarray(origins, dtype=np.int32)
+        iters = o.size // (4 * B)
+        hist = np.zeros(iters, dtype=np.float32)
+        self._chk(load().msstab_cnn_train(self._h, iters, B, D, o.ctypes.data, float(lr), hist.ctypes.data))
+        return hist
+
+    def forward(self, x, B, D):
+        import torch
+        out = torch.empty((B, D * D * D), dtype=torch.float32, device=self.device)
+        self._chk(load().msstab_cnn_forward(self._h, _ptr(x), B, D, out.data_ptr()))
+        return out
+
+    def grad(self, x, t, B, D):
+        import torch
+        g = torch.empty(load().msstab_cnn_num_params(), dtype=torch.float32, device=self.device)
+        loss = ctypes.c_double()
+        self._chk(load().msstab_cnn_grad(self._h, _ptr(x), _ptr(t), B, D, g.data_ptr(), ctypes.byref(loss)))
+        return g, loss.value
+
+    def adam_step(self, g, lr):
+        self._chk(load().msstab_cnn_adam_step(self._h, _ptr(g), float(lr)))
+
+    def infer(self, r0, x_prev, delta):
+        """delta = the network's correction from r0 = b - A x_prev and x_prev."""
+        self._chk(load().msstab_cnn_infer(self._h, _ptr(r0), _ptr(x_prev), _ptr(delta)))
 
 
 def exported_symbols():

@@ -201,6 +201,17 @@ def crop_origins(shape, crop: int, count: int, seed: int) -> np.ndarray:
                      rng.integers(0, nx - crop + 1, count)], axis=1).astype(np.int32)
 
 
+def cnn_crop_batches(n_pairs: int, shape, crop: int, batch: int, iters: int, seed: int = SEED_CNN) -> np.ndarray:
+    """Crop origins for training the learned-guess CNN: iters x batch rows of
+    (pair index, z0, y0, x0), int32, uniform over the stored pairs and over
+    the positions of a crop^3 box inside the (x, y, z) grid."""
+    rng = np.random.default_rng(seed)
+    nx, ny, nz = shape
+    m = iters * batch
+    return np.stack([rng.integers(0, n_pairs, m), rng.integers(0, nz - crop + 1, m),
+                     rng.integers(0, ny - crop + 1, m), rng.integers(0, nx - crop + 1, m)], axis=1).astype(np.int32)
+
+
 @dataclasses.dataclass
 class Workload:
     """One implicit-Euler sequence: A = I/tau + L_h, b^(i+1) = x^(i)/tau + f."""
@@ -214,6 +225,7 @@ class Workload:
     ell: int
     tol: float = 1e-8
     variable_kappa: bool = False
+    replace_every: int = 0      # r := b - A x after every this many cycles (0: only to confirm)
 
     @property
     def n(self) -> int:
@@ -238,14 +250,17 @@ WORKLOADS = {
     # 2D, 32 x 32 interior grid, beta = (10, 10), 10 steps of tau = 0.01, s = 4, l = 2
     "convdiff2d_32": Workload("convdiff2d_32", (32, 32), (10.0, 10.0), 0.01, 10, 4, 2),
     # 3D, 128^3 grid, beta = (20, 10, 5), 50 steps of tau = 0.005, s = 8, l = 4
-    "convdiff3d_128": Workload("convdiff3d_128", (128, 128, 128), (20.0, 10.0, 5.0), 0.005, 50, 8, 4),
+    # (true residual at every cycle end: the level vectors grow like ||A||^k and
+    # the drift of V from A U would otherwise open a gap above tol)
+    "convdiff3d_128": Workload("convdiff3d_128", (128, 128, 128), (20.0, 10.0, 5.0), 0.005, 50, 8, 4,
+                               replace_every=1),
     # the same 128^3 sequence extended to 100 steps (learned initial guess)
     "convdiff3d_128_long": Workload("convdiff3d_128_long", (128, 128, 128), (20.0, 10.0, 5.0),
-                                    0.005, 100, 8, 4),
+                                    0.005, 100, 8, 4, replace_every=1),
     # 3D variable-coefficient (lognormal kappa), 256^3, 100 steps, s = 16, l = 4;
     # beta and tau are not given for it and are taken equal to the 128^3 sequence
     "kappa3d_256": Workload("kappa3d_256", (256, 256, 256), (20.0, 10.0, 5.0), 0.005, 100, 16, 4,
-                            variable_kappa=True),
+                            variable_kappa=True, replace_every=1),
     # small 3D cases with the 128^3 sequence's physics, for parity tests that
     # span many thread blocks and a ragged tail
     "convdiff3d_24": Workload("convdiff3d_24", (24, 24, 24), (20.0, 10.0, 5.0), 0.005, 4, 8, 4),

@@ -2,14 +2,15 @@
 
 The oracle (``oracle/``) solves the first systems of the 3D convection-diffusion
 sequence (128^3 grid, beta = (20, 10, 5), tau = 0.005, s = 8, l = 4, tol 1e-8,
-M(s)stab with one fetch in the first solve) from the seeded inputs, and this
+M(s)stab with one fetch in the first solve, the true residual replacing the
+recursive one at every cycle end) from the seeded inputs, and this
 script stores, per system: products with A, cycles, the relative recursive
 residual after each cycle, the true relative residual, ||x||, and x at 512
 seeded sample rows.  The full-size GPU parity tests compare against this
 record, and the CPU baseline of the benchmark takes its cycles per system from
 it.  Nothing here touches the CUDA path.
 
-    python tests/golden/make_oracle_records.py [systems]
+    python tests/golden/make_oracle_records.py [systems [output.json]]
 """
 
 import json
@@ -33,12 +34,13 @@ def sample_rows(n, k=512, seed=99):
     return np.sort(np.concatenate([[0, n - 1], rows])).astype(np.int64)
 
 
-def main(systems=23):
+def main(systems=23, out=OUT):
     w = pb.WORKLOADS["convdiff3d_128"]
     A = w.matrix()
     rows = sample_rows(w.n)
     rec = {"workload": w.name, "n": w.n, "nnz": A.nnz, "s": w.s, "ell": w.ell, "tau": w.tau, "tol": w.tol,
            "policy": "once", "fetch_threshold": "sqrt(tol)", "orth_recycle": True,
+           "replace_every": w.replace_every,
            "sample_rows": rows.tolist(), "systems": []}
     t_start = time.time()
 
@@ -50,15 +52,15 @@ def main(systems=23):
             "x_norm": float(np.linalg.norm(res.x)), "x_sample": res.x[rows].tolist(),
             "seconds": time.time() - t_start,
         })
-        tmp = OUT + ".tmp"
+        tmp = out + ".tmp"
         with open(tmp, "w") as fh:
             json.dump(rec, fh)
-        os.replace(tmp, OUT)
+        os.replace(tmp, out)
         print(len(rec["systems"]), res.mvs, res.cycles, res.relres_true, time.time() - t_start, flush=True)
 
     O.msstab_sequence(A, w.f(), w.x0(), w.tau, systems, w.s, w.ell, w.p_raw(), tol=w.tol, policy="once",
-                      on_solve=on_solve)
+                      replace_every=w.replace_every, on_solve=on_solve)
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 23)
+    main(int(sys.argv[1]) if len(sys.argv) > 1 else 23, sys.argv[2] if len(sys.argv) > 2 else OUT)

@@ -1,0 +1,160 @@
+"""The learned-initial-guess CNN on the GPU against its FP64 oracle.
+
+Both sides round the same operands to bfloat16 (weights, biases, inputs,
+hidden activations, upstream gradients) and accumulate wider (FP32 on the GPU,
+FP64 in the oracle).  A bfloat16 rounding can then land on either side of a
+rounding boundary for a few elements (the FP32 and FP64 pre-rounding values
+differ by ~1e-7 relative; bfloat16 spacing is 2^-8), so whole-network
+results are compared in norm: relative error <= 2e-3 for outputs and 5e-3 for
+gradients, far below the bfloat16 step and far above FP32 accumulation error.
+"""
+
+import numpy as np
+import pytest
+
+from oracle import cnn as C
+from paper_1604_06043_gb300 import problems as pb
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def M():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1604_06043_gb300 import build, msstab
+    build.build()
+    return msstab
+
+
+def _params(seed=5):
+    rng = np.random.default_rng(seed)
+    th = pb.cnn_init_params(seed)
+    th += 0.05 * rng.standard_normal(th.size)      # non-zero biases, generic weights
+    return th.astype(np.float32).astype(np.float64)
+
+
+def _t(a, dt=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dt, device=DEV)
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / np.linalg.norm(b)
+
+
+def test_forward_matches_oracle(M):
+    B, D = 2, 12
+    th = _params()
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal((B, 2, D, D, D)).astype(np.float32)
+    net = M.CNN((D, D, D), th, max_batch=B, crop=D, device=DEV)
+    out = net.forward(_t(x), B, D).cpu().numpy().reshape(B, 1, D, D, D)
+    ref = np.stack([C.forward(th, xb.astype(np.float64)) for xb in x])
+    assert _rel(out, ref) <= 2e-3
+    assert np.max(np.abs(out - ref)) <= 1e-2 * np.max(np.abs(ref))
+
+
+def test_gradient_matches_oracle(M):
+    B, D = 2, 10
+    th = _params(6)
+    rng = np.random.default_rng(2)
+    x = rng.standard_normal((B, 2, D, D, D)).astype(np.float32)
+    t = rng.standard_normal((B, 1, D, D, D)).astype(np.float32)
+    net = M.CNN((D, D, D), th, max_batch=B, crop=D, device=DEV)
+    g, loss = net.grad(_t(x), _t(t), B, D)
+    ref_loss, ref_g = C.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - ref_loss) <= 1e-4 * ref_loss
+    g = g.cpu().numpy()
+    o = 0
+    for ci, co in C.LAYERS:
+        n = co * ci * 27 + co
+        assert _rel(g[o:o + n], ref_g[o:o + n]) <= 5e-3, (ci, co)
+        o += n
+
+
+def test_adam_step_matches_oracle(M):
+    th = _params(7)
+    g = np.random.default_rng(3).standard_normal(th.size).astype(np.float32).astype(np.float64)
+    net = M.CNN((8, 8, 8), th, max_batch=1, crop=8, device=DEV)
+    net.adam_step(_t(g), 1e-3)
+    net.adam_step(_t(0.5 * g), 1e-3)
+    p = net.params().cpu().numpy()
+    r, m, v = C.adam_step(th, np.zeros_like(th), np.zeros_like(th), g, 1, lr=1e-3)
+    r, m, v = C.adam_step(r, m, v, 0.5 * g, 2, lr=1e-3)
+    assert np.max(np.abs(p - r)) <= 1e-6 * (np.max(np.abs(th)) + 1e-3)
+
+
+def test_training_reduces_loss_on_a_learnable_map(M):
+    # x_next - x_prev is a fixed stencil of (r0, x_prev): exactly representable
+    n = 16
+    K = np.zeros((1, 2, 3, 3, 3))
+    K[0, 0, 1, 1, 1], K[0, 1, 1, 1, 2], K[0, 1, 0, 1, 1] = 0.5, -0.3, 0.2
+    rng = np.random.default_rng(4)
+    net = M.CNN((n, n, n), pb.cnn_init_params(5), max_pairs=4, max_batch=4, crop=8, device=DEV)
+    for k in range(4):
+        r0 = rng.standard_normal(n ** 3)
+        xp = rng.standard_normal(n ** 3)
+        inp = np.stack([r0, xp]).reshape(2, n, n, n)
+        xn = xp + C.conv3d(inp, K, np.zeros(1)).reshape(-1)
+        net.add_pair(_t(r0, torch.float64), _t(xp, torch.float64), _t(xn, torch.float64))
+    net.fit_scales()
+    s = net.scales()
+    assert all(v > 0 for v in s)
+    origins = []
+    for it in range(60):
+        for bb in range(4):
+            origins.append([rng.integers(0, 4), rng.integers(0, n - 8 + 1), rng.integers(0, n - 8 + 1),
+                            rng.integers(0, n - 8 + 1)])
+    hist = net.train(np.array(origins), 4, 8, 3e-3)
+    assert np.isfinite(hist).all()
+    assert hist[-10:].mean() < 0.3 * hist[:3].mean()
+
+
+def test_infer_matches_oracle(M):
+    n = 12
+    th = _params(8)
+    rng = np.random.default_rng(5)
+    r0 = rng.standard_normal(n ** 3) * 50
+    xp = rng.standard_normal(n ** 3)
+    net = M.CNN((n, n, n), th, device=DEV, crop=8)
+    net.set_scales(2.0, 4.0)
+    delta = torch.empty(n ** 3, dtype=torch.float64, device=DEV)
+    net.infer(_t(r0, torch.float64), _t(xp, torch.float64), delta)
+    torch.cuda.synchronize()
+    # per-instance residual scale s_r = 1/RMS(r0); global s_x = 2, c = 4
+    s_r = np.float32(1.0 / np.sqrt(np.mean(r0 * r0)))
+    s_x, c = np.float32(2.0), np.float32(4.0)
+    inp = np.stack([(s_r * r0.astype(np.float32)), (s_x * xp.astype(np.float32))]).reshape(2, n, n, n)
+    ref = C.forward(th, inp.astype(np.float64)).reshape(-1) / (float(c) * float(s_r))
+    assert _rel(delta.cpu().numpy(), ref) <= 2e-3
+
+
+def test_select_guess_keeps_only_a_better_start(M):
+    w = pb.WORKLOADS["convdiff3d_24"]
+    A = w.matrix()
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV)
+    xp = w.x0()
+    b = xp / w.tau + w.f()
+    import scipy.sparse.linalg as spla
+    exact = spla.spsolve(A.to_scipy().tocsc(), b)
+    bt, xpt = _t(b, torch.float64), _t(xp, torch.float64)
+    x = torch.empty_like(xpt)
+    good = _t(exact - xp, torch.float64)
+    assert S.select_guess(bt, xpt, good, x)
+    np.testing.assert_allclose(x.cpu().numpy(), xp + (exact - xp), rtol=0, atol=1e-12 * np.abs(exact).max())
+    bad = _t(1e3 * np.random.default_rng(0).standard_normal(A.n), torch.float64)
+    assert not S.select_guess(bt, xpt, bad, x)
+    np.testing.assert_array_equal(x.cpu().numpy(), xp)
+    # scaled: x_prev + alpha delta with the residual-minimising alpha (1 for the exact correction)
+    used, alpha, red = S.select_guess_scaled(bt, xpt, good, x)
+    assert used and abs(alpha - 1.0) < 1e-8 and red < 1e-6   # sqrt(1 - cos^2): floor near sqrt(eps)
+    half = _t(0.5 * (exact - xp), torch.float64)
+    used, alpha, red = S.select_guess_scaled(bt, xpt, half, x)
+    assert used and abs(alpha - 2.0) < 1e-8
+    used, alpha, red = S.select_guess_scaled(bt, xpt, bad, x)
+    assert used and 0.0 < red <= 1.0
+    r = b - A.to_scipy() @ x.cpu().numpy()
+    r0 = b - A.to_scipy() @ xp
+    assert abs(np.linalg.norm(r) / np.linalg.norm(r0) - red) < 1e-6

@@ -82,12 +82,12 @@ def test_sequence_2d_matches_oracle(M, policy):
         assert not any(s[4] for s in g)
 
 
-@pytest.mark.parametrize("fmt", [0, 1])
-def test_sequence_3d_matches_oracle(M, fmt):
+@pytest.mark.parametrize("fmt,re", [(0, 0), (1, 0), (0, 1)])
+def test_sequence_3d_matches_oracle(M, fmt, re):
     w = pb.WORKLOADS["convdiff3d_33"]
     A = w.matrix()
-    g = _gpu_sequence(M, w, A, w.steps, spmv_format=fmt)
-    o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol)
+    g = _gpu_sequence(M, w, A, w.steps, spmv_format=fmt, replace_every=re)
+    o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol, replace_every=re)
     As = A.to_scipy()
     xprev = w.x0()
     for i, (gs, os_) in enumerate(zip(g, o.solves)):
@@ -112,6 +112,31 @@ def test_history_matches_oracle_cycle_by_cycle(M):
     np.testing.assert_array_equal(mvs, ref.mv_history)
     # rounding differences grow with the iteration; they stay far below the residual
     np.testing.assert_allclose(rel, ref.history, rtol=1e-6)
+
+
+def test_replace_every_cycle_history_matches_oracle(M):
+    # a stiff 48^3 system on which the plain recursion drifts past tol: with
+    # r := b - A x at each cycle end both sides follow the true residual
+    A = pb.convdiff((48, 48, 48), (20.0, 10.0, 5.0), tau=0.005)
+    b = pb.uniform(A.n, 2) / 0.005 + pb.uniform(A.n, 1)
+    x0 = pb.uniform(A.n, 2)
+    p_raw = pb.randn_cols(A.n, 8, 3)
+    S = M.Solver(A, 8, 4, p_raw, device=DEV, fetch_policy=M.FETCH_NEVER, replace_every=1)
+    x = _t(x0)
+    st = S.solve(_t(b), x, 1e-8)
+    rel, mvs = S.history()
+    ref = O.idrstab(A, b, x0, 8, 4, O.orthonormalize_mgs2(p_raw), tol=1e-8, replace_every=1)
+    assert st.status == 0 and st.mvs == ref.mvs and st.cycles == ref.cycles
+    np.testing.assert_array_equal(mvs, ref.mv_history)
+    # the true residuals of the two FP64 paths differ by what the drift of V
+    # from A U adds (level vectors of norm up to ||A||^4 ||r||, rounded in a
+    # different order): far below the residual early, of its size near 1e-8
+    np.testing.assert_allclose(rel[:2], ref.history[:2], rtol=1e-6)
+    assert np.max(np.abs(np.array(rel) - np.array(ref.history))) <= 1e-6
+    assert st.relres_true == pytest.approx(rel[-1], rel=1e-12) and st.relres_true <= 1e-8
+    r = b - A.to_scipy() @ x.cpu().numpy()
+    assert np.linalg.norm(r) / np.linalg.norm(b) == pytest.approx(st.relres_true, rel=1e-6)
+    S.close()
 
 
 # ---------------------------------------------------------------------------
