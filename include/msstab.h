@@ -76,9 +76,12 @@ typedef struct msstab_options {
                               paper's plain hand-over) */
   int64_t max_mvs;         /* products with A per solve; <= 0: min(100000, 20 sqrt(n) + 1 + s + 2l(s+1)) */
   double inner_tol;        /* FP32 inner: relative tolerance of each inner solve (tested on its
-                              recursive residual); <= 0: max(1e-5, 0.5 tol ||b|| / ||r_outer||).
+                              recursive residual); <= 0: max(1e-2, 0.5 tol ||b|| / ||r_outer||).
                               An inner solve also stops when its residual has not halved in 4
-                              cycles (the FP32 floor near kappa * 6e-8 is reached) */
+                              cycles (the FP32 floor near kappa * 6e-8 is reached).  A correction
+                              that does not reduce the FP64 residual is undone and the next inner
+                              solve restarts its basis; a second one in a row ends the solve with
+                              MSSTAB_ERR_MAXIT and the better x */
   int32_t spmv_format;     /* MSSTAB_FORMAT_SELL (default, SELL-32-sigma) or MSSTAB_FORMAT_CSR */
   int32_t sell_sigma;      /* SELL sorting window in rows (1 = no sorting, default; else a
                               multiple of 32) */
@@ -111,6 +114,9 @@ typedef struct msstab_stats {
   int32_t fetched;        /* 1 if this call wrote the recycle store */
   int32_t used_recycle;   /* 1 if this call started from recycled U,V */
   int32_t guess_used;     /* set by msstab_select_guess */
+  int32_t fp64_finish;    /* FP32_INNER: 1 if the FP32 corrections stalled and FP64 IDR(s)stab(l)
+                             finished the solve from the current x */
+  int32_t reserved_s;
   double t_ms[MSSTAB_K_COUNT];     /* per kernel family, when options.kernel_timing */
   int64_t n_launch[MSSTAB_K_COUNT];
 } msstab_stats;

@@ -553,7 +553,7 @@ msstab_status solve_fp64(msstab_t h, double tol, SolveOut& o) {
 }
 
 // FP32 inner M(s)stab on A/rho inside an FP64 defect-correction loop.
-msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) {
+msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out, int* fp64_finish) {
   const Ctx c = h->ctx();
   const int n = h->n;
   DevState* st = h->st;
@@ -565,6 +565,9 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
   int64_t outer = 0;
   double nb = -1.0;
   bool cont = false;   // continue the inner basis (U, V) of the previous outer iteration
+  double prev = 0.0;   // FP64 relres before the last correction
+  bool corrected = false, restored = false, need_fp64 = false;
+  int rejected = 0;
   o.status = MSSTAB_OK;
   for (;;) {
     // FP64 true residual
@@ -582,6 +585,21 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     const double relres = sigma / nb;
     hist.push_back(relres);
     hmv.push_back(o.mvs);
+    if (corrected && !restored && !(relres < prev)) {
+      // the last correction did not reduce the FP64 residual (an FP32 inner
+      // solve that stagnated or diverged): undo it, and restart the inner
+      // basis; a second failure in a row ends the solve
+      CK(cudaMemcpyAsync(w.X, w.XB2, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+      cont = false;
+      restored = true;
+      if (++rejected >= 2) {
+        need_fp64 = true;
+        break;
+      }
+      continue;   // the residual of the restored x (one more product)
+    }
+    if (!restored) rejected = 0;
+    restored = false;
     o.relres_true = relres;
     o.relres_rec = relres;
     if (!std::isfinite(relres)) {
@@ -590,7 +608,7 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     }
     if (relres <= tol) break;
     if (outer >= max_outer) {
-      o.status = MSSTAB_ERR_MAXIT;
+      need_fp64 = true;
       break;
     }
     // inner system (A/rho) d' = r/sigma in FP32; then x += (sigma/rho) d'
@@ -598,7 +616,7 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     CK(cudaMemsetAsync(v.X, 0, sizeof(float) * n, h->stream));
     // the FP32 true residual cannot go much below kappa * eps_32, so the inner
     // solves stop on their recursive residual; the FP64 loop checks the truth
-    const double itol = h->opt.inner_tol > 0 ? h->opt.inner_tol : std::max(1e-5, 0.5 * tol * nb / sigma);
+    const double itol = h->opt.inner_tol > 0 ? h->opt.inner_tol : std::max(1e-2, 0.5 * tol * nb / sigma);
     SolveCtl ctl{};
     ctl.tol = itol;
     ctl.max_mvs = default_max_mvs(h);
@@ -621,12 +639,33 @@ msstab_status solve_dc(msstab_t h, double tol, SolveOut& o, int64_t* outer_out) 
     o.cycles += io.cycles;
     o.fetched |= io.fetched;
     o.used_recycle |= io.used_recycle;
-    if (io.status == MSSTAB_ERR_NAN) {
-      o.status = MSSTAB_ERR_NAN;
+    if (io.status == MSSTAB_ERR_NAN) {   // x is untouched: finish in FP64
+      need_fp64 = true;
       break;
     }
+    CK(cudaMemcpyAsync(w.XB2, w.X, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
     LAUNCH(MSSTAB_K_OTHER, axpy_f32_into_f64(c, n, v.X, w.X, sigma / h->rho));
+    prev = relres;
+    corrected = true;
     outer += 1;
+  }
+  if (need_fp64) {
+    // the FP32 corrections stopped reducing the FP64 residual (or the outer
+    // budget is spent): FP64 IDR(s)stab(l) from the current x to tol
+    SolveCtl c64 = make_ctl(h, tol, true);
+    c64.use_recycle = false;
+    c64.want_fetch = false;
+    c64.record_history = false;
+    SolveOut o64;
+    CKS(idrstab<double>(h, h->w64, 0, c64, o64));
+    o.mvs += o64.mvs;
+    o.cycles += o64.cycles;
+    o.status = o64.status;
+    o.relres_true = o64.relres_true;
+    o.relres_rec = o64.relres_rec;
+    hist.push_back(o64.relres_true);
+    hmv.push_back(o.mvs);
+    *fp64_finish = 1;
   }
   h->hist = hist;
   h->hist_mvs = hmv;
@@ -658,8 +697,9 @@ msstab_status solve_common(msstab_t h, double tol, msstab_stats* st) {
   h->tm.on = h->opt.kernel_timing != 0;
   CK(cudaEventRecord(h->e0, h->stream));
   msstab_status rc;
+  int fp64_finish = 0;
   if (h->opt.precision == MSSTAB_PREC_FP32_INNER)
-    rc = solve_dc(h, tol, o, &outer);
+    rc = solve_dc(h, tol, o, &outer, &fp64_finish);
   else
     rc = solve_fp64(h, tol, o);
   if (rc != MSSTAB_OK) return rc;
@@ -674,6 +714,7 @@ msstab_status solve_common(msstab_t h, double tol, msstab_stats* st) {
     st->mvs_fp32 = h->mvs32 - m320;
     st->cycles = o.cycles;
     st->outer = outer;
+    st->fp64_finish = fp64_finish;
     st->launches = h->launches - l0;
     st->relres_true = o.relres_true;
     st->relres_rec = o.relres_rec;
@@ -860,7 +901,7 @@ static msstab_status create_impl(msstab_t h, int64_t n, int64_t nnz, const int32
 
   // workspaces: FP64 levels for the FP64 mode; FP32 levels for the inner mode
   const bool inner = h->opt.precision == MSSTAB_PREC_FP32_INNER;
-  CKS(alloc_work<double>(h, h->w64, !inner));
+  CKS(alloc_work<double>(h, h->w64, true));   // FP64 levels also serve the FP32-inner form's FP64 finish
   CKS(alloc_work<float>(h, h->w32, inner));
 
   // cut space: orthonormalise the raw basis (Cholesky QR twice) in FP64

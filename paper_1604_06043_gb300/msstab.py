@@ -59,6 +59,8 @@ class Stats(ctypes.Structure):
         ("fetched", ctypes.c_int32),
         ("used_recycle", ctypes.c_int32),
         ("guess_used", ctypes.c_int32),
+        ("fp64_finish", ctypes.c_int32),
+        ("reserved_s", ctypes.c_int32),
         ("t_ms", ctypes.c_double * 8),
         ("n_launch", ctypes.c_int64 * 8),
     ]

@@ -394,3 +394,27 @@ def test_fp32_inner_reaches_fp64_accuracy(M):
         assert np.linalg.norm(x - os_.x) <= 1e-6 * np.linalg.norm(os_.x)
         xprev = x
     assert g[0][3] == 1 and all(s[4] == 1 for s in g[1:])
+
+
+def test_fp32_inner_measured_form_and_fp64_finish(M):
+    # the form the benchmark measures (inner l = 1, Arnoldi start per inner
+    # solve), and the FP64 finish when the defect correction stops early
+    w = pb.WORKLOADS["convdiff3d_33"]
+    A = w.matrix()
+    As = A.to_scipy()
+    b = w.x0() / w.tau + w.f()
+    ref = O.idrstab(A, b, w.x0(), w.s, w.ell, O.orthonormalize_mgs2(w.p_raw()), tol=1e-10).x
+    for max_outer, finish in ((40, None), (1, 1)):
+        S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, precision=M.PREC_FP32_INNER, inner_ell=1,
+                     fetch_policy=M.FETCH_NEVER, max_outer=max_outer, replace_every=1)
+        x = _t(w.x0())
+        st = S.solve(_t(b), x, w.tol)
+        xn = x.cpu().numpy()
+        assert st.status == 0 and st.relres_true <= w.tol
+        assert np.linalg.norm(b - As @ xn) <= w.tol * np.linalg.norm(b) * 1.0001
+        assert np.linalg.norm(xn - ref) <= 1e-6 * np.linalg.norm(ref)
+        if finish is not None:
+            assert st.fp64_finish == finish and st.outer == 1 and st.mvs > st.mvs_fp32
+        else:
+            assert st.mvs_fp32 > 0.8 * st.mvs
+        S.close()
