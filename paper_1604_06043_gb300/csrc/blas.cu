@@ -40,14 +40,14 @@ struct Acc<double, N> {
 };
 
 template <int N>
-struct Acc<float, N> {
-  float hi[N], lo[N];
+struct Acc<float, N> {   // FP32 partials, widened exactly for the FP64 reductions
+  float v[N];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int i = 0; i < N; ++i) hi[i] = lo[i] = 0.f;
+    for (int i = 0; i < N; ++i) v[i] = 0.f;
   }
-  __device__ __forceinline__ void add(int i, float x, float y) { df_add_prod(hi[i], lo[i], x, y); }
-  __device__ __forceinline__ double get(int i) const { return (double)hi[i] + (double)lo[i]; }
+  __device__ __forceinline__ void add(int i, float x, float y) { v[i] = fmaf(x, y, v[i]); }
+  __device__ __forceinline__ double get(int i) const { return widen_f32(v[i]); }
 };
 
 // ---------------------------------------------------------------------------

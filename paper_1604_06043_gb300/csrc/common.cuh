@@ -83,20 +83,23 @@ struct SellMat {           // SELL-32-sigma: slice k holds rows perm[32k .. 32k+
 };
 
 // ---------------------------------------------------------------------------
-// compensated FP32 accumulation (FP32 vectors): the product is split exactly
-// (FMA gives its rounding error) and summed with TwoSum, so a thread's partial
-// dot product carries about twice the FP32 precision without using the FP64
-// pipe, which on this GPU runs at 1/64 of the FP32 rate.  The rounded-mode
-// intrinsics keep the compiler from contracting the error terms away.
+// FP32 partial sums into the FP64 reductions.  A thread's FP32 dot partial
+// (a dozen rows) is exact to about 1e-6 of its terms, the level of the FP32
+// vectors themselves; the block and grid reductions are FP64.  The widening
+// is done with integer operations: this GPU converts between FP32 and FP64 on
+// its FP64 unit (1/64 of the FP32 rate), where a conversion per accumulator
+// and warp costs as much as the whole FP32 row loop.  Zero, subnormal and
+// non-finite values (rare) take the converting instruction.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float a, float b) {
-  const float p = __fmul_rn(a, b);
-  const float e = __fmaf_rn(a, b, -p);
-  const float s = __fadd_rn(hi, p);
-  const float bp = __fsub_rn(s, hi);
-  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bp)), __fsub_rn(p, bp));
-  hi = s;
-  lo = __fadd_rn(lo, __fadd_rn(err, e));
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned e = (u >> 23) & 0xffu;
+  if ((u & 0x7fffffffu) == 0u) return __longlong_as_double((long long)((unsigned long long)u << 32));
+  if (e == 0u || e == 0xffu) return (double)f;
+  const unsigned long long d = ((unsigned long long)(u & 0x80000000u) << 32) |
+                               ((unsigned long long)(e + 896u) << 52) |
+                               ((unsigned long long)(u & 0x7fffffu) << 29);
+  return __longlong_as_double((long long)d);
 }
 
 // ---------------------------------------------------------------------------
@@ -162,9 +165,18 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], int m, double* smem
   if ((lane & LOW_MASK) == 0 && idx < m) smem_w[w * MAXRED + idx] = v[0];
   __syncthreads();
   if (threadIdx.x < m) {
-    double s = 0.0;
-    for (int j = 0; j < (int)(blockDim.x >> 5); ++j) s += smem_w[j * MAXRED + threadIdx.x];
-    red[threadIdx.x] = s;
+    // four independent chains over the warps (fixed order), then their sum
+    const int nw = (int)(blockDim.x >> 5);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
+    for (; j + 3 < nw; j += 4) {
+      s0 += smem_w[j * MAXRED + threadIdx.x];
+      s1 += smem_w[(j + 1) * MAXRED + threadIdx.x];
+      s2 += smem_w[(j + 2) * MAXRED + threadIdx.x];
+      s3 += smem_w[(j + 3) * MAXRED + threadIdx.x];
+    }
+    for (; j < nw; ++j) s0 += smem_w[j * MAXRED + threadIdx.x];
+    red[threadIdx.x] = (s0 + s1) + (s2 + s3);
   }
   __syncthreads();
 }

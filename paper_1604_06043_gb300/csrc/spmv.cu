@@ -19,6 +19,13 @@
 
 namespace msk {
 
+// Products run one 1024-thread block per SM (32 warps, as many as four blocks
+// of 256 would give): the grid reduction that follows every fused product then
+// combines 152 partials instead of 608, on the critical path of the next small
+// solve.
+constexpr int SNT = 1024;
+constexpr int SNWARP = SNT / 32;
+
 template <typename T>
 __device__ __forceinline__ T ro(const T* p) { return __ldg(p); }
 
@@ -43,7 +50,7 @@ __host__ __device__ constexpr int pow2_at_least(int v) { return v <= 1 ? 1 : (v 
 
 // Per-thread accumulators of the fused dot products: NP slots for P^T y (np <=
 // NP used), then y.y and b.b in fixed slots.  FP64 vectors accumulate in FP64;
-// FP32 vectors in compensated FP32 pairs (df_add_prod), read out as FP64.
+// FP32 vectors in FP32, widened exactly to FP64 for the block reduction.
 template <typename T, int NP>
 struct DotAcc;
 
@@ -60,13 +67,13 @@ struct DotAcc<double, NP> {
 
 template <int NP>
 struct DotAcc<float, NP> {
-  float hi[NP + 2], lo[NP + 2];
+  float v[NP + 2];
   __device__ __forceinline__ void zero() {
 #pragma unroll
-    for (int i = 0; i < NP + 2; ++i) hi[i] = lo[i] = 0.f;
+    for (int i = 0; i < NP + 2; ++i) v[i] = 0.f;
   }
-  __device__ __forceinline__ void add(int i, float x, float y) { df_add_prod(hi[i], lo[i], x, y); }
-  __device__ __forceinline__ double get(int i) const { return (double)hi[i] + (double)lo[i]; }
+  __device__ __forceinline__ void add(int i, float x, float y) { v[i] = fmaf(x, y, v[i]); }
+  __device__ __forceinline__ double get(int i) const { return widen_f32(v[i]); }
 };
 
 template <typename T, int NP>
@@ -85,7 +92,7 @@ __device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, Dot
 template <typename T, int NP>
 __device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<T, NP>& acc) {
   constexpr int M = pow2_at_least(NP + 2);
-  __shared__ double smem_w[NWARP * MAXRED];
+  __shared__ double smem_w[SNWARP * MAXRED];
   __shared__ double red[MAXRED];
   __shared__ int s_last;
   __shared__ EpiScratch ew;
@@ -100,7 +107,15 @@ __device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<T, NP>
     if (a.bdot && i == a.np + a.self) v = acc.get(NP + 1);
     fin[i] = v;
   }
-  block_reduce<M>(fin, m, smem_w, red);
+  // the s dots of a cycle's products fill 8 of the 16 slots: reduce only those
+  if constexpr (M > 8) {
+    if (m <= 8)
+      block_reduce<8>(reinterpret_cast<double(&)[8]>(fin), m, smem_w, red);
+    else
+      block_reduce<M>(fin, m, smem_w, red);
+  } else {
+    block_reduce<M>(fin, m, smem_w, red);
+  }
   if (grid_reduce(a.rs, 0, blockIdx.x, gridDim.x, m, red, &s_last)) {
     if (threadIdx.x < m) a.out[threadIdx.x] = red[threadIdx.x];
     __threadfence();
@@ -149,13 +164,13 @@ __device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __re
 // NP < 0: plain product; NP >= 0: also the reduction of up to NP dots with P,
 // y.y and b.b, and the epilogue.
 template <typename T, int NP>
-__global__ void __launch_bounds__(NT, 4) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
+__global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
   constexpr int NA = NP < 0 ? 0 : NP;
   DotAcc<T, NA> acc;
   acc.zero();
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * NWARP;
-  for (int sl = (blockIdx.x * NT + threadIdx.x) >> 5; sl < A.nslices; sl += nwarps) {
+  const int nwarps = gridDim.x * SNWARP;
+  for (int sl = (blockIdx.x * SNT + threadIdx.x) >> 5; sl < A.nslices; sl += nwarps) {
     const int w = ro(A.slice_w + sl);
     const int64_t base = (int64_t)ro(A.slice_ptr + sl) + lane;
     const T sum = sell_row<T>(A.col, A.val, a.x, base, w);
@@ -171,12 +186,12 @@ __global__ void __launch_bounds__(NT, 4) spmv_sell_kernel(SellMat<T> A, SpmvArgs
 }
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(NT, 4) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a) {
+__global__ void __launch_bounds__(SNT, 1) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T> a) {
   constexpr int NA = NP < 0 ? 0 : NP;
   DotAcc<T, NA> acc;
   acc.zero();
-  const int stride = gridDim.x * NT;
-  for (int row = blockIdx.x * NT + threadIdx.x; row < A.n; row += stride) {
+  const int stride = gridDim.x * SNT;
+  for (int row = blockIdx.x * SNT + threadIdx.x; row < A.n; row += stride) {
     const int beg = ro(A.row_ptr + row), end = ro(A.row_ptr + row + 1);
     T sum = T(0);
     for (int p = beg; p < end; ++p) sum = fma_t(ro(A.val + p), ro(a.x + ro(A.col + p)), sum);
@@ -190,7 +205,7 @@ __global__ void __launch_bounds__(NT, 4) spmv_csr_kernel(CsrMat<T> A, SpmvArgs<T
 template <typename K>
 static int max_grid(K kernel, const Ctx& c) {
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, NT, 0) != cudaSuccess || nb < 1) nb = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, SNT, 0) != cudaSuccess || nb < 1) nb = 1;
   int g = nb * c.sms;
   return g > MAXBLK ? MAXBLK : g;
 }
@@ -205,15 +220,15 @@ const float* pick_val<float>(const MatDesc& A, bool sell) { return sell ? A.sval
 template <typename T, int NP>
 static void launch_sell(const Ctx& c, const SellMat<T>& M, const SpmvArgs<T>& a) {
   static int cap = max_grid(spmv_sell_kernel<T, NP>, c);
-  const int64_t need = ((int64_t)M.nslices * 32 + NT - 1) / NT;
-  spmv_sell_kernel<T, NP><<<(int)(need < cap ? need : cap), NT, 0, c.stream>>>(M, a);
+  const int64_t need = ((int64_t)M.nslices * 32 + SNT - 1) / SNT;
+  spmv_sell_kernel<T, NP><<<(int)(need < cap ? need : cap), SNT, 0, c.stream>>>(M, a);
 }
 
 template <typename T, int NP>
 static void launch_csr(const Ctx& c, const CsrMat<T>& M, const SpmvArgs<T>& a) {
   static int cap = max_grid(spmv_csr_kernel<T, NP>, c);
-  const int64_t need = ((int64_t)M.n + NT - 1) / NT;
-  spmv_csr_kernel<T, NP><<<(int)(need < cap ? need : cap), NT, 0, c.stream>>>(M, a);
+  const int64_t need = ((int64_t)M.n + SNT - 1) / SNT;
+  spmv_csr_kernel<T, NP><<<(int)(need < cap ? need : cap), SNT, 0, c.stream>>>(M, a);
 }
 
 template <typename T>
@@ -423,15 +438,15 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
     return MSSTAB_ERR_CUDA;
   }
   int nb = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_csr_kernel<double, 16>, NT, 0) != cudaSuccess ||
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, spmv_csr_kernel<double, 16>, SNT, 0) != cudaSuccess ||
       nb < 1)
     nb = 1;
-  int64_t g = ((int64_t)n + NT - 1) / NT;
+  int64_t g = ((int64_t)n + SNT - 1) / SNT;
   if (g > (int64_t)nb * sms[dev]) g = (int64_t)nb * sms[dev];
   if (g > NOALLOC_MAX_BLOCKS) g = NOALLOC_MAX_BLOCKS;
   CsrMat<double> M{(int)n, d_row_ptr, d_col, d_val};
   SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs};
-  spmv_csr_kernel<double, 16><<<(int)g, NT, 0, st>>>(M, a);
+  spmv_csr_kernel<double, 16><<<(int)g, SNT, 0, st>>>(M, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     set_global_error(std::string("msstab_spmv_dot_noalloc: launch: ") + cudaGetErrorString(e));
