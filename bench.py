@@ -38,6 +38,10 @@ WORKLOAD = "convdiff3d_128"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_128.json")
 FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+# DRAM bytes (read + write) of one launch of the dominant kernel of the FP64
+# form, from one ncu capture of the current kernel at 128^3
+# (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md); None for other forms.
+NCU_TRAFFIC = {("fp64", "spmv_dot"): 341_992_448}
 
 
 def parse_args(argv=None):
@@ -47,6 +51,9 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--workload", default=WORKLOAD)
+    p.add_argument("--form", choices=["fp64", "fp32_inner", "idrstab"], default="fp64",
+                   help="the solver form of the main line: FP64 M(s)stab (default), the FP32-inner "
+                        "defect-correction form, or FP64 IDR(s)stab with an Arnoldi start per system")
     p.add_argument("--no-variants", action="store_true", help="skip the IDRstab and FP32-inner runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -422,7 +429,8 @@ def main(argv=None):
     f_np, x0_np = w.f(), w.x0()
     K, W = args.steps, args.warmup
 
-    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, kernel_timing=1, replace_every=w.replace_every)
+    form_opts = {"fp64": {}, "fp32_inner": FP32_INNER_OPTS(M), "idrstab": dict(fetch_policy=M.FETCH_NEVER)}[args.form]
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, kernel_timing=1, replace_every=w.replace_every, **form_opts)
     stream = torch.cuda.current_stream()
     f = torch.tensor(f_np, device=dev)
     x = torch.tensor(x0_np, device=dev)
@@ -458,7 +466,10 @@ def main(argv=None):
     launches = sum(t["launches"] for t in timed) + K          # + the right-hand-side launches
     replaced = sum(t["cycles"] for t in timed) if w.replace_every == 1 else \
         sum(t["cycles"] // w.replace_every for t in timed) if w.replace_every > 1 else 0
-    model, spmv_b = family_model(A, w.s, w.ell, cycles, K, replaced)
+    if args.form == "fp32_inner":     # inner cycles of M(s)stab(1) on FP32 vectors dominate the launches
+        model, spmv_b = family_model(A, w.s, 1, cycles, K, 0, vb=4)
+    else:
+        model, spmv_b = family_model(A, w.s, w.ell, cycles, K, replaced)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -483,23 +494,28 @@ def main(argv=None):
     if kd["fp64_frac_nominal"] > kd["hbm_frac"]:
         # FP64 FMA throughput, not HBM, binds this kernel on GB300
         roofline = {"kernel": dom, "bound": "alu", "achieved": kd["fp64_tflops"], "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s (FP64)", "frac": kd["fp64_frac_nominal"], "traffic": None,
+                    "unit": "TFLOP/s (FP64)", "frac": kd["fp64_frac_nominal"],
+                    "traffic": NCU_TRAFFIC.get((args.form, dom)),
                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
                     "hbm": {"achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s", "frac": kd["hbm_frac"]},
                     "share_of_step": share}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": kd["hbm_frac"], "traffic": None,
+                    "frac": kd["hbm_frac"], "traffic": NCU_TRAFFIC.get((args.form, dom)),
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                     "fp64_frac_of_nominal": kd["fp64_frac_nominal"], "share_of_step": share}
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": round(T / K, 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f64", "data": "synthetic (seeded generators; the paper's ocean data is not available)",
+            "dtype": "f32+f64" if args.form == "fp32_inner" else "f64",
+            "data": "synthetic (seeded generators; the paper's ocean data is not available)",
             "config": {"workload": f"{w.name}: 3D convection-diffusion, 7-point FD on a 128^3 grid (N={A.n}, "
                                    f"nnz={A.nnz}), beta=(20,10,5), implicit Euler tau={w.tau}, systems "
                                    f"{W + 1}..{W + K} of the sequence",
-                       "method": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
+                       "method": {"fp64": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
+                                  "fp32_inner": f"FP32-inner M({w.s})stab(1) with FP64 defect correction, SELL-32",
+                                  "idrstab": f"IDR({w.s})stab({w.ell}), Arnoldi start per system, FP64, SELL-32"}[args.form],
+                       "true_residual": "replaced every cycle" if w.replace_every == 1 else "checked at convergence",
                        "tol": w.tol, "l2": "inputs larger than L2 (matrix 0.18 GB + ~90 vectors of 16.8 MB), no flush",
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "mvs_per_system": round(statistics.mean(mvs), 2), "cycles_per_system": round(cycles / K, 3),
@@ -511,7 +527,7 @@ def main(argv=None):
     # end to end through the public API with host buffers, on the same systems:
     # a fresh handle, the same warm-up, then the same K systems via msstab_solve_host
     if not args.no_e2e:
-        H = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
+        H = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every, **form_opts)
         xh = x0_np.copy()
         for _ in range(W):
             H.solve_host(xh / w.tau + f_np, xh, w.tol)
