@@ -315,24 +315,32 @@ def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300,
     r0 = torch.empty_like(x)
     nrm = torch.zeros(2, dtype=torch.float64, device=dev)
     D = min(32, w.shape[0])
-    net = M.CNN(w.shape, pb.cnn_init_params(), max_pairs=train_steps, max_batch=batch, crop=D, device=dev)
+    nets = {}
+    for loss in ("mse", "operator"):
+        nets[loss] = M.CNN(w.shape, pb.cnn_init_params(), max_pairs=train_steps, max_batch=batch, crop=D, device=dev)
+    # the operator-weighted loss uses the 7-point row of A at the grid centre
+    Kst = pb.row_stencil(A, w.shape, tuple(n // 2 for n in w.shape))
+    nets["operator"].set_loss_stencil(Kst / np.abs(Kst).max())
     for _ in range(train_steps):
         S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
         xp = x.clone()
         S.op_residual(b, x, r0, nrm)
         S.solve(b, x, w.tol)
-        net.add_pair(r0, xp, x)
-    net.fit_scales()
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    hist = net.train(pb.cnn_crop_batches(train_steps, w.shape, D, batch, iters), batch, D, lr)
-    torch.cuda.synchronize()
-    train_s = time.perf_counter() - t0
-    x_start = x.clone()
+        for net_ in nets.values():
+            net_.add_pair(r0, xp, x)
+    train = {}
+    for name_, net_ in nets.items():
+        net_.fit_scales()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hist = net_.train(pb.cnn_crop_batches(train_steps, w.shape, D, batch, iters), batch, D, lr)
+        torch.cuda.synchronize()
+        train[name_] = {"seconds": round(time.perf_counter() - t0, 3), "loss_first": float(np.mean(hist[:5])),
+                        "loss_last": float(np.mean(hist[-20:]))}
     S.close()
-    out = {"train": {"pairs": train_steps, "iters": iters, "batch": batch, "crop": D, "seconds": round(train_s, 3),
-                     "loss_first": float(np.mean(hist[:5])), "loss_last": float(np.mean(hist[-20:]))},
+    out = {"train": {"pairs": train_steps, "iters": iters, "batch": batch, "crop": D, "losses": train},
            "systems": f"{train_steps + 1}..{train_steps + K}"}
+    net = nets["mse"]
 
     def run(precision, mode):
         opts = FP32_INNER_OPTS(M) if precision == M.PREC_FP32_INNER else {}
@@ -353,8 +361,8 @@ def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300,
             extra = 0
             if mode != "plain":
                 V.op_residual(b, xs, r0, nrm)
-                net.infer(r0, xs, delta)
-                if mode == "rule":
+                (nets["operator"] if mode.endswith("_op") else net).infer(r0, xs, delta)
+                if mode.startswith("rule"):
                     u = V.select_guess(b, xs, delta, xg)
                 else:
                     u, a, rr = V.select_guess_scaled(b, xs, delta, xg)
@@ -381,10 +389,18 @@ def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300,
     out["fp64_plain"] = plain
     out["fp64_guess_rule"] = run(M.PREC_FP64, "rule")
     out["fp64_guess_scaled"] = run(M.PREC_FP64, "scaled")
+    out["fp64_guess_rule_op"] = run(M.PREC_FP64, "rule_op")
+    out["fp64_guess_scaled_op"] = run(M.PREC_FP64, "scaled_op")
+    out["fp32_inner_plain"] = run(M.PREC_FP32_INNER, "plain")
     out["fp32_inner_guess_rule"] = run(M.PREC_FP32_INNER, "rule")
-    for k in ("fp64_guess_rule", "fp64_guess_scaled", "fp32_inner_guess_rule"):
-        out[k]["mvs_saved_per_system"] = round(plain["mvs_per_system"] - out[k]["mvs_per_system"], 2)
-    net.close()
+    out["fp32_inner_guess_rule_op"] = run(M.PREC_FP32_INNER, "rule_op")
+    for k in list(out):
+        if k.startswith("fp64_guess"):
+            out[k]["mvs_saved_per_system"] = round(plain["mvs_per_system"] - out[k]["mvs_per_system"], 2)
+        if k.startswith("fp32_inner_guess"):
+            out[k]["mvs_saved_per_system"] = round(out["fp32_inner_plain"]["mvs_per_system"] - out[k]["mvs_per_system"], 2)
+    for net_ in nets.values():
+        net_.close()
     return out
 
 

@@ -311,6 +311,16 @@ msstab_status msstab_cnn_set_scales(msstab_cnn_t h, float s_x, float c);
 msstab_status msstab_cnn_get_scales(msstab_cnn_t h, float* scales2);
 msstab_status msstab_cnn_fit_scales(msstab_cnn_t h);
 
+/* Loss of training and msstab_cnn_grad.  k27 NULL (default): the mean of
+ * (out - t)^2.  Else a host array of 27 coefficients K[dz+1][dy+1][dx+1]
+ * (dx fastest): the mean of (K * (out - t))^2, K * e the cross-correlation
+ * over each crop with zero padding.  With K a row stencil of A (any scale)
+ * this weights the error of the predicted correction by the operator, i.e.
+ * trains for a small residual A (x_guess - x^(i+1)) of the guess rather than
+ * a small error; the stencil step runs in FP32.  Errors: INVALID_ARG for a
+ * zero or non-finite stencil. */
+msstab_status msstab_cnn_set_loss_stencil(msstab_cnn_t h, const double* k27);
+
 /* Store a training pair: r0 = b^(i+1) - A x^(i) and x^(i) -> x^(i+1) - x^(i)
  * (FP64 device vectors of the grid). */
 msstab_status msstab_cnn_add_pair(msstab_cnn_t h, const double* d_r0, const double* d_x_prev,

@@ -126,20 +126,33 @@ def forward(theta: np.ndarray, x: np.ndarray, keep: bool = False, rounding: bool
     return (h, cache) if keep else h
 
 
-def loss_and_grad(theta: np.ndarray, xb: np.ndarray, tb: np.ndarray, rounding: bool = True):
+def loss_and_grad(theta: np.ndarray, xb: np.ndarray, tb: np.ndarray, rounding: bool = True,
+                  stencil: np.ndarray = None):
     """Mean squared error over a batch (B, 2, ...) -> (B, 1, ...) and its
     gradient with respect to the (FP32 master) parameters; the convolutions
-    use bfloat16-rounded weights, inputs and upstream gradients."""
+    use bfloat16-rounded weights, inputs and upstream gradients.
+
+    With ``stencil`` (3, 3, 3), the error e = out - t is weighted by the
+    operator first: the loss is the mean of (K * e)^2, K * e the
+    cross-correlation with zero padding (for K taken from a row of A, the
+    residual A e of the guess on the crop's interior).  The stencil step is
+    exact here; the CUDA path does it in FP32."""
     q = bf16 if rounding else _identity
     params = unpack(q(theta))
     grads = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
     total = 0.0
     count = tb.size
+    K = None if stencil is None else np.asarray(stencil, dtype=np.float64).reshape(1, 1, 3, 3, 3)
     for x, t in zip(xb, tb):
         out, cache = forward(theta, x, keep=True, rounding=rounding)
         diff = out - t
-        total += float((diff * diff).sum())
-        g = 2.0 * diff / count
+        if K is None:
+            total += float((diff * diff).sum())
+            g = 2.0 * diff / count
+        else:
+            s = conv3d(diff, K, np.zeros(1))
+            total += float((s * s).sum())
+            g = conv3d_backward(diff, K, 2.0 * s / count)[0]
         for li in range(len(params) - 1, -1, -1):
             h, z = cache[li]
             W, _ = params[li]

@@ -278,6 +278,65 @@ __global__ void loss_kernel(const float* out, const float* t, int64_t n, double 
   }
 }
 
+// Operator-weighted loss: s = K * (out - t) on each D^3 crop (cross-
+// correlation, zero outside the crop), per-block partial sums of s^2.
+__global__ void stencil_fwd_kernel(const float* out, const float* t, int B, int D, const float* k27, float* s,
+                                   double* partial) {
+  __shared__ double red[32];
+  __shared__ float k[27];
+  if (threadIdx.x < 27) k[threadIdx.x] = k27[threadIdx.x];
+  __syncthreads();
+  const int64_t n = (int64_t)B * D * D * D;
+  double acc2 = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), y = (int)((i / D) % D), z = (int)((i / ((int64_t)D * D)) % D);
+    const int64_t base = i - x - (int64_t)y * D - (int64_t)z * D * D;
+    float v = 0.f;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const float kk = k[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+          const int zz = z + dz, yy = y + dy, xx = x + dx;
+          if (kk == 0.f || zz < 0 || zz >= D || yy < 0 || yy >= D || xx < 0 || xx >= D) continue;
+          const int64_t j = base + ((int64_t)zz * D + yy) * D + xx;
+          v = fmaf(kk, out[j] - t[j], v);
+        }
+    s[i] = v;
+    acc2 += (double)v * v;
+  }
+  for (int o = 16; o > 0; o >>= 1) acc2 += __shfl_xor_sync(0xffffffffu, acc2, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc2;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tot = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += red[w];
+    partial[blockIdx.x] = tot;
+  }
+}
+
+// g = bf16((2 / count) K^T * s): the gradient of mean(s^2) with respect to out
+__global__ void stencil_bwd_kernel(const float* s, int B, int D, const float* k27, double inv_count,
+                                   __nv_bfloat16* g) {
+  __shared__ float k[27];
+  if (threadIdx.x < 27) k[threadIdx.x] = k27[threadIdx.x];
+  __syncthreads();
+  const int64_t n = (int64_t)B * D * D * D;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int x = (int)(i % D), y = (int)((i / D) % D), z = (int)((i / ((int64_t)D * D)) % D);
+    const int64_t base = i - x - (int64_t)y * D - (int64_t)z * D * D;
+    float v = 0.f;
+    for (int dz = -1; dz <= 1; ++dz)
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          const float kk = k[(dz + 1) * 9 + (dy + 1) * 3 + (dx + 1)];
+          const int zz = z - dz, yy = y - dy, xx = x - dx;   // the rows whose tap (dz, dy, dx) reads i
+          if (kk == 0.f || zz < 0 || zz >= D || yy < 0 || yy >= D || xx < 0 || xx >= D) continue;
+          v = fmaf(kk, s[base + ((int64_t)zz * D + yy) * D + xx], v);
+        }
+    g[i] = __float2bfloat16_rn((float)(2.0 * (double)v * inv_count));
+  }
+}
+
 // bf16 copies of the weights (and transposed, flipped copies for the data
 // gradient: wt[ci][co][26 - tap] = w[co][ci][tap]) and bf16-rounded biases
 __global__ void quantize_kernel(const float* theta, __nv_bfloat16* wq, __nv_bfloat16* wt, float* bq, int ci, int co) {
@@ -399,6 +458,9 @@ struct msstab_cnn_s {
   float* z[NL] = {};            // pre-activation of layer l
   __nv_bfloat16* dz[NL] = {};   // gradient of the pre-activation of layer l (bf16)
   float* tgt = nullptr;
+  float* kst = nullptr;         // operator stencil of the loss (27 floats), or unused
+  bool use_stencil = false;
+  float* sbuf = nullptr;        // K * (out - t) of the batch
   float* partials = nullptr;
   double* dpart = nullptr;
   double* h_small = nullptr;
@@ -483,7 +545,13 @@ msstab_status backward_batch(msstab_cnn_t h, int B, int D, double* loss) {
   cudaStream_t st = h->stream;
   const int64_t n = (int64_t)B * D * D * D;
   const int lg = grid1(n) < 1024 ? grid1(n) : 1024;
-  loss_kernel<<<lg, 256, 0, st>>>(h->z[3], h->tgt, n, 1.0 / (double)n, h->dz[3], h->dpart);
+  if (h->use_stencil) {
+    stencil_fwd_kernel<<<lg, 256, 0, st>>>(h->z[3], h->tgt, B, D, h->kst, h->sbuf, h->dpart);
+    CCK(cudaGetLastError());
+    stencil_bwd_kernel<<<lg, 256, 0, st>>>(h->sbuf, B, D, h->kst, 1.0 / (double)n, h->dz[3]);
+  } else {
+    loss_kernel<<<lg, 256, 0, st>>>(h->z[3], h->tgt, n, 1.0 / (double)n, h->dz[3], h->dpart);
+  }
   CCK(cudaGetLastError());
   int nb = 0;
   // layer 3 (16 -> 1)
@@ -583,6 +651,8 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
     CKC(calloc_(h, &h->dz[l], (size_t)CO_[l] * bv));
   }
   CKC(calloc_(h, &h->tgt, bv));
+  CKC(calloc_(h, &h->sbuf, bv));
+  CKC(calloc_(h, &h->kst, 27));
   const int64_t tiles = ((crop + TX - 1) / TX) * (int64_t)((crop + TY - 1) / TY) * ((crop + TZ - 1) / TZ) * max_batch;
   CKC(calloc_(h, &h->partials, (size_t)tiles * (16 * 16 * 27 + 16)));
   CKC(calloc_(h, &h->dpart, 4096));
@@ -636,6 +706,26 @@ msstab_status msstab_cnn_set_scales(msstab_cnn_t h, float s_x, float c) {
   if (!h || !(s_x > 0.f) || !(c > 0.f)) return cfail(h, MSSTAB_ERR_INVALID_ARG, "scales must be positive");
   h->scale[0] = s_x;
   h->scale[1] = c;
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_cnn_set_loss_stencil(msstab_cnn_t h, const double* k27) {
+  if (!h) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL handle");
+  if (!k27) {
+    h->use_stencil = false;
+    return MSSTAB_OK;
+  }
+  float k[27];
+  bool any = false;
+  for (int i = 0; i < 27; ++i) {
+    if (!std::isfinite(k27[i])) return cfail(h, MSSTAB_ERR_INVALID_ARG, "stencil entries must be finite");
+    k[i] = (float)k27[i];
+    any |= k[i] != 0.f;
+  }
+  if (!any) return cfail(h, MSSTAB_ERR_INVALID_ARG, "stencil is zero");
+  CCK(cudaMemcpyAsync(h->kst, k, sizeof(k), cudaMemcpyHostToDevice, h->stream));
+  CCK(cudaStreamSynchronize(h->stream));
+  h->use_stencil = true;
   return MSSTAB_OK;
 }
 

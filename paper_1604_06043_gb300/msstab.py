@@ -116,6 +116,7 @@ _SIGS = {
     "msstab_cnn_get_params": (_I32, [_P, _P]),
     "msstab_cnn_set_params": (_I32, [_P, _P]),
     "msstab_cnn_set_scales": (_I32, [_P, ctypes.c_float, ctypes.c_float]),
+    "msstab_cnn_set_loss_stencil": (_I32, [_P, _P]),
     "msstab_cnn_get_scales": (_I32, [_P, _P]),
     "msstab_cnn_fit_scales": (_I32, [_P]),
     "msstab_cnn_add_pair": (_I32, [_P, _P, _P, _P]),
@@ -384,6 +385,15 @@ class CNN:
 
     def set_scales(self, s_x, c):
         self._chk(load().msstab_cnn_set_scales(self._h, s_x, c))
+
+    def set_loss_stencil(self, k27=None):
+        """Operator-weighted loss with the 3x3x3 stencil k27 (host array, any
+        scale), or the plain mean squared error for None."""
+        if k27 is None:
+            self._chk(load().msstab_cnn_set_loss_stencil(self._h, None))
+            return
+        k = np.ascontiguousarray(np.asarray(k27, dtype=np.float64).reshape(27))
+        self._chk(load().msstab_cnn_set_loss_stencil(self._h, k.ctypes.data))
 
     def scales(self):
         out = (ctypes.c_float * 2)()

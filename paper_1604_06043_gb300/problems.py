@@ -192,6 +192,25 @@ def cnn_init_params(seed: int = SEED_CNN) -> np.ndarray:
     return np.concatenate(parts)
 
 
+def row_stencil(A: CSR, shape: tuple, point: tuple) -> np.ndarray:
+    """The 3x3x3 stencil of row `point` (z, y, x) of a matrix on the grid
+    `shape` (x fastest): K[dz+1, dy+1, dx+1] = a(point, point + (dz, dy, dx)).
+    Entries reaching beyond one cell raise."""
+    nz, ny, nx = shape if len(shape) == 3 else (1,) + tuple(shape)
+    z, y, x = point
+    row = (z * ny + y) * nx + x
+    K = np.zeros((3, 3, 3))
+    for p in range(A.row_ptr[row], A.row_ptr[row + 1]):
+        c = int(A.col[p])
+        cz, rem = divmod(c, ny * nx)
+        cy, cx = divmod(rem, nx)
+        dz, dy, dx = cz - z, cy - y, cx - x
+        if max(abs(dz), abs(dy), abs(dx)) > 1:
+            raise ValueError("row reaches beyond the 3x3x3 neighbourhood")
+        K[dz + 1, dy + 1, dx + 1] = A.val[p]
+    return K
+
+
 def crop_origins(shape, crop: int, count: int, seed: int) -> np.ndarray:
     """count random crop origins (z, y, x) of a crop^3 box inside a grid of the
     given (x, y, z) shape, as an int32 array (count, 3)."""

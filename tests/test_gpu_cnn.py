@@ -74,6 +74,31 @@ def test_gradient_matches_oracle(M):
         o += n
 
 
+def test_operator_weighted_gradient_matches_oracle(M):
+    B, D = 2, 10
+    th = _params(9)
+    rng = np.random.default_rng(7)
+    x = rng.standard_normal((B, 2, D, D, D)).astype(np.float32)
+    t = rng.standard_normal((B, 1, D, D, D)).astype(np.float32)
+    A = pb.convdiff((12, 12, 12), (20.0, 10.0, 5.0), tau=0.005)
+    K = pb.row_stencil(A, (12, 12, 12), (6, 6, 6))
+    K = K / np.abs(K).max()
+    net = M.CNN((D, D, D), th, max_batch=B, crop=D, device=DEV)
+    net.set_loss_stencil(K)
+    g, loss = net.grad(_t(x), _t(t), B, D)
+    ref_loss, ref_g = C.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64), stencil=K)
+    assert abs(loss - ref_loss) <= 1e-4 * ref_loss
+    g = g.cpu().numpy()
+    o = 0
+    for ci, co in C.LAYERS:
+        n = co * ci * 27 + co
+        assert _rel(g[o:o + n], ref_g[o:o + n]) <= 5e-3, (ci, co)
+        o += n
+    net.set_loss_stencil(None)          # back to the mean squared error
+    g2, loss2 = net.grad(_t(x), _t(t), B, D)
+    assert abs(loss2 - C.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64))[0]) <= 1e-4 * loss2
+
+
 def test_adam_step_matches_oracle(M):
     th = _params(7)
     g = np.random.default_rng(3).standard_normal(th.size).astype(np.float32).astype(np.float64)

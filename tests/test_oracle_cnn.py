@@ -99,6 +99,36 @@ def test_network_gradient_finite_differences():
         assert abs((lp - lm) / (2 * eps) - grad[i]) <= 1e-5 * (1e-3 + abs(grad[i]))
 
 
+def test_stencil_loss_is_operator_residual_and_gradient_checks():
+    # with K the 7-point row of A, the loss is mean((A e)^2) on the crop
+    # interior (zero padding outside), and its gradient passes finite differences
+    rng = np.random.default_rng(6)
+    A = pb.convdiff((6, 6, 6), (20.0, 10.0, 5.0), tau=0.005)
+    K = pb.row_stencil(A, (6, 6, 6), (3, 3, 3))
+    assert np.count_nonzero(K) == 7 and K[1, 1, 1] == A.to_dense()[3 * 36 + 3 * 6 + 3, 3 * 36 + 3 * 6 + 3]
+    e = rng.standard_normal((1, 6, 6, 6))
+    s = C.conv3d(e, K.reshape(1, 1, 3, 3, 3), np.zeros(1))
+    Ae = (A.to_dense() @ e.reshape(-1)).reshape(6, 6, 6)
+    # equal at every point: Dirichlet rows lack the outside neighbours, as the padding does
+    np.testing.assert_allclose(s[0], Ae, rtol=1e-12, atol=1e-9 * np.abs(Ae).max())
+    theta = pb.cnn_init_params(5) + 0.01 * rng.standard_normal(C.n_params())
+    xb = rng.standard_normal((2, 2, 4, 4, 4))
+    tb = rng.standard_normal((2, 1, 4, 4, 4))
+    Kn = K / np.abs(K).max()
+    loss, grad = C.loss_and_grad(theta, xb, tb, rounding=False, stencil=Kn)
+    out = np.stack([C.forward(theta, x, rounding=False) for x in xb])
+    s = np.stack([C.conv3d(o - tt, Kn.reshape(1, 1, 3, 3, 3), np.zeros(1)) for o, tt in zip(out, tb)])
+    assert loss == pytest.approx(float((s * s).sum()) / tb.size, rel=1e-12)
+    eps = 1e-6
+    for i in rng.choice(C.n_params(), size=12, replace=False):
+        th = theta.copy()
+        th[i] += eps
+        lp, _ = C.loss_and_grad(th, xb, tb, rounding=False, stencil=Kn)
+        th[i] -= 2 * eps
+        lm, _ = C.loss_and_grad(th, xb, tb, rounding=False, stencil=Kn)
+        assert abs((lp - lm) / (2 * eps) - grad[i]) <= 1e-5 * (1e-3 + abs(grad[i]))
+
+
 def test_param_count_and_layout():
     assert C.n_params() == 2 * 16 * 27 + 16 + 2 * (16 * 16 * 27 + 16) + 16 * 27 + 1
     theta = pb.cnn_init_params(5)
