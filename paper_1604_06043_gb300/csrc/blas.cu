@@ -228,8 +228,10 @@ struct TauArgs {
   RedScratch rs;
 };
 
-template <typename T>
-__global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
+// L: compile-time bound on the degree l (1, 2, 4 or 8): level arrays of L + 2
+// entries, so that the FP32 inner form (l = 1) keeps few registers.
+template <typename T, int L>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs<T> a) {
   __shared__ T tau[LMAX];
   __shared__ EpiScratch ew;
   __shared__ double smem_w[NWARP * MAXRED];
@@ -248,7 +250,7 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
   // Two rows per iteration; every load of both rows (levels, x, and the P
   // entries of the projection) is issued before any arithmetic, so that
   // enough bytes are in flight per SM (this kernel runs 2 blocks per SM).
-  auto load_row = [&](int row, T (&lv)[LMAX + 2], T (&pv)[SMAX], T& xv) {
+  auto load_row = [&](int row, T (&lv)[L + 2], T (&pv)[SMAX], T& xv) {
     if (a.proj) {
 #pragma unroll
       for (int c = 0; c < SMAX; ++c) {
@@ -261,7 +263,7 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
       if (a.do_update) {
         xv = a.x[row];
 #pragma unroll
-        for (int i = 1; i <= LMAX; ++i) {
+        for (int i = 1; i <= L; ++i) {
           if (i > a.ell) break;
           lv[i] = a.R[(int64_t)i * ld + row];                         // r^(i)
         }
@@ -272,20 +274,20 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
       if (a.do_update) {
         lv[0] = a.V[(int64_t)q * ld + row];                           // v_q^(-1)
 #pragma unroll
-        for (int i = 1; i <= LMAX; ++i) {
+        for (int i = 1; i <= L; ++i) {
           if (i > a.ell) break;
           lv[i + 1] = a.V[((int64_t)(i + 1) * a.s + q) * ld + row];   // v_q^(i)
         }
       }
     }
   };
-  auto update_row = [&](int row, T (&lv)[LMAX + 2], const T (&pv)[SMAX], T xv) {
+  auto update_row = [&](int row, T (&lv)[L + 2], const T (&pv)[SMAX], T xv) {
     T out;
     if (t == 0) {
       T r = lv[0];
       if (a.do_update) {
 #pragma unroll
-        for (int i = 1; i <= LMAX; ++i) {
+        for (int i = 1; i <= L; ++i) {
           if (i > a.ell) break;
           r -= tau[i - 1] * lv[i];
           xv += tau[i - 1] * lv[i - 1];
@@ -300,7 +302,7 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
       if (a.do_update) {
         T vnew = lv[1], unew = lv[0];
 #pragma unroll
-        for (int i = 1; i <= LMAX; ++i) {
+        for (int i = 1; i <= L; ++i) {
           if (i > a.ell) break;
           vnew -= tau[i - 1] * lv[i + 1];
           unew -= tau[i - 1] * lv[i];
@@ -323,7 +325,7 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
   int row = chunk * NT + threadIdx.x;
   if constexpr (sizeof(T) == 4) {   // FP64 keeps one row: two would spill registers
     for (; row + stride < a.n; row += 2 * stride) {
-      T lv0[LMAX + 2], lv1[LMAX + 2], pv0[SMAX], pv1[SMAX];
+      T lv0[L + 2], lv1[L + 2], pv0[SMAX], pv1[SMAX];
       T x0 = T(0), x1 = T(0);
       load_row(row, lv0, pv0, x0);
       load_row(row + stride, lv1, pv1, x1);
@@ -332,7 +334,7 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
     }
   }
   for (; row < a.n; row += stride) {
-    T lv0[LMAX + 2], pv0[SMAX];
+    T lv0[L + 2], pv0[SMAX];
     T x0 = T(0);
     load_row(row, lv0, pv0, x0);
     update_row(row, lv0, pv0, x0);
@@ -361,19 +363,31 @@ __global__ void __launch_bounds__(NT, 2) tau_kernel(TauArgs<T> a) {
   if (threadIdx.x < 32) run_epilogue(a.epi, ew);
 }
 
-template <typename T>
-cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
-                       const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi) {
-  static int cap = max_grid(tau_kernel<T>, c, MAXBLK);
-  const int nt = s + 1;
-  int64_t chunks = (n + NT - 1) / NT;
+template <typename T, int L>
+static void launch_tau(const Ctx& c, const TauArgs<T>& a) {
+  static int cap = max_grid(tau_kernel<T, L>, c, MAXBLK);
+  const int nt = a.s + 1;
+  int64_t chunks = (a.n + NT - 1) / NT;
   int64_t capc = cap / nt;
   if (capc < 1) capc = 1;
   if (chunks > capc) chunks = capc;
   if (chunks < 1) chunks = 1;
+  tau_kernel<T, L><<<(int)(chunks * nt), NT, 0, c.stream>>>(a);
+}
+
+template <typename T>
+cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
+                       const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
+                       Epi epi) {
   TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs};
-  tau_kernel<T><<<(int)(chunks * nt), NT, 0, c.stream>>>(a);
+  if (ell <= 1)
+    launch_tau<T, 1>(c, a);
+  else if (ell <= 2)
+    launch_tau<T, 2>(c, a);
+  else if (ell <= 4)
+    launch_tau<T, 4>(c, a);
+  else
+    launch_tau<T, LMAX>(c, a);
   return cudaGetLastError();
 }
 

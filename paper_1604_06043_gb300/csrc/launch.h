@@ -48,9 +48,16 @@ double spmv_bytes(const MatDesc& A, int prec);
 // y = A x  (b == NULL) or y = b - A x; with np > 0: out[c] = P_c . y for
 // c < np (P columns at P + c*ldp), then out[np] = y.y if self, then b.b if
 // bdot.  The last block runs the epilogue.
+// Pil (optional): the same P interleaved by row, Pil[row * sp + c], rows on
+// 16-byte boundaries (sp a multiple of 16 / sizeof(T)); the SELL kernel then
+// loads a row's P entries with vector loads issued with the matrix loads.
 template <typename T>
 cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
-                 int np, int self, int bdot, double* out, Epi epi);
+                 int np, int self, int bdot, double* out, Epi epi, const T* Pil = nullptr, int sp = 0);
+
+// Pil[row * sp + c] = P[c * ldp + row] (c < s), zero padding up to sp.
+template <typename T>
+cudaError_t interleave_rows(const Ctx& c, int n, int s, const T* P, int64_t ldp, int sp, T* Pil);
 
 // Multi-dot: for targets t < nt: out[t*ostride + c] = X_t . Y_c (c < ny) and,
 // if self, out[t*ostride + ny] = X_t . X_t.  Column pointers are given

@@ -37,6 +37,8 @@ struct Work {
   T* Urec = nullptr;  // recycle store
   T* Vrec = nullptr;
   T* P = nullptr;     // orthonormal cut-space basis
+  T* Pil = nullptr;   // P interleaved by row (row stride sp), for the fused products
+  int sp = 0;
   bool has_rec = false;
 };
 
@@ -412,13 +414,13 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     for (int k = 0; k < ell; ++k) {
       LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
       LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
-                                        &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0)));
+                                        &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp));
       for (int q = 0; q < s; ++q) {
         LAUNCH(MSSTAB_K_ETA, eta_eager<T>(c, n, s, w.R, w.V, ld, k, q, &st->eta[(k * SMAX + q) * SMAX]));
         Epi next = q + 1 < s ? epi_of(EPI_ETA, k, q + 1)
                              : (k + 1 < ell ? epi_of(EPI_GAMMA, k + 1, 0) : epi_none(h));
         LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
-                                          &st->projV[((k + 1) * SMAX + q) * SMAX], next));
+                                          &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp));
       }
       LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
                                              &st->eta[k * SMAX * SMAX], SMAX));
@@ -441,7 +443,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     const bool replaced = ctl.replace_every > 0 && out.cycles % ctl.replace_every == 0;
     if (replaced) {
       LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
-                                        epi_of(EPI_GAMMA, 0, 0)));
+                                        epi_of(EPI_GAMMA, 0, 0), w.Pil, w.sp));
       out.mvs += 1;
       if (prec) h->mvs32 += 1;
     }
@@ -913,6 +915,18 @@ static msstab_status create_impl(msstab_t h, int64_t n, int64_t nnz, const int32
   for (int q = 0; q < h->s; ++q)
     LAUNCH(MSSTAB_K_OTHER, f64_to_f32_n(c, n, h->w64.P + (int64_t)q * h->w64.ld,
                                         h->w32.P + (int64_t)q * h->w32.ld, 1.0));
+  {
+    // row-interleaved copies of P (rows on 16-byte boundaries)
+    void* p = nullptr;
+    h->w64.sp = (h->s + 1) / 2 * 2;
+    CKS(dalloc(h, &p, sizeof(double) * (size_t)n * h->w64.sp));
+    h->w64.Pil = (double*)p;
+    LAUNCH(MSSTAB_K_OTHER, interleave_rows<double>(c, n, h->s, h->w64.P, h->w64.ld, h->w64.sp, h->w64.Pil));
+    h->w32.sp = (h->s + 3) / 4 * 4;
+    CKS(dalloc(h, &p, sizeof(float) * (size_t)n * h->w32.sp));
+    h->w32.Pil = (float*)p;
+    LAUNCH(MSSTAB_K_OTHER, interleave_rows<float>(c, n, h->s, h->w32.P, h->w32.ld, h->w32.sp, h->w32.Pil));
+  }
   CK(cudaStreamSynchronize(h->stream));
   return MSSTAB_OK;
 }
@@ -1142,10 +1156,10 @@ msstab_status msstab_op_spmv_dot(msstab_t h, int32_t prec, const void* d_x, void
   const Ctx c = h->ctx();
   if (prec == 0)
     LAUNCH(MSSTAB_K_SPMV_DOT, spmv<double>(c, h->A, (const double*)d_x, (double*)d_y, nullptr, h->w64.P,
-                                           h->w64.ld, h->s, 1, 0, d_dots, epi_none(h)));
+                                           h->w64.ld, h->s, 1, 0, d_dots, epi_none(h), h->w64.Pil, h->w64.sp));
   else
     LAUNCH(MSSTAB_K_SPMV_DOT, spmv<float>(c, h->A, (const float*)d_x, (float*)d_y, nullptr, h->w32.P, h->w32.ld,
-                                          h->s, 1, 0, d_dots, epi_none(h)));
+                                          h->s, 1, 0, d_dots, epi_none(h), h->w32.Pil, h->w32.sp));
   CK(cudaStreamSynchronize(h->stream));
   return MSSTAB_OK;
 }

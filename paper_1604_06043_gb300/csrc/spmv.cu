@@ -13,6 +13,7 @@
 // All loads of matrix data are single-use and go through the read-only path.
 
 #include <mutex>
+#include <type_traits>
 
 #include "launch.h"
 #include "msstab.h"
@@ -43,6 +44,8 @@ struct SpmvArgs {
   double* out;
   Epi epi;
   RedScratch rs;
+  const T* Pil;   // P interleaved by row (Pil[row * sp + c]), rows 16-byte aligned; or NULL
+  int sp;
 };
 
 // Smallest power of two >= v (v <= 32).
@@ -75,6 +78,40 @@ struct DotAcc<float, NP> {
   __device__ __forceinline__ void add(int i, float x, float y) { v[i] = fmaf(x, y, v[i]); }
   __device__ __forceinline__ double get(int i) const { return widen_f32(v[i]); }
 };
+
+// The row's NP entries of the interleaved P (zero beyond np), with 16-byte loads.
+template <typename T, int NP>
+__device__ __forceinline__ void load_prow(const SpmvArgs<T>& a, int row, T (&pr)[NP]) {
+  static_assert(NP % (16 / sizeof(T)) == 0, "NP must fill 16-byte vectors");
+  constexpr int VW = 16 / sizeof(T);
+  using V = std::conditional_t<sizeof(T) == 8, double2, float4>;
+  const V* src = reinterpret_cast<const V*>(a.Pil + (int64_t)row * a.sp);
+#pragma unroll
+  for (int v = 0; v < NP / VW; ++v) {
+    if (v * VW < a.sp) {
+      const V q = __ldg(src + v);
+      const T* e = reinterpret_cast<const T*>(&q);
+#pragma unroll
+      for (int u = 0; u < VW; ++u) pr[v * VW + u] = e[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < VW; ++u) pr[v * VW + u] = T(0);
+    }
+  }
+}
+
+template <typename T, int NP>
+__device__ __forceinline__ void acc_row_pre(const SpmvArgs<T>& a, int row, T yv, const T (&pr)[NP],
+                                            DotAcc<T, NP>& acc) {
+#pragma unroll
+  for (int c = 0; c < NP; ++c)
+    if (c < a.np) acc.add(c, yv, pr[c]);
+  if (a.self) acc.add(NP, yv, yv);
+  if (a.bdot) {
+    const T bd = a.b[row];
+    acc.add(NP + 1, bd, bd);
+  }
+}
 
 template <typename T, int NP>
 __device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc<T, NP>& acc) {
@@ -170,16 +207,42 @@ __global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArg
   acc.zero();
   const int lane = threadIdx.x & 31;
   const int nwarps = gridDim.x * SNWARP;
-  for (int sl = (blockIdx.x * SNT + threadIdx.x) >> 5; sl < A.nslices; sl += nwarps) {
-    const int w = ro(A.slice_w + sl);
-    const int64_t base = (int64_t)ro(A.slice_ptr + sl) + lane;
-    const T sum = sell_row<T>(A.col, A.val, a.x, base, w);
+  int sl = (blockIdx.x * SNT + threadIdx.x) >> 5;
+  // the next slice's width and start are loaded one iteration ahead
+  int w_next = 0, base_next = 0;
+  if (sl < A.nslices) {
+    w_next = ro(A.slice_w + sl);
+    base_next = ro(A.slice_ptr + sl);
+  }
+  for (; sl < A.nslices; sl += nwarps) {
+    const int w = w_next;
+    const int64_t base = (int64_t)base_next + lane;
+    if (sl + nwarps < A.nslices) {
+      w_next = ro(A.slice_w + sl + nwarps);
+      base_next = ro(A.slice_ptr + sl + nwarps);
+    }
     const int pos = sl * 32 + lane;
+    const int row = pos < A.n ? (A.perm ? ro(A.perm + pos) : pos) : 0;
+    // FP32: the row's P entries (interleaved layout) are in flight with the
+    // matrix loads (FP64: the 8 extra doubles would spill at 64 registers)
+    constexpr bool PRE = NA > 0 && sizeof(T) == 4;
+    T pr[PRE ? NA : 1];
+    const bool pre = PRE && a.Pil != nullptr && pos < A.n;
+    if constexpr (PRE) {
+      if (pre) load_prow<T, NA>(a, row, pr);
+    }
+    const T sum = sell_row<T>(A.col, A.val, a.x, base, w);
     if (pos < A.n) {
-      const int row = A.perm ? ro(A.perm + pos) : pos;
       const T yv = a.b ? (T)(a.b[row] - sum) : sum;
       a.y[row] = yv;
-      if (NP >= 0) acc_row<T, NA>(a, row, yv, acc);
+      if constexpr (PRE) {
+        if (pre)
+          acc_row_pre<T, NA>(a, row, yv, pr, acc);
+        else
+          acc_row<T, NA>(a, row, yv, acc);
+      } else if constexpr (NP >= 0) {
+        acc_row<T, NA>(a, row, yv, acc);
+      }
     }
   }
   if constexpr (NP >= 0) finish<T, NA>(a, acc);
@@ -233,9 +296,9 @@ static void launch_csr(const Ctx& c, const CsrMat<T>& M, const SpmvArgs<T>& a) {
 
 template <typename T>
 cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
-                 int np, int self, int bdot, double* out, Epi epi) {
+                 int np, int self, int bdot, double* out, Epi epi, const T* Pil, int sp) {
   if (np < 0 || np > SMAX) return cudaErrorInvalidValue;
-  SpmvArgs<T> a{x, y, b, P, ldp, np, self, bdot, out, epi, c.rs};
+  SpmvArgs<T> a{x, y, b, P, ldp, np, self, bdot, out, epi, c.rs, Pil, sp};
   const bool dot = (np + self + bdot) > 0;
   if (A.format == 0) {
     SellMat<T> M{A.n, A.nslices, A.slice_ptr, A.slice_w, A.perm, A.scol, pick_val<T>(A, true)};
@@ -266,9 +329,31 @@ cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, c
 }
 
 template cudaError_t spmv<double>(const Ctx&, const MatDesc&, const double*, double*, const double*,
-                                  const double*, int64_t, int, int, int, double*, Epi);
+                                  const double*, int64_t, int, int, int, double*, Epi, const double*, int);
 template cudaError_t spmv<float>(const Ctx&, const MatDesc&, const float*, float*, const float*, const float*,
-                                 int64_t, int, int, int, double*, Epi);
+                                 int64_t, int, int, int, double*, Epi, const float*, int);
+
+// Pil[row * sp + c] = P[c * ldp + row] for c < s, zero for s <= c < sp.
+template <typename T>
+__global__ void interleave_kernel(int n, int s, const T* P, int64_t ldp, int sp, T* Pil) {
+  const int64_t total = (int64_t)n * sp;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t row = i / sp;
+    const int c = (int)(i % sp);
+    Pil[i] = c < s ? P[(int64_t)c * ldp + row] : T(0);
+  }
+}
+
+template <typename T>
+cudaError_t interleave_rows(const Ctx& c, int n, int s, const T* P, int64_t ldp, int sp, T* Pil) {
+  const int64_t total = (int64_t)n * sp;
+  int64_t g = (total + NT - 1) / NT;
+  if (g > 8192) g = 8192;
+  interleave_kernel<T><<<(int)g, NT, 0, c.stream>>>(n, s, P, ldp, sp, Pil);
+  return cudaGetLastError();
+}
+template cudaError_t interleave_rows<double>(const Ctx&, int, int, const double*, int64_t, int, double*);
+template cudaError_t interleave_rows<float>(const Ctx&, int, int, const float*, int64_t, int, float*);
 
 double spmv_bytes(const MatDesc& A, int prec) {
   const double vb = prec == 0 ? 8.0 : 4.0;
@@ -445,7 +530,7 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
   if (g > (int64_t)nb * sms[dev]) g = (int64_t)nb * sms[dev];
   if (g > NOALLOC_MAX_BLOCKS) g = NOALLOC_MAX_BLOCKS;
   CsrMat<double> M{(int)n, d_row_ptr, d_col, d_val};
-  SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs};
+  SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs, nullptr, 0};
   spmv_csr_kernel<double, 16><<<(int)g, SNT, 0, st>>>(M, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
