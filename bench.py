@@ -564,10 +564,14 @@ def main(argv=None):
         ref_x = []
         xs = torch.tensor(x0_np, device=dev)
         variants = {}
-        for name, opts in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER)),
-                           ("msstab_fp32_inner", FP32_INNER_OPTS(M))):
+        p_block = pb.randn_block_partitioned(A.n, w.s, pb.SEED_P)
+        for name, opts, praw in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER), None),
+                                 ("msstab_fp32_inner", FP32_INNER_OPTS(M), None),
+                                 ("msstab_fp64_block_p", {}, p_block),
+                                 ("msstab_fp32_inner_block_p", FP32_INNER_OPTS(M), p_block)):
           try:
-            V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every, **opts)
+            V = M.Solver(A, w.s, w.ell, w.p_raw() if praw is None else praw, device=dev,
+                         replace_every=w.replace_every, **opts)
             xv = torch.tensor(x0_np, device=dev)
             run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W, check=False)
             torch.cuda.synchronize()
@@ -583,10 +587,14 @@ def main(argv=None):
                               "mvs_per_system": round(statistics.mean(t["mvs"] for t in tv), 2),
                               "relres_true_max": max(t["relres_true"] for t in tv),
                               "failed_solves": sum(1 for t in tv if t["status"] != 0)}
-            if name == "msstab_fp32_inner":
+            if "fp32_inner" in name:
                 variants[name]["mvs_fp32_per_system"] = round(statistics.mean(t["mvs_fp32"] for t in tv), 2)
                 variants[name]["outer_per_system"] = round(statistics.mean(t["outer"] for t in tv), 2)
+                variants[name]["fp64_finishes"] = sum(t["fp64_finish"] for t in tv)
+            if name == "msstab_fp32_inner":
                 variants[name]["_xs"] = xs_list
+            if praw is not None:
+                variants[name]["cut_space"] = "block-partitioned N(0,1), seed 3 (rows (i // 32) mod s)"
             V.close()
           except Exception as e:  # a failing variant is reported, the main line still stands
             variants[name] = {"error": str(e)[-300:]}

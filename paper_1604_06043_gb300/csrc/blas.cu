@@ -226,6 +226,7 @@ struct TauArgs {
   DevState* st;
   Epi epi;
   RedScratch rs;
+  const T* Pb;   // block-partitioned P (see pblock_col), or NULL
 };
 
 // L: compile-time bound on the degree l (1, 2, 4 or 8): level arrays of L + 2
@@ -252,10 +253,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs
   // enough bytes are in flight per SM (this kernel runs 2 blocks per SM).
   auto load_row = [&](int row, T (&lv)[L + 2], T (&pv)[SMAX], T& xv) {
     if (a.proj) {
+      if (a.Pb) {
+        pv[0] = __ldg(a.Pb + row);
+      } else {
 #pragma unroll
-      for (int c = 0; c < SMAX; ++c) {
-        if (c >= a.s) break;
-        pv[c] = __ldg(a.P + (int64_t)c * a.ldp + row);
+        for (int c = 0; c < SMAX; ++c) {
+          if (c >= a.s) break;
+          pv[c] = __ldg(a.P + (int64_t)c * a.ldp + row);
+        }
       }
     }
     if (t == 0) {
@@ -314,10 +319,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs
       out = lv[1];
     }
     if (a.proj) {
+      if (a.Pb) {
+        add_to_slot<SMAX>(acc, pblock_col(row, a.s), out, pv[0]);
+      } else {
 #pragma unroll
-      for (int c = 0; c < SMAX; ++c) {
-        if (c >= a.s) break;
-        acc.add(c, out, pv[c]);
+        for (int c = 0; c < SMAX; ++c) {
+          if (c >= a.s) break;
+          acc.add(c, out, pv[c]);
+        }
       }
       if (t == 0) acc.add(SMAX, out, out);
     }
@@ -378,8 +387,8 @@ static void launch_tau(const Ctx& c, const TauArgs<T>& a) {
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi) {
-  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs};
+                       Epi epi, const T* Pb) {
+  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs, Pb};
   if (ell <= 1)
     launch_tau<T, 1>(c, a);
   else if (ell <= 2)
@@ -638,7 +647,7 @@ cudaError_t f64_to_f32_n(const Ctx& c, int64_t n, const double* x, float* y, dou
   template cudaError_t lazy_update<T>(const Ctx&, int, int, T*, T*, T*, int64_t, int, const double*,      \
                                       const double*, int);                                                \
   template cudaError_t tau_update<T>(const Ctx&, int, int, int, T*, T*, T*, T*, int64_t, const double*,   \
-                                     const T*, int64_t, int, int, DevState*, Epi);                        \
+                                     const T*, int64_t, int, int, DevState*, Epi, const T*);             \
   template cudaError_t cols_axpy<T>(const Ctx&, int, T*, const T*, int64_t, int, const double*);          \
   template cudaError_t scale_rsqrt<T>(const Ctx&, int, const T*, T*, const double*);                      \
   template cudaError_t tri_apply<T>(const Ctx&, int, int, T*, T*, int64_t, const double*);

@@ -103,6 +103,31 @@ __device__ __forceinline__ double widen_f32(float f) {
 }
 
 // ---------------------------------------------------------------------------
+// block-partitioned cut space.  When every row i of P has its only non-zero
+// in column c(i) = (i / 32) mod s (32-row blocks dealt round-robin to the s
+// columns), P^T y needs one multiply-add per row instead of s.  A warp always
+// handles 32 consecutive rows starting at a multiple of 32, so c is the same
+// for all its lanes and the switch below runs one branch (an FP64 multiply-
+// add predicated off would still occupy the FP64 unit of this GPU).
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int pblock_col(int64_t row, int s) { return (int)((row >> 5) % s); }
+
+template <int NP, typename Acc, typename T>
+__device__ __forceinline__ void add_to_slot(Acc& acc, int c, T y, T p) {
+  switch (c) {
+#define MSK_SLOT(J) \
+  case J:           \
+    if constexpr (J < NP) acc.add(J, y, p); \
+    break;
+    MSK_SLOT(0) MSK_SLOT(1) MSK_SLOT(2) MSK_SLOT(3) MSK_SLOT(4) MSK_SLOT(5) MSK_SLOT(6) MSK_SLOT(7)
+    MSK_SLOT(8) MSK_SLOT(9) MSK_SLOT(10) MSK_SLOT(11) MSK_SLOT(12) MSK_SLOT(13) MSK_SLOT(14) MSK_SLOT(15)
+#undef MSK_SLOT
+    default:
+      break;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // reductions
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ double warp_sum(double v) {

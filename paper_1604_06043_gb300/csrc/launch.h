@@ -51,9 +51,16 @@ double spmv_bytes(const MatDesc& A, int prec);
 // Pil (optional): the same P interleaved by row, Pil[row * sp + c], rows on
 // 16-byte boundaries (sp a multiple of 16 / sizeof(T)); the SELL kernel then
 // loads a row's P entries with vector loads issued with the matrix loads.
+// Pb (optional): P in block-partitioned form (row i's only non-zero in column
+// (i / 32) mod np, Pb[i] its value): one multiply-add per row for the dots.
 template <typename T>
 cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
-                 int np, int self, int bdot, double* out, Epi epi, const T* Pil = nullptr, int sp = 0);
+                 int np, int self, int bdot, double* out, Epi epi, const T* Pil = nullptr, int sp = 0,
+                 const T* Pb = nullptr);
+
+// Pb[i] = P[(i / 32) mod s][i]; *flag |= 1 if P has any other non-zero.
+template <typename T>
+cudaError_t pblock_compress(const Ctx& c, int n, int s, const T* P, int64_t ldp, T* Pb, int* flag);
 
 // Pil[row * sp + c] = P[c * ldp + row] (c < s), zero padding up to sp.
 template <typename T>
@@ -94,7 +101,7 @@ cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi);
+                       Epi epi, const T* Pb = nullptr);
 
 // w -= sum_{c<nc} h[c] U_c (h: FP64 device), columns U_c at U + c*ld.
 template <typename T>

@@ -39,6 +39,7 @@ struct Work {
   T* P = nullptr;     // orthonormal cut-space basis
   T* Pil = nullptr;   // P interleaved by row (row stride sp), for the fused products
   int sp = 0;
+  T* Pb = nullptr;    // block-partitioned P (one value per row), when P has that structure
   bool has_rec = false;
 };
 
@@ -407,20 +408,20 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     }
     if (need_proj) {
       LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, nullptr, ld, nullptr, P, ld, 0, 1, st,
-                                         epi_of(EPI_GAMMA, 0, 0)));
+                                         epi_of(EPI_GAMMA, 0, 0), w.Pb));
       need_proj = false;
     }
     // ---- one cycle: level steps k = 0..l-1 ----
     for (int k = 0; k < ell; ++k) {
       LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
       LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
-                                        &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp));
+                                        &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp, w.Pb));
       for (int q = 0; q < s; ++q) {
         LAUNCH(MSSTAB_K_ETA, eta_eager<T>(c, n, s, w.R, w.V, ld, k, q, &st->eta[(k * SMAX + q) * SMAX]));
         Epi next = q + 1 < s ? epi_of(EPI_ETA, k, q + 1)
                              : (k + 1 < ell ? epi_of(EPI_GAMMA, k + 1, 0) : epi_none(h));
         LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
-                                          &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp));
+                                          &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp, w.Pb));
       }
       LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
                                              &st->eta[k * SMAX * SMAX], SMAX));
@@ -433,7 +434,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
                                        epi_of(EPI_TAU, 0, 0)));
     }
     LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
-                                       epi_of(EPI_GAMMA, 0, 0)));
+                                       epi_of(EPI_GAMMA, 0, 0), w.Pb));
     out.mvs += cyc_mvs;
     if (prec) h->mvs32 += cyc_mvs;
     out.cycles += 1;
@@ -443,7 +444,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     const bool replaced = ctl.replace_every > 0 && out.cycles % ctl.replace_every == 0;
     if (replaced) {
       LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
-                                        epi_of(EPI_GAMMA, 0, 0), w.Pil, w.sp));
+                                        epi_of(EPI_GAMMA, 0, 0), w.Pil, w.sp, w.Pb));
       out.mvs += 1;
       if (prec) h->mvs32 += 1;
     }
@@ -927,6 +928,27 @@ static msstab_status create_impl(msstab_t h, int64_t n, int64_t nnz, const int32
     h->w32.Pil = (float*)p;
     LAUNCH(MSSTAB_K_OTHER, interleave_rows<float>(c, n, h->s, h->w32.P, h->w32.ld, h->w32.sp, h->w32.Pil));
   }
+  {
+    // a block-partitioned cut space (each row's only non-zero in column
+    // (row / 32) mod s; orthonormalisation keeps that structure exactly)
+    // makes the projections one multiply-add per row
+    void* p = nullptr;
+    CKS(dalloc(h, &p, sizeof(double) * (size_t)n));
+    double* pb64 = (double*)p;
+    CKS(dalloc(h, &p, sizeof(float) * (size_t)n));
+    float* pb32 = (float*)p;
+    CK(cudaMemsetAsync(&h->st->flag, 0, sizeof(int), h->stream));
+    LAUNCH(MSSTAB_K_OTHER, pblock_compress<double>(c, n, h->s, h->w64.P, h->w64.ld, pb64, &h->st->flag));
+    LAUNCH(MSSTAB_K_OTHER, pblock_compress<float>(c, n, h->s, h->w32.P, h->w32.ld, pb32, &h->st->flag));
+    CKS(sync_read(h, &h->st->flag, sizeof(int)));
+    int f = 0;
+    std::memcpy(&f, h->h_small, sizeof(int));
+    CK(cudaMemsetAsync(&h->st->flag, 0, sizeof(int), h->stream));
+    if (f == 0 && h->s > 1) {
+      h->w64.Pb = pb64;
+      h->w32.Pb = pb32;
+    }
+  }
   CK(cudaStreamSynchronize(h->stream));
   return MSSTAB_OK;
 }
@@ -1156,10 +1178,11 @@ msstab_status msstab_op_spmv_dot(msstab_t h, int32_t prec, const void* d_x, void
   const Ctx c = h->ctx();
   if (prec == 0)
     LAUNCH(MSSTAB_K_SPMV_DOT, spmv<double>(c, h->A, (const double*)d_x, (double*)d_y, nullptr, h->w64.P,
-                                           h->w64.ld, h->s, 1, 0, d_dots, epi_none(h), h->w64.Pil, h->w64.sp));
+                                           h->w64.ld, h->s, 1, 0, d_dots, epi_none(h), h->w64.Pil, h->w64.sp,
+                                           h->w64.Pb));
   else
     LAUNCH(MSSTAB_K_SPMV_DOT, spmv<float>(c, h->A, (const float*)d_x, (float*)d_y, nullptr, h->w32.P, h->w32.ld,
-                                          h->s, 1, 0, d_dots, epi_none(h), h->w32.Pil, h->w32.sp));
+                                          h->s, 1, 0, d_dots, epi_none(h), h->w32.Pil, h->w32.sp, h->w32.Pb));
   CK(cudaStreamSynchronize(h->stream));
   return MSSTAB_OK;
 }

@@ -46,6 +46,7 @@ struct SpmvArgs {
   RedScratch rs;
   const T* Pil;   // P interleaved by row (Pil[row * sp + c]), rows 16-byte aligned; or NULL
   int sp;
+  const T* Pb;    // block-partitioned P: Pb[row] = P[pblock_col(row)][row]; or NULL
 };
 
 // Smallest power of two >= v (v <= 32).
@@ -116,9 +117,13 @@ __device__ __forceinline__ void acc_row_pre(const SpmvArgs<T>& a, int row, T yv,
 template <typename T, int NP>
 __device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, DotAcc<T, NP>& acc) {
   // NP is the compile-time slot count chosen for np (np == NP in the cycle)
+  if (a.Pb) {
+    add_to_slot<NP>(acc, pblock_col(row, a.np), yv, ro(a.Pb + row));
+  } else {
 #pragma unroll
-  for (int c = 0; c < NP; ++c)
-    if (c < a.np) acc.add(c, yv, ro(a.P + (int64_t)c * a.ldp + row));
+    for (int c = 0; c < NP; ++c)
+      if (c < a.np) acc.add(c, yv, ro(a.P + (int64_t)c * a.ldp + row));
+  }
   if (a.self) acc.add(NP, yv, yv);
   if (a.bdot) {
     const T bd = a.b[row];
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArg
     // matrix loads (FP64: the 8 extra doubles would spill at 64 registers)
     constexpr bool PRE = NA > 0 && sizeof(T) == 4;
     T pr[PRE ? NA : 1];
-    const bool pre = PRE && a.Pil != nullptr && pos < A.n;
+    const bool pre = PRE && a.Pil != nullptr && a.Pb == nullptr && pos < A.n;
     if constexpr (PRE) {
       if (pre) load_prow<T, NA>(a, row, pr);
     }
@@ -296,9 +301,11 @@ static void launch_csr(const Ctx& c, const CsrMat<T>& M, const SpmvArgs<T>& a) {
 
 template <typename T>
 cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, const T* P, int64_t ldp,
-                 int np, int self, int bdot, double* out, Epi epi, const T* Pil, int sp) {
+                 int np, int self, int bdot, double* out, Epi epi, const T* Pil, int sp, const T* Pb) {
   if (np < 0 || np > SMAX) return cudaErrorInvalidValue;
-  SpmvArgs<T> a{x, y, b, P, ldp, np, self, bdot, out, epi, c.rs, Pil, sp};
+  // the block-partitioned form needs 32 consecutive rows per warp (no SELL sorting)
+  const T* pb = (Pb && !(A.format == 0 && A.perm)) ? Pb : nullptr;
+  SpmvArgs<T> a{x, y, b, P, ldp, np, self, bdot, out, epi, c.rs, Pil, sp, pb};
   const bool dot = (np + self + bdot) > 0;
   if (A.format == 0) {
     SellMat<T> M{A.n, A.nslices, A.slice_ptr, A.slice_w, A.perm, A.scol, pick_val<T>(A, true)};
@@ -329,9 +336,10 @@ cudaError_t spmv(const Ctx& c, const MatDesc& A, const T* x, T* y, const T* b, c
 }
 
 template cudaError_t spmv<double>(const Ctx&, const MatDesc&, const double*, double*, const double*,
-                                  const double*, int64_t, int, int, int, double*, Epi, const double*, int);
+                                  const double*, int64_t, int, int, int, double*, Epi, const double*, int,
+                                  const double*);
 template cudaError_t spmv<float>(const Ctx&, const MatDesc&, const float*, float*, const float*, const float*,
-                                 int64_t, int, int, int, double*, Epi, const float*, int);
+                                 int64_t, int, int, int, double*, Epi, const float*, int, const float*);
 
 // Pil[row * sp + c] = P[c * ldp + row] for c < s, zero for s <= c < sp.
 template <typename T>
@@ -354,6 +362,30 @@ cudaError_t interleave_rows(const Ctx& c, int n, int s, const T* P, int64_t ldp,
 }
 template cudaError_t interleave_rows<double>(const Ctx&, int, int, const double*, int64_t, int, double*);
 template cudaError_t interleave_rows<float>(const Ctx&, int, int, const float*, int64_t, int, float*);
+
+// flag |= 1 if a row of P (s columns, leading dimension ldp) has a non-zero
+// outside column pblock_col(row); else Pb[row] = P[pblock_col(row)][row].
+template <typename T>
+__global__ void pblock_kernel(int n, int s, const T* P, int64_t ldp, T* Pb, int* flag) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int c = pblock_col(i, s);
+    bool ok = true;
+    for (int j = 0; j < s; ++j)
+      if (j != c && P[(int64_t)j * ldp + i] != T(0)) ok = false;
+    if (!ok) atomicOr(flag, 1);
+    Pb[i] = P[(int64_t)c * ldp + i];
+  }
+}
+
+template <typename T>
+cudaError_t pblock_compress(const Ctx& c, int n, int s, const T* P, int64_t ldp, T* Pb, int* flag) {
+  int64_t g = ((int64_t)n + NT - 1) / NT;
+  if (g > 8192) g = 8192;
+  pblock_kernel<T><<<(int)g, NT, 0, c.stream>>>(n, s, P, ldp, Pb, flag);
+  return cudaGetLastError();
+}
+template cudaError_t pblock_compress<double>(const Ctx&, int, int, const double*, int64_t, double*, int*);
+template cudaError_t pblock_compress<float>(const Ctx&, int, int, const float*, int64_t, float*, int*);
 
 double spmv_bytes(const MatDesc& A, int prec) {
   const double vb = prec == 0 ? 8.0 : 4.0;
@@ -530,7 +562,7 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
   if (g > (int64_t)nb * sms[dev]) g = (int64_t)nb * sms[dev];
   if (g > NOALLOC_MAX_BLOCKS) g = NOALLOC_MAX_BLOCKS;
   CsrMat<double> M{(int)n, d_row_ptr, d_col, d_val};
-  SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs, nullptr, 0};
+  SpmvArgs<double> a{d_x, d_y, nullptr, d_P, ldp, s, 1, 0, d_dots, Epi{EPI_NONE, 0, 0, s, 1, nullptr}, rs, nullptr, 0, nullptr};
   spmv_csr_kernel<double, 16><<<(int)g, SNT, 0, st>>>(M, a);
   e = cudaGetLastError();
   if (e != cudaSuccess) {

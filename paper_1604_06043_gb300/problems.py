@@ -155,6 +155,19 @@ def randn_cols(n: int, s: int, seed: int = SEED_P) -> np.ndarray:
     return np.random.default_rng(seed).standard_normal((s, n))
 
 
+def randn_block_partitioned(n: int, s: int, seed: int) -> np.ndarray:
+    """(s, n) raw cut space whose row i has its only non-zero, N(0,1), in
+    column (i // 32) mod s: 32-row blocks dealt round-robin to the s columns.
+    A random P with disjoint column supports (the columns are orthogonal
+    already); the CUDA path detects this form and needs one multiply-add per
+    row for P^T y."""
+    rng = np.random.default_rng(seed)
+    P = np.zeros((s, n))
+    rows = np.arange(n)
+    P[(rows // 32) % s, rows] = rng.standard_normal(n)
+    return P
+
+
 def lognormal_kappa(shape: Sequence[int], sigma: float = 1.0, corr: float = 8.0,
                     seed: int = SEED_KAPPA) -> np.ndarray:
     """kappa = exp(sigma g): g is white noise smoothed by a separable Gaussian of

@@ -37,7 +37,11 @@ def _mvs_match(gs, ref, tol):
 
 
 def _gpu_sequence(M, w, A, steps, **opt):
-    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, **opt)
+    return _gpu_sequence_p(M, w, A, steps, w.p_raw(), **opt)
+
+
+def _gpu_sequence_p(M, w, A, steps, p_raw, **opt):
+    S = M.Solver(A, w.s, w.ell, p_raw, device=DEV, **opt)
     f = _t(w.f())
     x = _t(w.x0())
     b = torch.empty_like(x)
@@ -412,3 +416,34 @@ def test_fp32_inner_measured_form_and_fp64_finish(M):
         else:
             assert st.mvs_fp32 > 0.8 * st.mvs
         S.close()
+
+
+def test_block_partitioned_cut_space_matches_oracle(M):
+    # P with disjoint 32-row-block supports takes the one-multiply-add-per-row
+    # projections; N = 35937 ends in a partial block
+    w = pb.WORKLOADS["convdiff3d_33"]
+    A = w.matrix()
+    Pr = pb.randn_block_partitioned(A.n, w.s, 3)
+    S = M.Solver(A, w.s, w.ell, Pr, device=DEV, replace_every=1)
+    x = torch.tensor(pb.uniform(A.n, 21) - 0.5, device=DEV)
+    y = torch.empty_like(x)
+    d = torch.zeros(w.s + 1, dtype=torch.float64, device=DEV)
+    S.op_spmv_dot(x, y, d)
+    P = torch.empty((w.s, A.n), dtype=torch.float64, device=DEV)
+    S.op_get_p(P)
+    Pn, yn = P.cpu().numpy(), y.cpu().numpy()
+    assert np.count_nonzero(Pn) == A.n
+    ref = Pn @ yn
+    assert np.all(np.abs(d.cpu().numpy()[:w.s] - ref) <= 1e-12 * (np.abs(Pn) @ np.abs(yn)))
+    S.close()
+    g = _gpu_sequence_p(M, w, A, w.steps, Pr, replace_every=1)
+    o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, Pr, tol=w.tol, replace_every=1)
+    As = A.to_scipy()
+    xprev = w.x0()
+    for i, (gs, os_) in enumerate(zip(g, o.solves)):
+        mvs, cycles, relres, fetched, used, xg, hist = gs
+        b = xprev / w.tau + w.f()
+        assert np.linalg.norm(b - As @ xg) <= w.tol * np.linalg.norm(b) * 1.0001
+        assert _mvs_match(gs, os_, w.tol), (i, mvs, os_.mvs, hist, os_.history)
+        assert np.linalg.norm(xg - os_.x) <= 1e-6 * np.linalg.norm(os_.x)
+        xprev = xg
