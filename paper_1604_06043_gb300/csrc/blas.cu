@@ -1,3 +1,4 @@
+#include <type_traits>
 // Tall-skinny block kernels of libmsstab: the vector updates of Algorithm 1
 // (gamma step, eta steps, degree-l step), multi-dots with a deterministic
 // single grid-level combine, and the helpers of the Arnoldi start and of the
@@ -53,7 +54,60 @@ struct Acc<float, N> {   // FP32 partials, widened exactly for the FP64 reductio
 // ---------------------------------------------------------------------------
 // gamma step on the top level:  r^(k) -= V^(k) gamma
 // ---------------------------------------------------------------------------
+// Rows are handled VW at a time (VW = 16 / sizeof(T): 16-byte loads, when
+// every column start is 16-byte aligned; else VW = 1), all s + 1 loads of a
+// group issued before the arithmetic; a ragged tail of n % VW rows is done
+// row by row.
+template <typename T, int VW>
+struct VecOf {
+  using type = std::conditional_t<VW == 1, T, std::conditional_t<sizeof(T) == 8, double2, float4>>;
+};
+
+template <typename T, int VW>
+__device__ __forceinline__ T vget(const typename VecOf<T, VW>::type& v, int u) {
+  return reinterpret_cast<const T*>(&v)[u];
+}
+template <typename T, int VW>
+__device__ __forceinline__ void vset(typename VecOf<T, VW>::type& v, int u, T x) {
+  reinterpret_cast<T*>(&v)[u] = x;
+}
+
+template <typename T, int S, int VW, typename ColOf>
+__device__ __forceinline__ void combine_rows(int n, int s, const T* base, T* out, const T* c, ColOf col_of) {
+  using V = typename VecOf<T, VW>::type;
+  const int64_t groups = n / VW;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t g = blockIdx.x * (int64_t)NT + threadIdx.x; g < groups; g += stride) {
+    V acc = reinterpret_cast<const V*>(base)[g];
+    V v[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+      v[j] = __ldg(reinterpret_cast<const V*>(col_of(j)) + g);
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+#pragma unroll
+      for (int u = 0; u < VW; ++u) vset<T, VW>(acc, u, vget<T, VW>(acc, u) - c[j] * vget<T, VW>(v[j], u));
+    }
+    reinterpret_cast<V*>(out)[g] = acc;
+  }
+  if constexpr (VW > 1) {   // ragged tail: rows groups * VW .. n - 1
+    const int64_t row = groups * VW + threadIdx.x;
+    if (blockIdx.x == 0 && row < n) {
+      T v = base[row];
+      for (int j = 0; j < s; ++j) v -= c[j] * col_of(j)[row];
+      out[row] = v;
+    }
+  }
+}
+
 template <typename T>
+static bool aligned16(const T* p) { return ((uintptr_t)p & 15u) == 0; }
+
+// gamma step on the top level:  r^(k) -= V^(k) gamma
+template <typename T, int S, int VW>
 __global__ void __launch_bounds__(NT) gamma_eager_kernel(int n, int s, T* __restrict__ R,
                                                          const T* __restrict__ V, int64_t ld, int k,
                                                          const double* __restrict__ gamma) {
@@ -62,26 +116,43 @@ __global__ void __launch_bounds__(NT) gamma_eager_kernel(int n, int s, T* __rest
   __syncthreads();
   T* rk = R + (int64_t)k * ld;
   const T* vk = V + (int64_t)(k + 1) * s * ld;
-  const int stride = gridDim.x * NT;
-  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
-    T v = rk[row];
-#pragma unroll 4
-    for (int j = 0; j < s; ++j) v -= g[j] * __ldg(vk + (int64_t)j * ld + row);
-    rk[row] = v;
+  combine_rows<T, S, VW>(n, s, rk, rk, g, [&](int j) { return vk + (int64_t)j * ld; });
+}
+
+// launch kern<S, VW> for the smallest S in {4, 8, 16} >= s, VW = 16-byte
+// vectors when vec, else 1; one cached grid bound per instantiation
+template <typename T, template <typename, int, int> class KS, typename Launch>
+static void dispatch_sv(int s, bool vec, Launch&& launch) {
+  constexpr int V16 = 16 / sizeof(T);
+  if (vec) {
+    if (s <= 4) launch(KS<T, 4, V16>{}); else if (s <= 8) launch(KS<T, 8, V16>{}); else launch(KS<T, 16, V16>{});
+  } else {
+    if (s <= 4) launch(KS<T, 4, 1>{}); else if (s <= 8) launch(KS<T, 8, 1>{}); else launch(KS<T, 16, 1>{});
   }
 }
 
+template <typename T, int S, int VW>
+struct GammaK {
+  static constexpr int vw = VW;
+  static constexpr auto fn = gamma_eager_kernel<T, S, VW>;
+};
+
 template <typename T>
 cudaError_t gamma_eager(const Ctx& c, int n, int s, T* R, const T* V, int64_t ld, int k, const double* gamma) {
-  static int cap = max_grid(gamma_eager_kernel<T>, c);
-  gamma_eager_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, R, V, ld, k, gamma);
+  const bool vec = aligned16(R) && aligned16(V) && ((ld * (int64_t)sizeof(T)) % 16) == 0;
+  dispatch_sv<T, GammaK>(s, vec, [&](auto kk) {
+    using KK = decltype(kk);
+    static int cap = max_grid(KK::fn, c);
+    const int64_t groups = (n + KK::vw - 1) / KK::vw;
+    KK::fn<<<clamp_grid((groups + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, R, V, ld, k, gamma);
+  });
   return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
 // eta step on the top level:  v_q^(k) = r^(k+1) - [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}] eta
 // ---------------------------------------------------------------------------
-template <typename T>
+template <typename T, int S, int VW>
 __global__ void __launch_bounds__(NT) eta_eager_kernel(int n, int s, const T* __restrict__ R, T* V, int64_t ld,
                                                        int k, int q, const double* __restrict__ eta) {
   __shared__ T e[SMAX];
@@ -91,22 +162,24 @@ __global__ void __launch_bounds__(NT) eta_eager_kernel(int n, int s, const T* __
   const T* vk = V + (int64_t)(k + 1) * s * ld;      // V^(k)
   const T* vk1 = V + (int64_t)(k + 2) * s * ld;     // V^(k+1)
   T* out = V + ((int64_t)(k + 1) * s + q) * ld;     // v_q^(k)
-  const int stride = gridDim.x * NT;
-  for (int row = blockIdx.x * NT + threadIdx.x; row < n; row += stride) {
-    T v = __ldg(r1 + row);
-#pragma unroll 4
-    for (int j = 0; j < s; ++j) {
-      const T* col = (j < q ? vk1 : vk) + (int64_t)j * ld;
-      v -= e[j] * col[row];
-    }
-    out[row] = v;
-  }
+  combine_rows<T, S, VW>(n, s, r1, out, e, [&](int j) { return (j < q ? vk1 : vk) + (int64_t)j * ld; });
 }
+
+template <typename T, int S, int VW>
+struct EtaK {
+  static constexpr int vw = VW;
+  static constexpr auto fn = eta_eager_kernel<T, S, VW>;
+};
 
 template <typename T>
 cudaError_t eta_eager(const Ctx& c, int n, int s, const T* R, T* V, int64_t ld, int k, int q, const double* eta) {
-  static int cap = max_grid(eta_eager_kernel<T>, c);
-  eta_eager_kernel<T><<<clamp_grid((n + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, R, V, ld, k, q, eta);
+  const bool vec = aligned16(R) && aligned16(V) && ((ld * (int64_t)sizeof(T)) % 16) == 0;
+  dispatch_sv<T, EtaK>(s, vec, [&](auto kk) {
+    using KK = decltype(kk);
+    static int cap = max_grid(KK::fn, c);
+    const int64_t groups = (n + KK::vw - 1) / KK::vw;
+    KK::fn<<<clamp_grid((groups + NT - 1) / NT, cap), NT, 0, c.stream>>>(n, s, R, V, ld, k, q, eta);
+  });
   return cudaGetLastError();
 }
 
