@@ -74,6 +74,37 @@ def test_128_sequence_matches_oracle_record(M):
     print("products with A, systems 1..%d: GPU %d, oracle record %d" % (len(rec["systems"]), total, total_rec))
 
 
+def test_128_fp32_inner_form_against_oracle_record(M):
+    # the FP32-inner form as benchmarked (inner M(s)stab(1), FP64 defect
+    # correction): every system to the FP64 true residual tol, the solution
+    # against the FP64 oracle's record on the sampled rows
+    rec = json.load(open(GOLDEN))
+    w = pb.WORKLOADS["convdiff3d_128"]
+    A = w.matrix()
+    As = A.to_scipy()
+    rows = np.array(rec["sample_rows"])
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, precision=M.PREC_FP32_INNER, inner_ell=1,
+                 fetch_policy=M.FETCH_NEVER, max_outer=40, replace_every=w.replace_every)
+    f = torch.tensor(w.f(), device=DEV)
+    x = torch.tensor(w.x0(), device=DEV)
+    b = torch.empty_like(x)
+    xprev = w.x0()
+    worst = 0.0
+    for i, r in enumerate(rec["systems"]):
+        S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
+        st = S.solve(b, x, w.tol)
+        xn = x.cpu().numpy()
+        bn = xprev / w.tau + w.f()
+        assert st.status == 0 and st.mvs_fp32 > 0
+        assert np.linalg.norm(bn - As @ xn) <= w.tol * np.linalg.norm(bn) * 1.0001, i
+        xo = np.array(r["x_sample"])
+        err = np.max(np.abs(xn[rows] - xo)) / np.max(np.abs(xo))
+        assert err <= 1e-6, (i, err)
+        worst = max(worst, err)
+        xprev = xn
+    print("FP32-inner form, systems 1..%d: max sampled error vs the oracle %.2e" % (len(rec["systems"]), worst))
+
+
 def test_256_kappa_sampled_rows_and_first_solve(M):
     w = pb.WORKLOADS["kappa3d_256"]
     A = w.matrix()
