@@ -207,6 +207,19 @@ def FP32_INNER_OPTS(M):
     return dict(precision=M.PREC_FP32_INNER, inner_ell=1, fetch_policy=M.FETCH_NEVER, max_outer=40)
 
 
+def workload_config(w, n, nnz, W, K, form, world):
+    """The `config` object of both arms' JSON lines."""
+    dims = "x".join(str(d) for d in w.shape)
+    return {"workload": f"{w.name}: 3D convection-diffusion, 7-point FD on a {dims} grid (N={n}, nnz={nnz}), "
+                        f"beta={tuple(w.beta)}, implicit Euler tau={w.tau}, systems {W + 1}..{W + K} of the sequence",
+            "method": {"fp64": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
+                       "fp32_inner": f"FP32-inner M({w.s})stab(1) with FP64 defect correction, SELL-32",
+                       "idrstab": f"IDR({w.s})stab({w.ell}), Arnoldi start per system, FP64, SELL-32"}[form],
+            "true_residual": "replaced every cycle" if w.replace_every == 1 else "checked at convergence",
+            "tol": w.tol, "l2": "inputs larger than L2 (matrix 0.18 GB + ~90 vectors of 16.8 MB), no flush",
+            "parallelism": "replicas" if world > 1 else "single GPU"}
+
+
 def extra_mvs(w, cyc):
     """Products with A per system outside the level steps: r0 = b - A x0, and
     the true residuals (one per replace_every cycles, else one to confirm)."""
@@ -269,14 +282,15 @@ def run_cpu_sample(args, level_steps, k0=0):
 def reference_arm(args):
     """--impl reference: the oracle on the host cores, same metric and unit.
     Each step is one level step of Algorithm 1 (k cycling through 0..l-1);
-    ms/system = mean level-step time x l x cycles per system + 2 MVs (r0 and
-    the true residual), the cycles per system taken from the oracle's own
-    committed record of the same systems."""
+    ms/system = mean level-step time x l x cycles per system + the products
+    for r0 and the true residuals, the cycles per system taken from the
+    oracle's own committed record of the same systems."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
     from paper_1604_06043_gb300 import problems as pb
     w = pb.WORKLOADS[args.workload]
+    nnz = w.matrix().nnz
     res = run_cpu_sample(args, args.warmup + args.steps)
     timed = res["level_step_s"][args.warmup:]
     g = golden_cycles(args.warmup + 1, args.steps)
@@ -289,7 +303,8 @@ def reference_arm(args):
     line = {"impl": "reference", "metric": METRIC, "value": ms, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.mean(timed) * 1e3,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic (seeded)", "config": {"workload": args.workload},
+            "data": "synthetic (seeded generators; the paper's ocean data is not available)",
+            "config": workload_config(w, w.n, nnz, args.warmup, args.steps, "fp64", world),
             "cpu_baseline": {"value": ms, "unit": UNIT, "cores": res["threads"], "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": ms, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -525,15 +540,7 @@ def main(argv=None):
             "ms_per_step": round(T / K, 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f32+f64" if args.form == "fp32_inner" else "f64",
             "data": "synthetic (seeded generators; the paper's ocean data is not available)",
-            "config": {"workload": f"{w.name}: 3D convection-diffusion, 7-point FD on a 128^3 grid (N={A.n}, "
-                                   f"nnz={A.nnz}), beta=(20,10,5), implicit Euler tau={w.tau}, systems "
-                                   f"{W + 1}..{W + K} of the sequence",
-                       "method": {"fp64": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
-                                  "fp32_inner": f"FP32-inner M({w.s})stab(1) with FP64 defect correction, SELL-32",
-                                  "idrstab": f"IDR({w.s})stab({w.ell}), Arnoldi start per system, FP64, SELL-32"}[args.form],
-                       "true_residual": "replaced every cycle" if w.replace_every == 1 else "checked at convergence",
-                       "tol": w.tol, "l2": "inputs larger than L2 (matrix 0.18 GB + ~90 vectors of 16.8 MB), no flush",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "config": workload_config(w, A.n, A.nnz, W, K, args.form, world),
             "mvs_per_system": round(statistics.mean(mvs), 2), "cycles_per_system": round(cycles / K, 3),
             "relres_true_max": max(t["relres_true"] for t in timed),
             "system1": {"ms": round(warm[0]["ms"], 3), "mvs": warm[0]["mvs"], "cycles": warm[0]["cycles"]} if warm else None,
