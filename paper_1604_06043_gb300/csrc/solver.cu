@@ -84,6 +84,17 @@ struct msstab_s {
   int64_t launches = 0;
   int64_t mvs32 = 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // instantiated CUDA graphs of one cycle's launch sequence, by (precision,
+  // degree, x-backup buffer, residual replacement)
+  struct CycleGraph {
+    int prec, ell;
+    const void* xb2;
+    bool replaced;
+    cudaGraphExec_t exec;
+    int launches;
+  };
+  std::vector<CycleGraph> graphs;
+  cudaStream_t cap_stream = nullptr;   // private stream the cycle is captured on (replayed on `stream`)
 
   Ctx ctx() const { return Ctx{stream, sms, rs}; }
 };
@@ -411,43 +422,76 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
                                          epi_of(EPI_GAMMA, 0, 0), w.Pb));
       need_proj = false;
     }
-    // ---- one cycle: level steps k = 0..l-1 ----
-    for (int k = 0; k < ell; ++k) {
-      LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
-      LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
-                                        &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp, w.Pb));
-      for (int q = 0; q < s; ++q) {
-        LAUNCH(MSSTAB_K_ETA, eta_eager<T>(c, n, s, w.R, w.V, ld, k, q, &st->eta[(k * SMAX + q) * SMAX]));
-        Epi next = q + 1 < s ? epi_of(EPI_ETA, k, q + 1)
-                             : (k + 1 < ell ? epi_of(EPI_GAMMA, k + 1, 0) : epi_none(h));
-        LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
-                                          &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp, w.Pb));
+    // ---- one cycle: level steps k = 0..l-1, the degree-l step, and the
+    // residual replacement; the same launch sequence every cycle ----
+    const bool replaced = ctl.replace_every > 0 && (out.cycles + 1) % ctl.replace_every == 0;
+    auto launch_cycle = [&](const Ctx& c) -> msstab_status {
+      for (int k = 0; k < ell; ++k) {
+        LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
+        LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
+                                          &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp, w.Pb));
+        for (int q = 0; q < s; ++q) {
+          LAUNCH(MSSTAB_K_ETA, eta_eager<T>(c, n, s, w.R, w.V, ld, k, q, &st->eta[(k * SMAX + q) * SMAX]));
+          Epi next = q + 1 < s ? epi_of(EPI_ETA, k, q + 1)
+                               : (k + 1 < ell ? epi_of(EPI_GAMMA, k + 1, 0) : epi_none(h));
+          LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
+                                            &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp, w.Pb));
+        }
+        LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
+                                               &st->eta[k * SMAX * SMAX], SMAX));
       }
-      LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
-                                             &st->eta[k * SMAX * SMAX], SMAX));
+      // degree-l minimisation
+      {
+        MdCols<T> cols{};
+        for (int i = 0; i <= ell; ++i) cols.x[i] = cols.y[i] = Rk(i);
+        LAUNCH(MSSTAB_K_TAU, multidot<T>(c, n, cols, ell + 1, ell + 1, 0, st->gram, ell + 1,
+                                         epi_of(EPI_TAU, 0, 0)));
+      }
+      LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
+                                         epi_of(EPI_GAMMA, 0, 0), w.Pb));
+      // residual replacement at the cycle end: r = b - A x with P^T r and ||r||^2 in the same pass
+      // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
+      // level step from P^T V (left by tau_update) in the epilogue
+      if (replaced)
+        LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
+                                          epi_of(EPI_GAMMA, 0, 0), w.Pil, w.sp, w.Pb));
+      return MSSTAB_OK;
+    };
+    if (h->tm.on) {
+      CKS(launch_cycle(c));   // per-launch event timing: plain launches
+    } else {
+      // replay the captured launch sequence (captured on first use)
+      msstab_s::CycleGraph* g = nullptr;
+      for (auto& e : h->graphs)
+        if (e.prec == prec && e.ell == ell && e.xb2 == (const void*)w.XB2 && e.replaced == replaced) g = &e;
+      if (!g) {
+        const int64_t l0 = h->launches;
+        if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+        Ctx cc = c;
+        cc.stream = h->cap_stream;
+        cudaGraph_t graph = nullptr;
+        CK(cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+        const msstab_status cs = launch_cycle(cc);
+        const cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+        if (cs != MSSTAB_OK) {
+          if (graph) cudaGraphDestroy(graph);
+          return cs;
+        }
+        if (ce != cudaSuccess) return cuda_fail(h, ce, "cudaStreamEndCapture");
+        cudaGraphExec_t exec = nullptr;
+        const cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) return cuda_fail(h, ie, "cudaGraphInstantiate");
+        h->graphs.push_back({prec, ell, (const void*)w.XB2, replaced, exec, (int)(h->launches - l0)});
+        h->launches = l0;
+        g = &h->graphs.back();
+      }
+      CK(cudaGraphLaunch(g->exec, h->stream));
+      h->launches += g->launches;
     }
-    // ---- degree-l minimisation ----
-    {
-      MdCols<T> cols{};
-      for (int i = 0; i <= ell; ++i) cols.x[i] = cols.y[i] = Rk(i);
-      LAUNCH(MSSTAB_K_TAU, multidot<T>(c, n, cols, ell + 1, ell + 1, 0, st->gram, ell + 1,
-                                       epi_of(EPI_TAU, 0, 0)));
-    }
-    LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
-                                       epi_of(EPI_GAMMA, 0, 0), w.Pb));
-    out.mvs += cyc_mvs;
-    if (prec) h->mvs32 += cyc_mvs;
+    out.mvs += cyc_mvs + (replaced ? 1 : 0);
+    if (prec) h->mvs32 += cyc_mvs + (replaced ? 1 : 0);
     out.cycles += 1;
-    // residual replacement at the cycle end: r = b - A x with P^T r and ||r||^2 in the same pass
-    // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
-    // level step from P^T V (left by tau_update) in the epilogue
-    const bool replaced = ctl.replace_every > 0 && out.cycles % ctl.replace_every == 0;
-    if (replaced) {
-      LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
-                                        epi_of(EPI_GAMMA, 0, 0), w.Pil, w.sp, w.Pb));
-      out.mvs += 1;
-      if (prec) h->mvs32 += 1;
-    }
     // ---- cycle end: the one host synchronisation ----
     CK(cudaMemcpyAsync(h->h_small, replaced ? &st->projR[s] : &st->rr, sizeof(double), cudaMemcpyDeviceToHost,
                        h->stream));
@@ -778,6 +822,8 @@ msstab_status msstab_destroy(msstab_t h) {
   if (h->e1) cudaEventDestroy(h->e1);
   if (h->h_small) cudaFreeHost(h->h_small);
   if (h->h_stage) cudaFreeHost(h->h_stage);
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
   return MSSTAB_OK;
 }
@@ -1008,22 +1054,14 @@ msstab_status msstab_solve_host(msstab_t h, const double* b, double* x, double t
   CKS(check_handle(h));
   if (!b || !x) return fail(h, MSSTAB_ERR_INVALID_ARG, "b or x is NULL");
   const size_t bytes = sizeof(double) * h->n;
-  if (!h->h_stage) {
-    cudaError_t e = cudaMallocHost((void**)&h->h_stage, 2 * bytes);
-    if (e != cudaSuccess) {
-      h->h_stage = nullptr;
-      return cuda_fail(h, e, "cudaMallocHost(staging)");
-    }
-  }
-  std::memcpy(h->h_stage, b, bytes);
-  std::memcpy(h->h_stage + h->n, x, bytes);
-  CK(cudaMemcpyAsync(h->w64.B, h->h_stage, bytes, cudaMemcpyHostToDevice, h->stream));
-  CK(cudaMemcpyAsync(h->w64.X, h->h_stage + h->n, bytes, cudaMemcpyHostToDevice, h->stream));
+  // b and x go straight between the caller's memory and the device (the
+  // driver stages pageable memory itself, in pipelined chunks)
+  CK(cudaMemcpyAsync(h->w64.B, b, bytes, cudaMemcpyHostToDevice, h->stream));
+  CK(cudaMemcpyAsync(h->w64.X, x, bytes, cudaMemcpyHostToDevice, h->stream));
   msstab_status rc = solve_common(h, tol, st);
   if (rc == MSSTAB_OK || rc == MSSTAB_ERR_MAXIT || rc == MSSTAB_ERR_NAN || rc == MSSTAB_ERR_BREAKDOWN) {
-    CK(cudaMemcpyAsync(h->h_stage + h->n, h->w64.X, bytes, cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(x, h->w64.X, bytes, cudaMemcpyDeviceToHost, h->stream));
     CK(cudaStreamSynchronize(h->stream));
-    std::memcpy(x, h->h_stage + h->n, bytes);
   }
   return rc;
 }
