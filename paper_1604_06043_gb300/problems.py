@@ -136,6 +136,30 @@ def tridiag(n: int, sub: float, diag: float, sup: float) -> CSR:
     return _from_stencil(cols, vals, mask)
 
 
+def random_sparse(n: int, per_row: int, seed: int, band: Optional[int] = None) -> CSR:
+    """A random sparse matrix with a general (non-stencil) pattern: each row
+    holds its diagonal and up to per_row distinct off-diagonal columns drawn
+    uniformly (from |j - i| <= band if band is given), columns sorted; the
+    off-diagonal values are uniform in [-1, 1) and the diagonal is one plus the
+    row's sum of their magnitudes (strict diagonal dominance)."""
+    rng = np.random.default_rng(seed)
+    rp = [0]
+    cols, vals = [], []
+    for i in range(n):
+        lo, hi = (0, n) if band is None else (max(0, i - band), min(n, i + band + 1))
+        cand = rng.integers(lo, hi, size=per_row)
+        off = np.unique(cand[cand != i])
+        v = rng.uniform(-1.0, 1.0, size=off.size)
+        c = np.concatenate([off, [i]])
+        w = np.concatenate([v, [1.0 + np.abs(v).sum()]])
+        o = np.argsort(c)
+        cols.append(c[o])
+        vals.append(w[o])
+        rp.append(rp[-1] + c.size)
+    return CSR(n, np.array(rp, dtype=np.int32), np.concatenate(cols).astype(np.int32),
+               np.concatenate(vals).astype(np.float64))
+
+
 def termination_rhs(n: int = 40):
     """The two right-hand sides of the finite-termination experiments (Section 5.2):
     b1 = (1, ..., 1) and b2_i = sin(2 pi i / n), i = 1..n."""
