@@ -36,12 +36,12 @@ METRIC = "ms/system & #MVs for 128³ implicit-Euler seq at 1e-8 rel res; SpMV HB
 UNIT = "ms/system"
 WORKLOAD = "convdiff3d_128"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_128.json")
-FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn"]
+FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
-# DRAM bytes (read + write) of one launch of the dominant kernel of the FP64
-# form, from one ncu capture of the current kernel at 128^3
-# (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md); None for other forms.
-NCU_TRAFFIC = {("fp64", "spmv_dot"): 341_992_448}
+# DRAM bytes (read + write) of one launch of the dominant kernel of each form,
+# from one ncu capture of the current kernel at 128^3
+# (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md, ..._fp32inner_...).
+NCU_TRAFFIC = {("fp64", "spmv_dot"): 342_601_472, ("fp32_inner", "spmv_dot"): 200_179_712}
 
 
 def parse_args(argv=None):
@@ -419,6 +419,35 @@ def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300,
     return out
 
 
+def ilu_report(V, A, tv, create_ms):
+    """The ILU(0) split-preconditioned variant: level schedules, the time of
+    one triangular sweep and what bounds it.  A sweep reads, per row, its
+    strict lower (or upper) entries (8-byte value + 4-byte column), the row
+    pointer, diagonal position and level-order index (4 bytes each), the
+    right-hand side and writes the solution (8 bytes each); with the diagonal
+    for the upper sweep: about 12 nnz/2 + 28 n bytes (nnz/2: half of the
+    off-diagonal entries on each side)."""
+    info = V.op_ilu_levels()
+    t_ms = sum(t["t_ms"]["precond"] for t in tv)
+    n_l = sum(t["n_launch"]["precond"] for t in tv)
+    off = A.nnz - A.n
+    sweep_bytes = 12 * off / 2 + 28 * A.n
+    us = t_ms / max(1, n_l) * 1e3
+    return {"create_ms": round(create_ms, 1),
+            "levels_lower_upper": [info[0], info[1]], "widest_level": [info[2], info[3]],
+            "sweep_blocks": [info[4], info[5]],
+            "precond_launches_per_system": round(n_l / max(1, len(tv)), 1),
+            "precond_ms_per_system": round(t_ms / max(1, len(tv)), 3),
+            "sweep_us": round(us, 2), "us_per_level": round(us / max(1, (info[0] + info[1]) / 2), 3),
+            "sweep_alg_bytes": int(sweep_bytes),
+            "sweep_GBps": round(sweep_bytes / (us * 1e-6) / 1e9, 1) if us > 0 else None,
+            "relres_orig_max": max(t["relres_orig"] for t in tv),
+            "note": "level-scheduled: one cooperative launch per triangular solve, a grid barrier between "
+                    "levels; bound by the levels' latency (about 3n - 2 planes for a 7-point stencil), "
+                    "not by HBM"}
+
+
+
 def run_sequence(M, torch, S, f, x, b, tau, tol, count, collect=None, check=True):
     out = []
     for _ in range(count):
@@ -597,10 +626,15 @@ def main(argv=None):
         for name, opts, praw in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER), None),
                                  ("msstab_fp32_inner", FP32_INNER_OPTS(M), None),
                                  ("msstab_fp64_block_p", {}, p_block),
-                                 ("msstab_fp32_inner_block_p", FP32_INNER_OPTS(M), p_block)):
+                                 ("msstab_fp32_inner_block_p", FP32_INNER_OPTS(M), p_block),
+                                 ("msstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1), None),
+                                 ("idrstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1,
+                                                            fetch_policy=M.FETCH_NEVER), None)):
           try:
+            c0 = time.perf_counter()
             V = M.Solver(A, w.s, w.ell, w.p_raw() if praw is None else praw, device=dev,
                          replace_every=w.replace_every, **opts)
+            create_ms = (time.perf_counter() - c0) * 1e3
             xv = torch.tensor(x0_np, device=dev)
             run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W, check=False)
             torch.cuda.synchronize()
@@ -624,6 +658,8 @@ def main(argv=None):
                 variants[name]["_xs"] = xs_list
             if praw is not None:
                 variants[name]["cut_space"] = "block-partitioned N(0,1), seed 3 (rows (i // 32) mod s)"
+            if "ilu0" in name:
+                variants[name].update(ilu_report(V, A, tv, create_ms))
             V.close()
           except Exception as e:  # a failing variant is reported, the main line still stands
             variants[name] = {"error": str(e)[-300:]}
