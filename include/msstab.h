@@ -47,6 +47,7 @@ typedef enum msstab_status {
 enum { MSSTAB_PREC_FP64 = 0, MSSTAB_PREC_FP32_INNER = 1 };
 enum { MSSTAB_FETCH_ONCE = 0, MSSTAB_FETCH_EVERY = 1, MSSTAB_FETCH_NEVER = 2 };
 enum { MSSTAB_FORMAT_SELL = 0, MSSTAB_FORMAT_CSR = 1 };
+enum { MSSTAB_PRECOND_NONE = 0, MSSTAB_PRECOND_ILU0 = 1 };
 
 /* Kernel families, the index into msstab_stats.t_ms / n_launch. */
 enum {
@@ -58,7 +59,8 @@ enum {
   MSSTAB_K_TAU = 5,      /* Gram, tau step, P^T [r, V] */
   MSSTAB_K_OTHER = 6,    /* Arnoldi start, orthonormalisation, conversions, copies */
   MSSTAB_K_CNN = 7,      /* learned initial guess */
-  MSSTAB_K_COUNT = 8
+  MSSTAB_K_PRECOND = 8,  /* ILU(0) triangular solves and U x (the preconditioned operator) */
+  MSSTAB_K_COUNT = 9
 };
 
 typedef struct msstab_options {
@@ -94,10 +96,17 @@ typedef struct msstab_options {
   int32_t replace_every;   /* > 0: replace the recursive residual by the true residual b - A x at
                               the end of every replace_every-th cycle (one product with A, fused
                               with the projections the next cycle needs), as the preconditioned
-                              experiment of Section 6 does after each cycle; bounds the gap that
+                              experiment of Section 5.1 does after each cycle; bounds the gap that
                               the drift of V from A U opens between the two.  0 (default):
                               Algorithm 1 as printed, true residual only to confirm convergence */
-  int32_t reserved[2];
+  int32_t precond;         /* MSSTAB_PRECOND_NONE (default) or MSSTAB_PRECOND_ILU0: split
+                              preconditioning with the incomplete LU factorisation with zero
+                              fill-in (Section 5.1): every solve runs on L^-1 A U^-1 x~ = L^-1 b
+                              from x~0 = U x0 and returns x = U^-1 x~; the tolerance, the fetching
+                              point, the recycled U, V and replace_every refer to that system (its
+                              true residual is L^-1 (b - A U^-1 x~)).  FP64 only; A must hold every
+                              diagonal entry and strictly increasing columns in each row */
+  int32_t reserved;
   void* stream;            /* cudaStream_t for all work of the handle; NULL = default stream */
 } msstab_options;
 
@@ -117,6 +126,9 @@ typedef struct msstab_stats {
   int32_t fp64_finish;    /* FP32_INNER: 1 if the FP32 corrections stalled and FP64 IDR(s)stab(l)
                              finished the solve from the current x */
   int32_t reserved_s;
+  double relres_orig;     /* ||b - A x|| / ||b|| of the original system (differs from relres_true
+                             only with the ILU(0) preconditioner, whose relres_true is that of
+                             L^-1 A U^-1 x~ = L^-1 b) */
   double t_ms[MSSTAB_K_COUNT];     /* per kernel family, when options.kernel_timing */
   int64_t n_launch[MSSTAB_K_COUNT];
 } msstab_stats;
@@ -155,7 +167,7 @@ msstab_status msstab_create(int64_t n, int64_t nnz, const int32_t* d_row_ptr, co
 msstab_status msstab_solve(msstab_t h, const double* d_b, double* d_x, double tol, msstab_stats* st);
 
 /* As msstab_solve with host buffers b[n] and x[n]: the copies to and from the
- * device (through handle-owned staging memory) are part of the call. */
+ * device (straight from and to the caller's memory) are part of the call. */
 msstab_status msstab_solve_host(msstab_t h, const double* b, double* x, double tol, msstab_stats* st);
 
 /* Free all device and host memory of the handle.  NULL is accepted. */
@@ -270,6 +282,27 @@ msstab_status msstab_op_small_solve(msstab_t h, int32_t n, const double* d_M, co
  * equations of min ||r^(0) - Z tau||, diagonally scaled, by Cholesky (LU if
  * that fails); tau = 0 if a level vector is zero. */
 msstab_status msstab_op_tau_solve(msstab_t h, int32_t ell, const double* d_gram, double* d_tau);
+
+/* ILU(0) of a handle created with MSSTAB_PRECOND_ILU0 (Section 5.1's split
+ * preconditioner).  The factor is stored on A's CSR pattern: entries left of
+ * the diagonal are L (unit lower; its diagonal is implicit), the others U.
+ * It is computed row by row by the IKJ elimination with every update outside
+ * the pattern dropped, each update one rounded product and one rounded
+ * difference, so it equals the sequential textbook factor bit for bit.
+ * msstab_op_ilu_factor copies the nnz factor values to d_lu (CSR order).
+ * msstab_op_ilu_levels copies the level of every row in the lower and upper
+ * dependency graphs (the longest chain of strict lower / strict upper
+ * dependencies below it; rows of one level are computed in parallel) to
+ * d_lev_lower[n], d_lev_upper[n] (either may be NULL) and writes
+ * h_info[0..5] = levels (lower, upper), widest level (lower, upper), blocks of
+ * the sweeps (lower, upper).
+ * msstab_op_ilu_apply: which = 0: d_out = L^-1 d_in; 1: d_out = U^-1 d_in;
+ * 2: d_out = U d_in; 3: d_out = L^-1 A U^-1 d_in.  d_out may equal d_in for 0,
+ * 1 and 3, not for 2.  All three block until done.  INVALID_ARG without the
+ * preconditioner; CUDA if a grid barrier of the sweeps timed out. */
+msstab_status msstab_op_ilu_factor(msstab_t h, double* d_lu);
+msstab_status msstab_op_ilu_levels(msstab_t h, int32_t* d_lev_lower, int32_t* d_lev_upper, int32_t* h_info);
+msstab_status msstab_op_ilu_apply(msstab_t h, int32_t which, const double* d_in, double* d_out);
 
 /* ---------------------------------------------------------------------------
  * Learned initial guess (not in the paper; the workload's learned-x0 form).

@@ -329,7 +329,7 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
     Algorithm 1 requires V = A U of its inputs.
     ``replace_every`` > 0 replaces the recursive residual by b - A x (one
     counted MV) at the end of every replace_every-th cycle, as the
-    preconditioned experiment of Section 6 does after each cycle; the stopping
+    preconditioned experiment of Section 5.1 does after each cycle; the stopping
     test then needs no confirming product.
     ``inspect(stage, state)`` is called after the level loop ("levels") and at
     each cycle end ("cycle") for the invariant tests."""

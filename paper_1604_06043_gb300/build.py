@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT = os.path.join(HERE, "_build")
-SOURCES = ["spmv.cu", "blas.cu", "solver.cu", "cnn.cu"]
+SOURCES = ["spmv.cu", "blas.cu", "solver.cu", "cnn.cu", "ilu.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE,
                 "-diag-suppress", "177"]

@@ -4,7 +4,8 @@
 // over a fixed row mapping, reduces per block in a fixed tree, writes one
 // partial per block and takes a ticket; the last block to arrive sums the
 // partials in index order.  The result does not depend on the order in which
-// blocks run, and no thread ever waits on another block (no spin-waits).
+// blocks run, and no reduction ever waits on another block (the one bounded
+// wait of the library is the grid barrier of the ILU(0) level sweeps).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -25,6 +26,10 @@ constexpr double CHOLQR_REL_TOL = 1e-14;   // rank test of the Cholesky QR
 // Flags raised on the device and read by the host at the cycle end.
 constexpr int FLAG_BREAKDOWN = 1;
 constexpr int FLAG_CHOL = 2;
+constexpr int FLAG_SYNC_TIMEOUT = 4;   // a grid barrier of the ILU(0) sweeps gave up waiting
+constexpr int FLAG_ZERO_PIVOT = 8;     // ILU(0) factor: u_ii == 0
+constexpr int FLAG_NO_DIAG = 16;       // ILU(0) set-up: a row without a diagonal entry
+constexpr int FLAG_UNSORTED = 32;      // ILU(0) set-up: columns of a row not strictly increasing
 
 // ---------------------------------------------------------------------------
 // device-resident state of one solve: projections, coefficients, norms

@@ -1,0 +1,575 @@
+// ILU(0) split preconditioning (the ocean experiment of Section 5.1): the
+// systems L^-1 A U^-1 x~ = L^-1 b with L unit lower and U upper triangular on
+// the sparsity pattern of A, the incomplete LU factorisation with zero fill-in.
+//
+// Factor.  Row i is reduced by the finished rows k < i of its strict lower
+// part, in increasing k (the IKJ form of Gaussian elimination), and every
+// update that would land outside A's pattern is dropped: l_ik = a_ik / u_kk,
+// then a_ij -= l_ik u_kj for the j > k that rows i and k share.  Each update is
+// a rounded multiplication followed by a rounded subtraction (no fused
+// multiply-add), so the factor is the textbook sequential one bit for bit.
+// The values are stored on A's CSR pattern: left of the diagonal L (unit
+// diagonal implicit), from the diagonal on U.
+//
+// Schedule.  Row i of the factor and of the lower solve needs the rows of its
+// strict lower part finished first; the upper solve needs those of its strict
+// upper part.  The level of a row is the length of the longest such chain
+// below it, so all rows of one level are independent: they are computed in
+// parallel, level after level, in ONE cooperative launch whose blocks meet at
+// a grid barrier between levels (a 7-point stencil on an n^3 grid in natural
+// order has 3n - 2 levels, the planes x + y + z = const).  The levels are
+// found on the device by relaxing lev(i) = 1 + max lev(j) over the
+// dependencies until nothing changes (values only grow towards the fixed
+// point), then rows are bucketed by level with a counting sort.
+//
+// The barrier between levels is the only place where a thread waits on
+// another block.  Every block of a cooperative launch is resident and runs the
+// same number of barriers.  The barrier is a counter, zeroed before the
+// launch, that thread 0 of every block raises by one with release semantics
+// after its block's rows (so the rows' stores are visible first) and then polls
+// with acquire loads until it reaches (level + 1) x blocks.  Every wait is
+// bounded: after BAR_SPIN_LIMIT polls the block raises FLAG_SYNC_TIMEOUT in
+// the device flag word and leaves, the blocks still waiting see the flag and
+// leave too, and the host reads the flag at the next cycle end.  Values
+// written by other blocks are read through L2 (__ldcg), never from a possibly
+// stale L1 line.
+
+#include <algorithm>
+#include <vector>
+
+#include "launch.h"
+#include "msstab.h"
+
+namespace msk {
+
+constexpr int ITS = 256;                       // threads per block of the level sweeps
+constexpr long long BAR_SPIN_LIMIT = 1LL << 22;
+
+__device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// The barrier after level l (see the file comment): false if it timed out.
+__device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned int target, int* flag) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    red_release_add(count, 1u);
+    for (long long it = 0; ld_acquire(count) < target; ++it) {
+      if ((it & 255) == 255 && (*(const volatile int*)flag & FLAG_SYNC_TIMEOUT)) {
+        ok = 0;
+        break;
+      }
+      if (it > BAR_SPIN_LIMIT) {
+        atomicOr(flag, FLAG_SYNC_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+enum SweepMode { SW_FACTOR = 0, SW_LOWER = 1, SW_UPPER = 2 };
+
+struct SweepArgs {
+  int nlev;
+  const int* lptr;     // rows of level l: rows[lptr[l] .. lptr[l+1])
+  const int* rows;
+  const int* rp;
+  const int* col;
+  const int* dg;
+  double* lu;
+  const double* in;    // right-hand side (the solves)
+  double* out;         // solution (may equal in)
+  unsigned int* count; // barrier counter (zero at launch)
+  int* flag;
+};
+
+template <int MODE>
+__global__ void __launch_bounds__(ITS) ilu_sweep_kernel(SweepArgs a) {
+  const int G = gridDim.x * ITS;
+  const int tid = blockIdx.x * ITS + threadIdx.x;
+  for (int l = 0; l < a.nlev; ++l) {
+    const int beg = a.lptr[l], end = a.lptr[l + 1];
+    for (int idx = beg + tid; idx < end; idx += G) {
+      const int i = a.rows[idx];
+      const int rb = a.rp[i], re = a.rp[i + 1], d = a.dg[i];
+      if constexpr (MODE == SW_FACTOR) {
+        for (int p = rb; p < d; ++p) {
+          const int k = a.col[p];
+          const double piv = __ldcg(a.lu + a.dg[k]);
+          const double lik = __ddiv_rn(__ldcg(a.lu + p), piv);
+          __stcg(a.lu + p, lik);
+          int q = a.dg[k] + 1, t = p + 1;
+          const int qe = a.rp[k + 1];
+          while (q < qe && t < re) {
+            const int cq = a.col[q], ct = a.col[t];
+            if (cq == ct) {
+              __stcg(a.lu + t, __dsub_rn(__ldcg(a.lu + t), __dmul_rn(lik, __ldcg(a.lu + q))));
+              ++q;
+              ++t;
+            } else if (cq < ct) {
+              ++q;
+            } else {
+              ++t;
+            }
+          }
+        }
+        if (__ldcg(a.lu + d) == 0.0) atomicOr(a.flag, FLAG_ZERO_PIVOT);
+      } else if constexpr (MODE == SW_LOWER) {
+        double sum = a.in[i];
+        for (int p = rb; p < d; ++p) sum = fma(-a.lu[p], __ldcg(a.out + a.col[p]), sum);
+        __stcg(a.out + i, sum);
+      } else {
+        double sum = a.in[i];
+        for (int p = d + 1; p < re; ++p) sum = fma(-a.lu[p], __ldcg(a.out + a.col[p]), sum);
+        __stcg(a.out + i, sum / a.lu[d]);
+      }
+    }
+    if (l + 1 < a.nlev && !level_barrier(a.count, (unsigned)(l + 1) * gridDim.x, a.flag)) return;
+  }
+}
+
+// The packed solves, level by level.  Each level's segment of the packed order
+// is padded to a multiple of 32 positions (padding holds row -1), so the lanes
+// of a warp work on rows of one level.  Nothing a row needs except the
+// solution values of earlier levels depends on the solve, so the next level's
+// row data (row index, dependencies, factor values, right-hand side) is loaded
+// before the barrier that ends the current level; a row's dependency values
+// are then gathered in one round trip through L2.  Sums run over the
+// dependencies in column order, as the CSR sweep.
+struct PackedArgs {
+  int n;                 // padded positions
+  const int* rows;       // row of each position, -1 for padding
+  const int* pcnt;
+  const int* pcol;
+  const double* pval;
+  const double* pdiag;   // upper solve: u_ii by position; NULL: unit diagonal
+  const double* in;
+  double* out;           // may equal in
+  int* flag;
+};
+
+template <int W>
+struct RowData {
+  int row, cnt;
+  int col[W];
+  double val[W];
+  double rhs, diag;
+};
+
+template <int W>
+__device__ __forceinline__ void load_row(const PackedArgs& a, int idx, RowData<W>& r) {
+  r.row = __ldg(a.rows + idx);
+  r.cnt = __ldg(a.pcnt + idx);      // 0 for padding
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    if (j < r.cnt) {
+      r.col[j] = __ldg(a.pcol + (int64_t)j * a.n + idx);
+      r.val[j] = __ldg(a.pval + (int64_t)j * a.n + idx);
+    }
+  }
+  // a plain load: with in == out other rows of in change during the launch
+  // (this row's entry does not before the row is solved)
+  r.rhs = r.row >= 0 ? a.in[r.row] : 0.0;
+  r.diag = a.pdiag ? __ldg(a.pdiag + idx) : 1.0;
+}
+
+struct LevelArgs {
+  PackedArgs p;
+  int nlev;
+  const int* pptr;       // padded positions of level l: [pptr[l], pptr[l+1])
+  unsigned int* count;
+};
+
+template <int W>
+__device__ __forceinline__ void level_row(const PackedArgs& a, const RowData<W>& r) {
+  double x[W];
+#pragma unroll
+  for (int j = 0; j < W; ++j) x[j] = j < r.cnt ? __ldcg(a.out + r.col[j]) : 0.0;
+  double sum = r.rhs;
+#pragma unroll
+  for (int j = 0; j < W; ++j)
+    if (j < r.cnt) sum = fma(-r.val[j], x[j], sum);
+  if (a.pdiag) sum = sum / r.diag;
+  if (r.row >= 0) __stcg(a.out + r.row, sum);
+}
+
+template <int W>
+__global__ void __launch_bounds__(ITS) ilu_sweep_level_kernel(LevelArgs L) {
+  const PackedArgs& a = L.p;
+  const int G = gridDim.x * ITS;
+  const int tid = blockIdx.x * ITS + threadIdx.x;
+  RowData<W> nxt;
+  int beg = L.pptr[0], end = L.pptr[1];
+  if (beg + tid < end) load_row<W>(a, beg + tid, nxt);
+  for (int l = 0; l < L.nlev; ++l) {
+    const bool mine = beg + tid < end;
+    const RowData<W> cur = nxt;
+    const int cbeg = beg, cend = end;
+    if (l + 1 < L.nlev) {
+      beg = L.pptr[l + 1];
+      end = L.pptr[l + 2];
+      if (beg + tid < end) load_row<W>(a, beg + tid, nxt);
+    }
+    if (mine) {
+      level_row<W>(a, cur);
+      for (int idx = cbeg + tid + G; idx < cend; idx += G) {   // levels wider than the grid
+        RowData<W> r;
+        load_row<W>(a, idx, r);
+        level_row<W>(a, r);
+      }
+    }
+    if (l + 1 < L.nlev && !level_barrier(L.count, (unsigned)(l + 1) * gridDim.x, a.flag)) return;
+  }
+}
+
+// dependencies of the level-ordered rows: count and the widest row
+// (W == 0: only the widest row into *maxdeps.)  Position idx of the level
+// order goes to padded position pptr[l] + (idx - lptr[l]) of its level l.
+__global__ void ilu_pack_kernel(int n, int npad, int upper, int W, const int* rows, const int* lev,
+                                const int* lptr, const int* pptr, const int* rp, const int* col, const int* dg,
+                                const double* lu, int* prow, int* pcnt, int* pcol, double* pval, double* pdiag,
+                                int* maxdeps) {
+  const int stride = gridDim.x * blockDim.x;
+  int md = 0;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
+    const int i = rows[idx];
+    const int b = upper ? dg[i] + 1 : rp[i], e = upper ? rp[i + 1] : dg[i];
+    md = max(md, e - b);
+    if (W > 0) {
+      const int l = lev[i];
+      const int pp = pptr[l] + (idx - lptr[l]);
+      prow[pp] = i;
+      pcnt[pp] = e - b;
+      for (int p = b; p < e; ++p) {
+        pcol[(int64_t)(p - b) * npad + pp] = col[p];
+        pval[(int64_t)(p - b) * npad + pp] = lu[p];
+      }
+      if (upper) pdiag[pp] = lu[dg[i]];
+    }
+  }
+  if (maxdeps) atomicMax(maxdeps, md);
+}
+
+// level sizes rounded up to whole warps
+__global__ void ilu_pad_counts_kernel(int nlev, const int* lptr, int* cnt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int l = blockIdx.x * blockDim.x + threadIdx.x; l < nlev; l += stride)
+    cnt[l] = (lptr[l + 1] - lptr[l] + 31) / 32 * 32;
+}
+
+// y = U x (the upper factor including its diagonal)
+__global__ void ilu_upper_mul_kernel(int n, const int* rp, const int* col, const int* dg, const double* lu,
+                                     const double* x, double* y) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    double sum = 0.0;
+    for (int p = dg[i]; p < rp[i + 1]; ++p) sum = fma(lu[p], x[col[p]], sum);
+    y[i] = sum;
+  }
+}
+
+// diagonal positions; flag: FLAG_NO_DIAG if a row has none, FLAG_UNSORTED if
+// the columns of a row are not strictly increasing
+__global__ void ilu_diag_kernel(int n, const int* rp, const int* col, int* dg, int* flag) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int d = -1;
+    for (int p = rp[i]; p < rp[i + 1]; ++p) {
+      if (p > rp[i] && col[p] <= col[p - 1]) atomicOr(flag, FLAG_UNSORTED);
+      if (col[p] == i) d = p;
+    }
+    if (d < 0) {
+      atomicOr(flag, FLAG_NO_DIAG);
+      d = rp[i];
+    }
+    dg[i] = d;
+  }
+}
+
+// one relaxation sweep of lev(i) = max(0, 1 + max lev(j)) over the strict
+// lower (upper == 0) or strict upper dependencies of row i
+__global__ void ilu_level_relax_kernel(int n, const int* rp, const int* col, const int* dg, int* lev, int upper,
+                                       int* changed) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const int b = upper ? dg[i] + 1 : rp[i], e = upper ? rp[i + 1] : dg[i];
+    int m = 0;
+    for (int p = b; p < e; ++p) m = max(m, __ldcg(lev + col[p]) + 1);
+    if (m != __ldcg(lev + i)) {
+      __stcg(lev + i, m);
+      *(volatile int*)changed = 1;
+    }
+  }
+}
+
+__global__ void ilu_level_max_kernel(int n, const int* lev, int* out) {
+  const int stride = gridDim.x * blockDim.x;
+  int m = 0;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) m = max(m, lev[i]);
+  atomicMax(out, m);
+}
+
+__global__ void ilu_level_hist_kernel(int n, const int* lev, int* cnt) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) atomicAdd(cnt + lev[i], 1);
+}
+
+// exclusive scan of cnt[0..m) into ptr[0..m] and the largest count, one block
+__global__ void ilu_level_scan_kernel(int m, const int* cnt, int* ptr, int* maxw) {
+  __shared__ int sh[1024];
+  __shared__ int carry_s;
+  int mw = 0;
+  if (threadIdx.x == 0) carry_s = 0;
+  __syncthreads();
+  for (int base = 0; base < m; base += 1024) {
+    const int i = base + threadIdx.x;
+    const int v = i < m ? cnt[i] : 0;
+    mw = max(mw, v);
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      const int add = threadIdx.x >= off ? sh[threadIdx.x - off] : 0;
+      __syncthreads();
+      sh[threadIdx.x] += add;
+      __syncthreads();
+    }
+    const int carry = carry_s;
+    if (i < m) ptr[i] = carry + sh[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry_s = carry + sh[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ptr[m] = carry_s;
+  atomicMax(maxw, mw);
+}
+
+__global__ void ilu_level_scatter_kernel(int n, const int* lev, int* cursor, int* rows) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) rows[atomicAdd(cursor + lev[i], 1)] = i;
+}
+
+static int stream_grid(const Ctx& c, int64_t n) {
+  int64_t g = (n + NT - 1) / NT;
+  if (g > (int64_t)c.sms * 8) g = (int64_t)c.sms * 8;
+  return (int)(g < 1 ? 1 : g);
+}
+
+template <int MODE>
+static cudaError_t launch_sweep(const Ctx& c, const IluDesc& F, int u, const double* in, double* out) {
+  cudaError_t e = cudaMemsetAsync(&F.bar->count, 0, sizeof(unsigned int), c.stream);
+  if (e != cudaSuccess) return e;
+  SweepArgs a{F.nlev[u], F.lptr[u], F.lrows[u], F.row_ptr, F.col, F.diag, F.lu, in, out, &F.bar->count, F.flag};
+  void* args[] = {&a};
+  return cudaLaunchCooperativeKernel((const void*)ilu_sweep_kernel<MODE>, dim3(F.grid[u]), dim3(ITS), args, 0,
+                                     c.stream);
+}
+
+// A triangular solve: the packed sweep when every row has at most 8
+// dependencies, else the CSR sweep.  in == out is allowed.
+static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const double* in, double* out) {
+  if (F.W[u] == 0)
+    return u == 0 ? launch_sweep<SW_LOWER>(c, F, 0, in, out) : launch_sweep<SW_UPPER>(c, F, 1, in, out);
+  cudaError_t e = cudaMemsetAsync(&F.bar->count, 0, sizeof(unsigned int), c.stream);
+  if (e != cudaSuccess) return e;
+  PackedArgs p{F.npad[u], F.prow[u], F.pcnt[u], F.pcol[u], F.pval[u], u == 1 ? F.pdiag[1] : nullptr, in, out,
+               F.flag};
+  LevelArgs L{p, F.nlev[u], F.pptr[u], &F.bar->count};
+  void* largs[] = {&L};
+  const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_level_kernel<4> : (const void*)ilu_sweep_level_kernel<8>;
+  return cudaLaunchCooperativeKernel(k, dim3(F.grid[u]), dim3(ITS), largs, 0, c.stream);
+}
+
+cudaError_t ilu_lower_solve(const Ctx& c, const IluDesc& F, const double* z, double* y) {
+  return solve_sweep(c, F, 0, z, y);
+}
+
+cudaError_t ilu_upper_solve(const Ctx& c, const IluDesc& F, const double* v, double* t) {
+  return solve_sweep(c, F, 1, v, t);
+}
+
+cudaError_t ilu_upper_mul(const Ctx& c, const IluDesc& F, const double* x, double* y) {
+  ilu_upper_mul_kernel<<<stream_grid(c, F.n), NT, 0, c.stream>>>(F.n, F.row_ptr, F.col, F.diag, F.lu, x, y);
+  return cudaGetLastError();
+}
+
+// Host side of the set-up: diagonal positions, both level schedules, the factor.
+IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx, int* h_scratch) {
+  IluSetupResult R{};
+  auto fail_cuda = [&](cudaError_t e, const char* where) {
+    R.code = 1;
+    R.cuda = e;
+    R.where = where;
+    return R;
+  };
+#define ICK(expr)                                  \
+  do {                                             \
+    cudaError_t e_ = (expr);                       \
+    if (e_ != cudaSuccess) return fail_cuda(e_, #expr); \
+  } while (0)
+  const int n = F.n;
+  const int g = stream_grid(c, n);
+  auto read_int = [&](const int* d, int* v) -> cudaError_t {
+    cudaError_t e = cudaMemcpyAsync(h_scratch, d, sizeof(int), cudaMemcpyDeviceToHost, c.stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c.stream);
+    *v = *h_scratch;
+    return e;
+  };
+  int* scratch = (int*)alloc(actx, 4 * sizeof(int));
+  F.diag = (int*)alloc(actx, sizeof(int) * (size_t)n);
+  if (!scratch || !F.diag) {
+    R.code = 4;
+    return R;
+  }
+  ICK(cudaMemsetAsync(scratch, 0, 4 * sizeof(int), c.stream));
+  ilu_diag_kernel<<<g, NT, 0, c.stream>>>(n, F.row_ptr, F.col, F.diag, scratch);
+  ICK(cudaGetLastError());
+  int f = 0;
+  ICK(read_int(scratch, &f));
+  if (f) {
+    R.code = 2;
+    R.where = (f & FLAG_NO_DIAG) ? "a row of A has no diagonal entry (ILU(0) needs every a_ii in the pattern)"
+                                 : "the columns of a row of A are not strictly increasing (ILU(0) needs sorted rows)";
+    return R;
+  }
+  int nb = 0;
+  ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, ilu_sweep_kernel<SW_FACTOR>, ITS, 0));
+  int nb2 = 0, nb3 = 0;
+  ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb2, ilu_sweep_kernel<SW_LOWER>, ITS, 0));
+  ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb3, ilu_sweep_kernel<SW_UPPER>, ITS, 0));
+  nb = std::min(nb, std::min(nb2, nb3));
+  {
+    int l4 = 0, l8 = 0;
+    ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l4, ilu_sweep_level_kernel<4>, ITS, 0));
+    ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l8, ilu_sweep_level_kernel<8>, ITS, 0));
+    nb = std::min(nb, std::min(l4, l8));
+  }
+  if (nb < 1) nb = 1;
+  const int co = nb * c.sms;
+  for (int u = 0; u < 2; ++u) {
+    F.lev[u] = (int*)alloc(actx, sizeof(int) * (size_t)n);
+    if (!F.lev[u]) {
+      R.code = 4;
+      return R;
+    }
+    ICK(cudaMemsetAsync(F.lev[u], 0, sizeof(int) * (size_t)n, c.stream));
+    // sweeps in batches of 8 until a whole batch changes nothing; the levels
+    // only grow towards the fixed point, which n + 8 sweeps always reach
+    int changed = 1;
+    int64_t sweeps = 0;
+    while (changed) {
+      if (sweeps > (int64_t)n + 8) {
+        R.code = 1;
+        R.cuda = cudaErrorUnknown;
+        R.where = "level relaxation did not settle";
+        return R;
+      }
+      ICK(cudaMemsetAsync(scratch + 1, 0, sizeof(int), c.stream));
+      for (int k = 0; k < 8; ++k)
+        ilu_level_relax_kernel<<<g, NT, 0, c.stream>>>(n, F.row_ptr, F.col, F.diag, F.lev[u], u, scratch + 1);
+      ICK(cudaGetLastError());
+      sweeps += 8;
+      ICK(read_int(scratch + 1, &changed));
+    }
+    ICK(cudaMemsetAsync(scratch + 2, 0, 2 * sizeof(int), c.stream));
+    ilu_level_max_kernel<<<g, NT, 0, c.stream>>>(n, F.lev[u], scratch + 2);
+    ICK(cudaGetLastError());
+    int mx = 0;
+    ICK(read_int(scratch + 2, &mx));
+    const int nlev = mx + 1;
+    F.nlev[u] = nlev;
+    int* cnt = (int*)alloc(actx, sizeof(int) * (size_t)(nlev + 1));
+    F.lptr[u] = (int*)alloc(actx, sizeof(int) * (size_t)(nlev + 1));
+    F.lrows[u] = (int*)alloc(actx, sizeof(int) * (size_t)n);
+    if (!cnt || !F.lptr[u] || !F.lrows[u]) {
+      R.code = 4;
+      return R;
+    }
+    ICK(cudaMemsetAsync(cnt, 0, sizeof(int) * (size_t)(nlev + 1), c.stream));
+    ilu_level_hist_kernel<<<g, NT, 0, c.stream>>>(n, F.lev[u], cnt);
+    ilu_level_scan_kernel<<<1, 1024, 0, c.stream>>>(nlev, cnt, F.lptr[u], scratch + 3);
+    ICK(cudaMemcpyAsync(cnt, F.lptr[u], sizeof(int) * (size_t)nlev, cudaMemcpyDeviceToDevice, c.stream));
+    ilu_level_scatter_kernel<<<g, NT, 0, c.stream>>>(n, F.lev[u], cnt, F.lrows[u]);
+    ICK(cudaGetLastError());
+    int mw = 0;
+    ICK(read_int(scratch + 3, &mw));
+    F.max_width[u] = mw;
+    const int want = (mw + ITS - 1) / ITS;
+    F.grid[u] = std::max(1, std::min(co, want));
+  }
+  ICK(launch_sweep<SW_FACTOR>(c, F, 0, nullptr, nullptr));
+  int flag = 0;
+  ICK(read_int(F.flag, &flag));
+  if (flag & FLAG_SYNC_TIMEOUT) {
+    R.code = 1;
+    R.cuda = cudaErrorLaunchTimeout;
+    R.where = "a grid barrier of the ILU(0) factor sweep timed out";
+    return R;
+  }
+  if (flag & FLAG_ZERO_PIVOT) {
+    R.code = 3;
+    R.where = "ILU(0) met a zero pivot u_ii (the incomplete factor does not exist in this ordering)";
+    return R;
+  }
+  // packed level-ordered dependencies for the solves (rows with at most 8),
+  // each level padded to whole warps
+  for (int u = 0; u < 2; ++u) {
+    ICK(cudaMemsetAsync(scratch, 0, sizeof(int), c.stream));
+    ilu_pack_kernel<<<g, NT, 0, c.stream>>>(n, 0, u, 0, F.lrows[u], F.lev[u], F.lptr[u], nullptr, F.row_ptr,
+                                            F.col, F.diag, F.lu, nullptr, nullptr, nullptr, nullptr, nullptr,
+                                            scratch);
+    ICK(cudaGetLastError());
+    int md = 0;
+    ICK(read_int(scratch, &md));
+    const int W = md <= 4 ? 4 : (md <= 8 ? 8 : 0);
+    F.W[u] = 0;
+    if (W == 0) continue;
+    const int nlev = F.nlev[u];
+    int* pcnt_l = (int*)alloc(actx, sizeof(int) * (size_t)(nlev + 1));
+    int* pptr = (int*)alloc(actx, sizeof(int) * (size_t)(nlev + 1));
+    F.pptr[u] = pptr;
+    if (!pcnt_l || !pptr) {
+      R.code = 4;
+      return R;
+    }
+    ilu_pad_counts_kernel<<<stream_grid(c, nlev), NT, 0, c.stream>>>(nlev, F.lptr[u], pcnt_l);
+    ilu_level_scan_kernel<<<1, 1024, 0, c.stream>>>(nlev, pcnt_l, pptr, scratch + 1);
+    ICK(cudaGetLastError());
+    int npad = 0;
+    ICK(read_int(pptr + nlev, &npad));
+    F.npad[u] = npad;
+    F.prow[u] = (int*)alloc(actx, sizeof(int) * (size_t)npad);
+    F.pcnt[u] = (int*)alloc(actx, sizeof(int) * (size_t)npad);
+    F.pcol[u] = (int*)alloc(actx, sizeof(int) * (size_t)npad * W);
+    F.pval[u] = (double*)alloc(actx, sizeof(double) * (size_t)npad * W);
+    F.pdiag[u] = (double*)alloc(actx, sizeof(double) * (size_t)npad);
+    if (!F.prow[u] || !F.pcnt[u] || !F.pcol[u] || !F.pval[u] || !F.pdiag[u]) {
+      R.code = 4;
+      return R;
+    }
+    ICK(cudaMemsetAsync(F.prow[u], 0xFF, sizeof(int) * (size_t)npad, c.stream));   // -1: padding
+    ICK(cudaMemsetAsync(F.pcnt[u], 0, sizeof(int) * (size_t)npad, c.stream));
+    ICK(cudaMemsetAsync(F.pdiag[u], 0, sizeof(double) * (size_t)npad, c.stream));
+    ilu_pack_kernel<<<g, NT, 0, c.stream>>>(n, npad, u, W, F.lrows[u], F.lev[u], F.lptr[u], pptr, F.row_ptr,
+                                            F.col, F.diag, F.lu, F.prow[u], F.pcnt[u], F.pcol[u], F.pval[u],
+                                            u == 1 ? F.pdiag[u] : nullptr, nullptr);
+    ICK(cudaGetLastError());
+    F.W[u] = W;
+  }
+  ICK(cudaStreamSynchronize(c.stream));
+#undef ICK
+  return R;
+}
+
+}  // namespace msk

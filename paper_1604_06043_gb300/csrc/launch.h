@@ -136,4 +136,60 @@ cudaError_t csr_max_diag(const Ctx& c, int n, const int* row_ptr, const int* col
 cudaError_t sell_fill(const Ctx& c, int n, int nslices, const int* row_ptr, const int* col, const double* val,
                       const int* slice_ptr, const int* slice_w, const int* perm, int* scol, double* sval);
 
+// y = z (b == NULL) or y = b - z, with the reductions and the epilogue of the
+// fused product (the same out layout as spmv): the tail of a product with a
+// preconditioned operator whose last stage produced z.
+template <typename T>
+cudaError_t vec_dots(const Ctx& c, int n, const T* z, T* y, const T* b, const T* P, int64_t ldp, int np,
+                     int self, int bdot, double* out, Epi epi, const T* Pb = nullptr);
+
+// ILU(0) of A on A's own pattern and its level schedules (ilu.cu).
+struct GridBar {
+  unsigned int count;             // level-barrier counter of the running sweep
+  unsigned int pad;
+};
+struct IluDesc {
+  int n = 0;
+  const int* row_ptr = nullptr;   // A's CSR pattern (sorted columns, diagonal present)
+  const int* col = nullptr;
+  double* lu = nullptr;           // factor values on that pattern: L left of the diagonal, U from it on
+  int* diag = nullptr;            // position of a_ii in each row
+  int nlev[2] = {0, 0};           // levels of the lower [0] and upper [1] dependency graphs
+  int* lev[2] = {nullptr, nullptr};     // level of each row
+  int* lptr[2] = {nullptr, nullptr};    // rows of level l: lrows[lptr[l] .. lptr[l+1])
+  int* lrows[2] = {nullptr, nullptr};
+  int max_width[2] = {0, 0};      // rows in the widest level
+  int grid[2] = {1, 1};           // blocks of the cooperative sweeps
+  // level-ordered packed dependencies of the two solves (when every row has at
+  // most 8), each level padded to a multiple of 32 positions: position idx
+  // holds row prow[idx] (-1: padding), its pcnt dependencies
+  // pcol[j * npad + idx] with factor values pval[j * npad + idx] (column
+  // order), and for the upper solve u_ii in pdiag[1][idx]
+  int W[2] = {0, 0};              // compile-time width used (4 or 8), 0: CSR sweeps
+  int npad[2] = {0, 0};
+  int* prow[2] = {nullptr, nullptr};
+  int* pcnt[2] = {nullptr, nullptr};
+  int* pcol[2] = {nullptr, nullptr};
+  double* pval[2] = {nullptr, nullptr};
+  double* pdiag[2] = {nullptr, nullptr};
+  int* pptr[2] = {nullptr, nullptr};   // padded positions of level l: [pptr[l], pptr[l+1])
+  GridBar* bar = nullptr;         // grid-barrier state (zero between launches)
+  int* flag = nullptr;            // device flag word (FLAG_SYNC_TIMEOUT, FLAG_ZERO_PIVOT)
+};
+struct IluSetupResult {
+  int code = 0;                   // 0 ok, 1 CUDA error, 2 bad structure, 3 zero pivot, 4 out of memory
+  cudaError_t cuda = cudaSuccess;
+  const char* where = nullptr;
+};
+typedef void* (*DevAllocFn)(void* ctx, size_t bytes);
+
+// Diagonal positions, levels and the numeric factor (F.n, row_ptr, col, lu =
+// a copy of A's values, bar and flag set by the caller; lu is overwritten).
+// h_scratch: one pinned int for the read-backs.
+IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx, int* h_scratch);
+// y = L^-1 z (unit lower; y may equal z); t = U^-1 v (t may equal v); y = U x.
+cudaError_t ilu_lower_solve(const Ctx& c, const IluDesc& F, const double* z, double* y);
+cudaError_t ilu_upper_solve(const Ctx& c, const IluDesc& F, const double* v, double* t);
+cudaError_t ilu_upper_mul(const Ctx& c, const IluDesc& F, const double* x, double* y);
+
 }  // namespace msk

@@ -12,6 +12,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "launch.h"
@@ -95,6 +96,12 @@ struct msstab_s {
   };
   std::vector<CycleGraph> graphs;
   cudaStream_t cap_stream = nullptr;   // private stream the cycle is captured on (replayed on `stream`)
+  // ILU(0) split preconditioning: the solver's operator is L^-1 A U^-1
+  bool precond = false;
+  IluDesc ilu{};
+  double* ilu_t = nullptr;   // U^-1 x of the running product, then L^-1 A U^-1 x
+  double* ilu_z = nullptr;   // A U^-1 x
+  double* borig = nullptr;   // the caller's b of the running solve
 
   Ctx ctx() const { return Ctx{stream, sms, rs}; }
 };
@@ -225,6 +232,27 @@ msstab_status sync_read(msstab_t h, const void* dsrc, size_t bytes) {
 
 Epi epi_none(msstab_t h) { return Epi{EPI_NONE, 0, 0, h->s, h->ell, h->st}; }
 
+// One product with the solver's operator: A, or with the ILU(0) split
+// preconditioner L^-1 A U^-1 (upper solve, product with A, lower solve, then
+// y = z or b - z with the reductions and epilogue of the fused product).  The
+// arguments and the out layout are those of spmv.
+template <typename T>
+msstab_status amv(msstab_t h, const Ctx& c, int fam, const T* x, T* y, const T* b, const T* P, int64_t ldp,
+                  int np, int self, int bdot, double* out, Epi epi, const T* Pil = nullptr, int sp = 0,
+                  const T* Pb = nullptr) {
+  if constexpr (std::is_same<T, double>::value) {
+    if (h->precond) {
+      LAUNCH(MSSTAB_K_PRECOND, ilu_upper_solve(c, h->ilu, x, h->ilu_t));
+      LAUNCH(fam, spmv<double>(c, h->A, h->ilu_t, h->ilu_z, nullptr, nullptr, 0, 0, 0, 0, nullptr, epi_none(h)));
+      LAUNCH(MSSTAB_K_PRECOND, ilu_lower_solve(c, h->ilu, h->ilu_z, h->ilu_t));
+      LAUNCH(fam, vec_dots<double>(c, h->n, h->ilu_t, y, b, P, ldp, np, self, bdot, out, epi, Pb));
+      return MSSTAB_OK;
+    }
+  }
+  LAUNCH(fam, spmv<T>(c, h->A, x, y, b, P, ldp, np, self, bdot, out, epi, Pil, sp, Pb));
+  return MSSTAB_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Cholesky QR (twice) of s columns V, applying the same R^-1 to U
 // ---------------------------------------------------------------------------
@@ -256,7 +284,7 @@ template <typename T>
 msstab_status refresh_v(msstab_t h, Work<T>& w, int prec, SolveOut& out) {
   const Ctx c = h->ctx();
   for (int q = 0; q < h->s; ++q)
-    LAUNCH(MSSTAB_K_SPMV, spmv<T>(c, h->A, w.Urec + (int64_t)q * w.ld, w.Vrec + (int64_t)q * w.ld, nullptr, nullptr,
+    CKS(amv<T>(h, c, MSSTAB_K_SPMV, w.Urec + (int64_t)q * w.ld, w.Vrec + (int64_t)q * w.ld, nullptr, nullptr,
                                   0, 0, 0, 0, nullptr, epi_none(h)));
   out.mvs += h->s;
   if (prec) h->mvs32 += h->s;
@@ -284,7 +312,7 @@ msstab_status arnoldi(msstab_t h, Work<T>& w, int prec, SolveOut& out) {
     LAUNCH(MSSTAB_K_OTHER, scale_rsqrt<T>(c, n, w.R, Ucol(0), &st->scal[0]));
   }
   for (int j = 0; j < s; ++j) {
-    LAUNCH(MSSTAB_K_SPMV, spmv<T>(c, h->A, Ucol(j), Vcol(j), nullptr, nullptr, 0, 0, 0, 0, nullptr, epi_none(h)));
+    CKS(amv<T>(h, c, MSSTAB_K_SPMV, Ucol(j), Vcol(j), nullptr, nullptr, 0, 0, 0, 0, nullptr, epi_none(h)));
     out.mvs += 1;
     if (prec) h->mvs32 += 1;
     if (j == s - 1) break;
@@ -345,7 +373,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
 
   CK(cudaMemsetAsync(&st->flag, 0, sizeof(int), h->stream));
   // r = b - A x, ||r||^2, ||b||^2
-  LAUNCH(MSSTAB_K_SPMV, spmv<T>(c, h->A, w.X, Rk(0), w.B, nullptr, 0, 0, 1, 1, &st->rr, epi_none(h)));
+  CKS(amv<T>(h, c, MSSTAB_K_SPMV, w.X, Rk(0), w.B, nullptr, 0, 0, 1, 1, &st->rr, epi_none(h)));
   out.mvs += 1;
   if (prec) h->mvs32 += 1;
   CK(cudaMemcpyAsync(w.XB, w.X, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream));
@@ -382,7 +410,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
         if (r_is_true) out.relres_true = nr / nb;
         break;
       }
-      LAUNCH(MSSTAB_K_SPMV, spmv<T>(c, h->A, w.X, w.Tm, w.B, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
+      CKS(amv<T>(h, c, MSSTAB_K_SPMV, w.X, w.Tm, w.B, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
       out.mvs += 1;
       if (prec) h->mvs32 += 1;
       CKS(sync_read(h, &st->scal[0], sizeof(double)));
@@ -428,13 +456,13 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     auto launch_cycle = [&](const Ctx& c) -> msstab_status {
       for (int k = 0; k < ell; ++k) {
         LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
-        LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
+        CKS(amv<T>(h, c, MSSTAB_K_SPMV_DOT, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
                                           &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp, w.Pb));
         for (int q = 0; q < s; ++q) {
           LAUNCH(MSSTAB_K_ETA, eta_eager<T>(c, n, s, w.R, w.V, ld, k, q, &st->eta[(k * SMAX + q) * SMAX]));
           Epi next = q + 1 < s ? epi_of(EPI_ETA, k, q + 1)
                                : (k + 1 < ell ? epi_of(EPI_GAMMA, k + 1, 0) : epi_none(h));
-          LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
+          CKS(amv<T>(h, c, MSSTAB_K_SPMV_DOT, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
                                             &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp, w.Pb));
         }
         LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
@@ -453,12 +481,13 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
       // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
       // level step from P^T V (left by tau_update) in the epilogue
       if (replaced)
-        LAUNCH(MSSTAB_K_SPMV_DOT, spmv<T>(c, h->A, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
+        CKS(amv<T>(h, c, MSSTAB_K_SPMV_DOT, w.X, Rk(0), w.B, P, ld, s, 1, 0, &st->projR[0],
                                           epi_of(EPI_GAMMA, 0, 0), w.Pil, w.sp, w.Pb));
       return MSSTAB_OK;
     };
-    if (h->tm.on) {
-      CKS(launch_cycle(c));   // per-launch event timing: plain launches
+    if (h->tm.on || h->precond) {
+      // per-launch event timing, or the cooperative ILU(0) sweeps: plain launches
+      CKS(launch_cycle(c));
     } else {
       // replay the captured launch sequence (captured on first use)
       msstab_s::CycleGraph* g = nullptr;
@@ -501,6 +530,11 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     rr = h->h_small[0];
     int flag = 0;
     std::memcpy(&flag, h->h_small + 1, sizeof(int));
+    if (flag & FLAG_SYNC_TIMEOUT) {
+      CK(cudaMemsetAsync(h->ilu.bar, 0, sizeof(GridBar), h->stream));
+      CK(cudaMemsetAsync(&st->flag, 0, sizeof(int), h->stream));
+      return fail(h, MSSTAB_ERR_CUDA, "a grid barrier of the ILU(0) level sweeps timed out");
+    }
     if (flag & FLAG_BREAKDOWN) {
       out.status = MSSTAB_ERR_BREAKDOWN;
       CK(cudaMemcpyAsync(w.X, w.XB, sizeof(T) * n, cudaMemcpyDeviceToDevice, h->stream));
@@ -542,7 +576,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
   }
   if (out.relres_rec == 0.0) out.relres_rec = std::sqrt(rr) / nb;
   if (ctl.true_check && (out.status != MSSTAB_OK || out.relres_true < 0.0)) {
-    LAUNCH(MSSTAB_K_SPMV, spmv<T>(c, h->A, w.X, w.Tm, w.B, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
+    CKS(amv<T>(h, c, MSSTAB_K_SPMV, w.X, w.Tm, w.B, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
     CKS(sync_read(h, &st->scal[0], sizeof(double)));
     out.relres_true = std::sqrt(h->h_small[0]) / nb;
   }
@@ -745,11 +779,39 @@ msstab_status solve_common(msstab_t h, double tol, msstab_stats* st) {
   CK(cudaEventRecord(h->e0, h->stream));
   msstab_status rc;
   int fp64_finish = 0;
+  const Ctx c = h->ctx();
+  Work<double>& w = h->w64;
+  const size_t bytes = sizeof(double) * h->n;
+  if (h->precond) {
+    // the split-preconditioned system: b~ = L^-1 b, x~0 = U x0
+    CK(cudaMemcpyAsync(h->borig, w.B, bytes, cudaMemcpyDeviceToDevice, h->stream));
+    LAUNCH(MSSTAB_K_PRECOND, ilu_lower_solve(c, h->ilu, w.B, w.B));
+    LAUNCH(MSSTAB_K_PRECOND, ilu_upper_mul(c, h->ilu, w.X, h->ilu_t));
+    CK(cudaMemcpyAsync(w.X, h->ilu_t, bytes, cudaMemcpyDeviceToDevice, h->stream));
+  }
   if (h->opt.precision == MSSTAB_PREC_FP32_INNER)
     rc = solve_dc(h, tol, o, &outer, &fp64_finish);
   else
     rc = solve_fp64(h, tol, o);
   if (rc != MSSTAB_OK) return rc;
+  double relres_orig = o.relres_true;
+  if (h->precond) {
+    // x = U^-1 x~, and the residual of the original system
+    LAUNCH(MSSTAB_K_PRECOND, ilu_upper_solve(c, h->ilu, w.X, w.X));
+    LAUNCH(MSSTAB_K_SPMV, spmv<double>(c, h->A, w.X, w.Tm, h->borig, nullptr, 0, 0, 1, 1, &h->st->scal[0],
+                                       epi_none(h)));
+    CK(cudaMemcpyAsync(h->h_small, &h->st->scal[0], 2 * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaMemcpyAsync(h->h_small + 2, &h->st->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    int flag = 0;
+    std::memcpy(&flag, h->h_small + 2, sizeof(int));
+    if (flag & FLAG_SYNC_TIMEOUT) {
+      CK(cudaMemsetAsync(h->ilu.bar, 0, sizeof(GridBar), h->stream));
+      CK(cudaMemsetAsync(&h->st->flag, 0, sizeof(int), h->stream));
+      return fail(h, MSSTAB_ERR_CUDA, "a grid barrier of the ILU(0) level sweeps timed out");
+    }
+    relres_orig = h->h_small[1] > 0.0 ? std::sqrt(h->h_small[0] / h->h_small[1]) : 0.0;
+  }
   CK(cudaEventRecord(h->e1, h->stream));
   CK(cudaEventSynchronize(h->e1));
   CKS(timing_flush(h));
@@ -765,6 +827,7 @@ msstab_status solve_common(msstab_t h, double tol, msstab_stats* st) {
     st->launches = h->launches - l0;
     st->relres_true = o.relres_true;
     st->relres_rec = o.relres_rec;
+    st->relres_orig = relres_orig;
     st->ms = ms;
     st->status = o.status;
     st->fetched = o.fetched;
@@ -825,6 +888,48 @@ msstab_status msstab_destroy(msstab_t h) {
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
+  return MSSTAB_OK;
+}
+
+static void* ilu_alloc(void* ctx, size_t bytes) {
+  void* p = nullptr;
+  return dalloc((msstab_t)ctx, &p, bytes) == MSSTAB_OK ? p : nullptr;
+}
+
+// The ILU(0) factor of A on the device, with its level schedules.
+static msstab_status ilu_create(msstab_t h, int64_t n, int64_t nnz, const int32_t* d_row_ptr,
+                                const int32_t* d_col, const double* d_val) {
+  IluDesc& F = h->ilu;
+  F.n = (int)n;
+  void* p = nullptr;
+  if (h->A.format == 1) {
+    F.row_ptr = h->A.row_ptr;
+    F.col = h->A.col;
+  } else {
+    CKS(dalloc(h, &p, sizeof(int) * (n + 1)));
+    CK(cudaMemcpyAsync(p, d_row_ptr, sizeof(int) * (n + 1), cudaMemcpyDeviceToDevice, h->stream));
+    F.row_ptr = (const int*)p;
+    CKS(dalloc(h, &p, sizeof(int) * nnz));
+    CK(cudaMemcpyAsync(p, d_col, sizeof(int) * nnz, cudaMemcpyDeviceToDevice, h->stream));
+    F.col = (const int*)p;
+  }
+  CKS(dalloc(h, &p, sizeof(double) * nnz));
+  F.lu = (double*)p;
+  CK(cudaMemcpyAsync(p, d_val, sizeof(double) * nnz, cudaMemcpyDeviceToDevice, h->stream));
+  CKS(dalloc(h, &p, sizeof(GridBar)));
+  F.bar = (GridBar*)p;
+  F.flag = &h->st->flag;
+  CK(cudaMemsetAsync(F.flag, 0, sizeof(int), h->stream));
+  const IluSetupResult r = ilu_setup(h->ctx(), F, ilu_alloc, h, (int*)h->h_small);
+  if (r.code == 4) return MSSTAB_ERR_OOM;   // dalloc wrote the message
+  if (r.code == 1) return cuda_fail(h, r.cuda, r.where ? r.where : "ILU(0) set-up");
+  if (r.code == 2) return fail(h, MSSTAB_ERR_INVALID_ARG, r.where);
+  if (r.code == 3) return fail(h, MSSTAB_ERR_BREAKDOWN, r.where);
+  CK(cudaMemsetAsync(F.flag, 0, sizeof(int), h->stream));
+  for (double** v : {&h->ilu_t, &h->ilu_z, &h->borig}) {
+    CKS(dalloc(h, &p, sizeof(double) * n));
+    *v = (double*)p;
+  }
   return MSSTAB_OK;
 }
 
@@ -948,6 +1053,8 @@ static msstab_status create_impl(msstab_t h, int64_t n, int64_t nnz, const int32
     CK(cudaStreamSynchronize(h->stream));
   }
 
+  if (h->precond) CKS(ilu_create(h, n, nnz, d_row_ptr, d_col, d_val));
+
   // workspaces: FP64 levels for the FP64 mode; FP32 levels for the inner mode
   const bool inner = h->opt.precision == MSSTAB_PREC_FP32_INNER;
   CKS(alloc_work<double>(h, h->w64, true));   // FP64 levels also serve the FP32-inner form's FP64 finish
@@ -1024,6 +1131,15 @@ msstab_status msstab_create(int64_t n, int64_t nnz, const int32_t* d_row_ptr, co
     delete h;
     return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "sell_sigma must be 1 or a multiple of 32");
   }
+  if (h->opt.precond != MSSTAB_PRECOND_NONE && h->opt.precond != MSSTAB_PRECOND_ILU0) {
+    delete h;
+    return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "precond must be MSSTAB_PRECOND_NONE or MSSTAB_PRECOND_ILU0");
+  }
+  if (h->opt.precond == MSSTAB_PRECOND_ILU0 && h->opt.precision != MSSTAB_PREC_FP64) {
+    delete h;
+    return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "the ILU(0) preconditioner needs precision MSSTAB_PREC_FP64");
+  }
+  h->precond = h->opt.precond == MSSTAB_PRECOND_ILU0;
   h->stream = (cudaStream_t)h->opt.stream;
   msstab_status rc = create_impl(h, n, nnz, d_row_ptr, d_col, d_val, d_p_raw);
   if (rc != MSSTAB_OK) {
@@ -1376,6 +1492,65 @@ msstab_status msstab_op_small_solve(msstab_t h, int32_t n, const double* d_M, co
   LAUNCH(MSSTAB_K_OTHER, small_lu(c, n, d_M, d_rhs, d_z, d_flag));
   CK(cudaStreamSynchronize(h->stream));
   return MSSTAB_OK;
+}
+
+static msstab_status check_ilu(msstab_t h) {
+  CKS(check_handle(h));
+  if (!h->precond) return fail(h, MSSTAB_ERR_INVALID_ARG, "the handle has no ILU(0) preconditioner");
+  return MSSTAB_OK;
+}
+
+// wait for the sweeps and turn a timed-out grid barrier into an error
+static msstab_status ilu_sync(msstab_t h) {
+  CK(cudaMemcpyAsync(h->h_small, &h->st->flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  int flag = 0;
+  std::memcpy(&flag, h->h_small, sizeof(int));
+  if (flag & FLAG_SYNC_TIMEOUT) {
+    CK(cudaMemsetAsync(h->ilu.bar, 0, sizeof(GridBar), h->stream));
+    CK(cudaMemsetAsync(&h->st->flag, 0, sizeof(int), h->stream));
+    CK(cudaStreamSynchronize(h->stream));
+    return fail(h, MSSTAB_ERR_CUDA, "a grid barrier of the ILU(0) level sweeps timed out");
+  }
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_op_ilu_factor(msstab_t h, double* d_lu) {
+  CKS(check_ilu(h));
+  CKS(check_ptr(h, d_lu, "lu"));
+  CK(cudaMemcpyAsync(d_lu, h->ilu.lu, sizeof(double) * h->nnz, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_op_ilu_levels(msstab_t h, int32_t* d_lev_lower, int32_t* d_lev_upper, int32_t* h_info) {
+  CKS(check_ilu(h));
+  const IluDesc& F = h->ilu;
+  if (d_lev_lower)
+    CK(cudaMemcpyAsync(d_lev_lower, F.lev[0], sizeof(int) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  if (d_lev_upper)
+    CK(cudaMemcpyAsync(d_lev_upper, F.lev[1], sizeof(int) * h->n, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  if (h_info) {
+    const int32_t info[6] = {F.nlev[0], F.nlev[1], F.max_width[0], F.max_width[1], F.grid[0], F.grid[1]};
+    std::memcpy(h_info, info, sizeof(info));
+  }
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_op_ilu_apply(msstab_t h, int32_t which, const double* d_in, double* d_out) {
+  CKS(check_ilu(h));
+  CKS(check_ptr(h, d_in, "in"));
+  CKS(check_ptr(h, d_out, "out"));
+  if (which < 0 || which > 3) return fail(h, MSSTAB_ERR_INVALID_ARG, "which must be 0, 1, 2 or 3");
+  if (which == 2 && d_in == d_out) return fail(h, MSSTAB_ERR_INVALID_ARG, "U x needs distinct in and out");
+  const Ctx c = h->ctx();
+  if (which == 0) LAUNCH(MSSTAB_K_PRECOND, ilu_lower_solve(c, h->ilu, d_in, d_out));
+  if (which == 1) LAUNCH(MSSTAB_K_PRECOND, ilu_upper_solve(c, h->ilu, d_in, d_out));
+  if (which == 2) LAUNCH(MSSTAB_K_PRECOND, ilu_upper_mul(c, h->ilu, d_in, d_out));
+  if (which == 3)
+    CKS(amv<double>(h, c, MSSTAB_K_SPMV, d_in, d_out, nullptr, nullptr, 0, 0, 0, 0, nullptr, epi_none(h)));
+  return ilu_sync(h);
 }
 
 msstab_status msstab_op_tau_solve(msstab_t h, int32_t ell, const double* d_gram, double* d_tau) {

@@ -341,6 +341,52 @@ template cudaError_t spmv<double>(const Ctx&, const MatDesc&, const double*, dou
 template cudaError_t spmv<float>(const Ctx&, const MatDesc&, const float*, float*, const float*, const float*,
                                  int64_t, int, int, int, double*, Epi, const float*, int, const float*);
 
+// y = z or b - z, row by row, with the fused reductions of the product.
+template <typename T, int NP>
+__global__ void __launch_bounds__(SNT, 1) vec_dots_kernel(int n, const T* z, SpmvArgs<T> a) {
+  constexpr int NA = NP < 0 ? 0 : NP;
+  DotAcc<T, NA> acc;
+  acc.zero();
+  const int stride = gridDim.x * SNT;
+  for (int row = blockIdx.x * SNT + threadIdx.x; row < n; row += stride) {
+    const T zv = z[row];
+    const T yv = a.b ? (T)(a.b[row] - zv) : zv;
+    a.y[row] = yv;
+    if constexpr (NP >= 0) acc_row<T, NA>(a, row, yv, acc);
+  }
+  if constexpr (NP >= 0) finish<T, NA>(a, acc);
+}
+
+template <typename T, int NP>
+static void launch_vec_dots(const Ctx& c, int n, const T* z, const SpmvArgs<T>& a) {
+  static int cap = max_grid(vec_dots_kernel<T, NP>, c);
+  const int64_t need = ((int64_t)n + SNT - 1) / SNT;
+  vec_dots_kernel<T, NP><<<(int)(need < cap ? need : cap), SNT, 0, c.stream>>>(n, z, a);
+}
+
+template <typename T>
+cudaError_t vec_dots(const Ctx& c, int n, const T* z, T* y, const T* b, const T* P, int64_t ldp, int np,
+                     int self, int bdot, double* out, Epi epi, const T* Pb) {
+  if (np < 0 || np > SMAX) return cudaErrorInvalidValue;
+  SpmvArgs<T> a{z, y, b, P, ldp, np, self, bdot, out, epi, c.rs, nullptr, 0, Pb};
+  if (np + self + bdot == 0)
+    launch_vec_dots<T, -1>(c, n, z, a);
+  else if (np == 0)
+    launch_vec_dots<T, 0>(c, n, z, a);
+  else if (np <= 4)
+    launch_vec_dots<T, 4>(c, n, z, a);
+  else if (np <= 8)
+    launch_vec_dots<T, 8>(c, n, z, a);
+  else
+    launch_vec_dots<T, 16>(c, n, z, a);
+  return cudaGetLastError();
+}
+
+template cudaError_t vec_dots<double>(const Ctx&, int, const double*, double*, const double*, const double*,
+                                      int64_t, int, int, int, double*, Epi, const double*);
+template cudaError_t vec_dots<float>(const Ctx&, int, const float*, float*, const float*, const float*, int64_t,
+                                     int, int, int, double*, Epi, const float*);
+
 // Pil[row * sp + c] = P[c * ldp + row] for c < s, zero for s <= c < sp.
 template <typename T>
 __global__ void interleave_kernel(int n, int s, const T* P, int64_t ldp, int sp, T* Pil) {

@@ -22,7 +22,8 @@ STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "oom", 4: "breakdown", 
 PREC_FP64, PREC_FP32_INNER = 0, 1
 FETCH_ONCE, FETCH_EVERY, FETCH_NEVER = 0, 1, 2
 FORMAT_SELL, FORMAT_CSR = 0, 1
-KERNEL_FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn"]
+PRECOND_NONE, PRECOND_ILU0 = 0, 1
+KERNEL_FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond"]
 
 
 class Options(ctypes.Structure):
@@ -40,7 +41,8 @@ class Options(ctypes.Structure):
         ("max_outer", ctypes.c_int32),
         ("inner_ell", ctypes.c_int32),
         ("replace_every", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("precond", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
     ]
 
@@ -61,8 +63,9 @@ class Stats(ctypes.Structure):
         ("guess_used", ctypes.c_int32),
         ("fp64_finish", ctypes.c_int32),
         ("reserved_s", ctypes.c_int32),
-        ("t_ms", ctypes.c_double * 8),
-        ("n_launch", ctypes.c_int64 * 8),
+        ("relres_orig", ctypes.c_double),
+        ("t_ms", ctypes.c_double * 9),
+        ("n_launch", ctypes.c_int64 * 9),
     ]
 
     def as_dict(self):
@@ -108,6 +111,9 @@ _SIGS = {
     "msstab_op_tau_update": (_I32, [_P, _I32, _P, _P, _P, _I64, _P]),
     "msstab_op_small_solve": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "msstab_op_tau_solve": (_I32, [_P, _I32, _P, _P]),
+    "msstab_op_ilu_factor": (_I32, [_P, _P]),
+    "msstab_op_ilu_levels": (_I32, [_P, _P, _P, _P]),
+    "msstab_op_ilu_apply": (_I32, [_P, _I32, _P, _P]),
     "msstab_spmv_dot_noalloc": (_I32, [_I64, _I64, _P, _P, _P, _P, _P, _P, _I64, _I32, _P, _P]),
     "msstab_cnn_num_params": (_I32, []),
     "msstab_cnn_create": (_I32, [_I32, _I32, _I32, _P, _I32, _I32, _I32, _P, ctypes.POINTER(_P)]),
@@ -185,7 +191,8 @@ class Solver:
     tuple ``(n, row_ptr, col, val)`` of CUDA tensors.  ``p_raw`` is the raw
     random basis of P, shape (s, n).  Keyword arguments set msstab_options
     fields (precision, fetch_policy, fetch_threshold, fetch_cycle, orth_recycle,
-    max_mvs, inner_tol, spmv_format, sell_sigma, kernel_timing, max_outer).
+    max_mvs, inner_tol, spmv_format, sell_sigma, kernel_timing, max_outer,
+    inner_ell, replace_every, precond).
     """
 
     def __init__(self, A, s: int, ell: int, p_raw, device: str = "cuda", stream=None, **options):
@@ -336,6 +343,21 @@ class Solver:
 
     def op_tau_solve(self, gram, tau):
         _check(load().msstab_op_tau_solve(self._h, tau.numel(), _ptr(gram), _ptr(tau)), self._h)
+
+    # ILU(0) split preconditioner (handles created with precond=PRECOND_ILU0)
+    def op_ilu_factor(self, lu):
+        _check(load().msstab_op_ilu_factor(self._h, _ptr(lu)), self._h)
+
+    def op_ilu_levels(self, lev_lower=None, lev_upper=None):
+        """Per-row levels (into the optional int32 tensors) and
+        (levels lower, levels upper, widest lower, widest upper, blocks lower, blocks upper)."""
+        info = (ctypes.c_int32 * 6)()
+        _check(load().msstab_op_ilu_levels(self._h, _ptr(lev_lower), _ptr(lev_upper), info), self._h)
+        return tuple(info)
+
+    def op_ilu_apply(self, which: int, x, y):
+        """which 0: y = L^-1 x; 1: y = U^-1 x; 2: y = U x; 3: y = L^-1 A U^-1 x."""
+        _check(load().msstab_op_ilu_apply(self._h, which, _ptr(x), _ptr(y)), self._h)
 
 
 class CNN:

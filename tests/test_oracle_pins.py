@@ -292,7 +292,7 @@ def test_mv_counts_table1(s, ell):
 
 
 def test_residual_replacement_every_cycle():
-    """r := b - A x at each cycle end (the preconditioned experiment of Section 6
+    """r := b - A x at each cycle end (the preconditioned experiment of Section 5.1
     replaces the residual this way): the iteration is unchanged in exact
     arithmetic, the recursive residual equals the true one at every cycle end,
     each cycle pays one product more and no confirmation product is needed."""
