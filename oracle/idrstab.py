@@ -311,9 +311,39 @@ class SolveResult:
     fetch_cycle: int = 0
 
 
+def slope_fires(history: List[float], k: int) -> bool:
+    """The online drop test at the end of cycle k (history[i]: relative
+    residual at the start, i = 0, and after cycle i): the residual fell in
+    cycle k by at least one decade and by at least twice the mean decrease (in
+    log10) of cycles 1..k-1.  A reading of "shortly before the residual drops"
+    (section on choosing the fetching point) as a test a solver can apply as it
+    runs; needs k >= 2."""
+    if k < 2:
+        return False
+    lg = [math.log10(max(h, 1e-300)) for h in history[:k + 1]]
+    drop = lg[k - 1] - lg[k]
+    mean = (lg[0] - lg[k - 1]) / (k - 1)
+    return drop >= 1.0 and drop >= 2.0 * mean
+
+
+def fetch_estimate(history: List[float]) -> Optional[int]:
+    """The fetching point estimated from a complete residual history (the
+    probe solve of the section on choosing the fetching point): the cycle end
+    just before the steepest one-cycle decrease of log10 relres, at least 1;
+    None if the solve ran no cycle."""
+    K = len(history) - 1
+    if K < 1:
+        return None
+    lg = [math.log10(max(h, 1e-300)) for h in history]
+    drops = [lg[k - 1] - lg[k] for k in range(1, K + 1)]
+    k_star = 1 + max(range(K), key=lambda i: (drops[i], -i))   # first of the steepest
+    return max(1, k_star - 1)
+
+
 def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
-            fetch_threshold=None, fetch_cycle=None, fetch_refresh=False,
-            replace_every=0, inspect: Optional[Callable] = None, mv: Optional[MatVec] = None) -> SolveResult:
+            fetch_threshold=None, fetch_cycle=None, fetch_refresh=False, fetch_slope=False,
+            fetch_at_end=False, replace_every=0, inspect: Optional[Callable] = None,
+            mv: Optional[MatVec] = None) -> SolveResult:
     """IDR(s)stab(l), Algorithm 1, with inputs A, b, x, s, l, P, U, V.
 
     Precondition V = A U, dim P = s (P orthonormal, (s, N) layout).  With
@@ -327,6 +357,9 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
     ``fetch_refresh`` the written V is recomputed as A U (s counted MVs): the
     recursions keep V = A U only up to a drift (about 1e-6 relative here), and
     Algorithm 1 requires V = A U of its inputs.
+    ``fetch_slope`` fetches instead the basis of the cycle before the first
+    cycle at whose end ``slope_fires``; ``fetch_at_end`` fetches the final
+    basis of a converged solve that fetched nothing before.
     ``replace_every`` > 0 replaces the recursive residual by b - A x (one
     counted MV) at the end of every replace_every-th cycle, as the
     preconditioned experiment of Section 5.1 does after each cycle; the stopping
@@ -353,6 +386,7 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
     mv_history = [mv.count - m0]
     fetched = None
     fetch_at = 0
+    prev_basis = None
     status = OK
     if U is not None:
         U = np.array(U, dtype=np.float64, copy=True)
@@ -414,12 +448,21 @@ def idrstab(A, b, x, s, ell, P, U=None, V=None, tol=1e-8, *, max_mvs=None,
         if inspect is not None:
             inspect("cycle", dict(r=r, x=x, U=U, V=V, R=R, tau=tau, P=P, b=b, mv=mv))
         if fetched is None:
-            if (fetch_cycle is not None and cycles == fetch_cycle) or \
-               (fetch_cycle is None and fetch_threshold is not None and relres <= fetch_threshold):
+            if fetch_slope:
+                if prev_basis is not None and slope_fires(history, cycles):
+                    Up, Vp = prev_basis
+                    fetched = (Up, np.stack([mv(u) for u in Up]) if fetch_refresh else Vp)
+                    fetch_at = cycles - 1
+                prev_basis = (U.copy(), V.copy())
+            elif (fetch_cycle is not None and cycles == fetch_cycle) or \
+                    (fetch_cycle is None and fetch_threshold is not None and relres <= fetch_threshold):
                 Vf = np.stack([mv(u) for u in U]) if fetch_refresh else V.copy()
                 fetched = (U.copy(), Vf)
                 fetch_at = cycles
 
+    if fetch_at_end and fetched is None and status == OK and cycles > 0:
+        fetched = (U.copy(), np.stack([mv(u) for u in U]) if fetch_refresh else V.copy())
+        fetch_at = cycles
     relres_rec = float(np.linalg.norm(r)) / nb
     relres_true = float(np.linalg.norm(b - mv.uncounted(x))) / nb
     return SolveResult(x, r, U, V, j, cycles, mv.count - m0, status, relres_rec, relres_true,
@@ -458,6 +501,14 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
                     (the IDRstab baseline).
     policy "every": the final U, V of each solve are passed to the next
                     (Miltenberger's chaining, Section 3.1).
+    policy "slope": as "once", with the fetching point of the first solve found
+                    as it runs: the basis of the cycle before the residual
+                    drops (``slope_fires``), else the final basis.
+    policy "probe": the first system is a probe solved by IDRstab without a
+                    fetch; its history gives the fetching point
+                    (``fetch_estimate``), at which the second system, again
+                    solved by IDRstab, writes U, V (the final basis if it
+                    converges earlier); the later systems recycle them.
     With ``orth_recycle`` (default) the passed basis is conditioned: V := A U
     (s MVs, counted in the solve that wrote it), then Cholesky QR twice.
     ``first_step``/``steps`` select the slice of the sequence that is solved;
@@ -468,16 +519,28 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
     x = np.array(x0, dtype=np.float64, copy=True)
     rec = None
     solves = []
+    probe_cycle = None
     for _ in range(first_step, first_step + steps):
         b = x / tau_t + f
         if policy == "never" or rec is None:
             U = V = None
         else:
             U, V = rec
-        want_fetch = policy == "once" and rec is None
-        res = idrstab(mv.A, b, x, s, ell, P, U, V, tol, max_mvs=max_mvs,
-                      fetch_threshold=thr if want_fetch else None, fetch_refresh=orth_recycle,
-                      replace_every=replace_every, mv=mv)
+        kw = {}
+        want_fetch = rec is None and policy in ("once", "slope", "probe")
+        if policy == "once" and want_fetch:
+            kw = dict(fetch_threshold=thr)
+        elif policy == "slope" and want_fetch:
+            kw = dict(fetch_slope=True, fetch_at_end=True)
+        elif policy == "probe" and want_fetch:
+            if probe_cycle is None:
+                want_fetch = False            # the probe itself writes nothing
+            else:
+                kw = dict(fetch_cycle=probe_cycle, fetch_at_end=True)
+        res = idrstab(mv.A, b, x, s, ell, P, U, V, tol, max_mvs=max_mvs, fetch_refresh=orth_recycle,
+                      replace_every=replace_every, mv=mv, **kw)
+        if policy == "probe" and rec is None and probe_cycle is None and res.status == OK:
+            probe_cycle = fetch_estimate(res.history)
         if want_fetch and res.fetched is not None:
             rec = _orth_or_none(res.fetched) if orth_recycle else res.fetched
         elif policy == "every" and res.U is not None and res.cycles > 0 and res.status == OK:
