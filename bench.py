@@ -627,6 +627,8 @@ def main(argv=None):
                                  ("msstab_fp32_inner", FP32_INNER_OPTS(M), None),
                                  ("msstab_fp64_block_p", {}, p_block),
                                  ("msstab_fp32_inner_block_p", FP32_INNER_OPTS(M), p_block),
+                                 ("msstab_fp64_fetch_slope", dict(fetch_policy=M.FETCH_SLOPE), None),
+                                 ("msstab_fp64_fetch_probe", dict(fetch_policy=M.FETCH_PROBE), None),
                                  ("msstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1), None),
                                  ("idrstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1,
                                                             fetch_policy=M.FETCH_NEVER), None)):
@@ -636,7 +638,7 @@ def main(argv=None):
                          replace_every=w.replace_every, **opts)
             create_ms = (time.perf_counter() - c0) * 1e3
             xv = torch.tensor(x0_np, device=dev)
-            run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W, check=False)
+            wv = run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, W, check=False)
             torch.cuda.synchronize()
             v0 = torch.cuda.Event(enable_timing=True)
             v1 = torch.cuda.Event(enable_timing=True)
@@ -660,6 +662,11 @@ def main(argv=None):
                 variants[name]["cut_space"] = "block-partitioned N(0,1), seed 3 (rows (i // 32) mod s)"
             if "ilu0" in name:
                 variants[name].update(ilu_report(V, A, tv, create_ms))
+            if "fetch_" in name:
+                variants[name]["fetched_in_warmup"] = [{"system": i + 1, "cycle": t["fetch_at"], "mvs": t["mvs"]}
+                                                       for i, t in enumerate(wv) if t["fetched"]]
+                variants[name]["note"] = ("fetching point from the running drop test (slope) or from a probe "
+                                          "solve's history (probe); the warm-up systems include the fetch")
             V.close()
           except Exception as e:  # a failing variant is reported, the main line still stands
             variants[name] = {"error": str(e)[-300:]}

@@ -45,7 +45,8 @@ typedef enum msstab_status {
 } msstab_status;
 
 enum { MSSTAB_PREC_FP64 = 0, MSSTAB_PREC_FP32_INNER = 1 };
-enum { MSSTAB_FETCH_ONCE = 0, MSSTAB_FETCH_EVERY = 1, MSSTAB_FETCH_NEVER = 2 };
+enum { MSSTAB_FETCH_ONCE = 0, MSSTAB_FETCH_EVERY = 1, MSSTAB_FETCH_NEVER = 2, MSSTAB_FETCH_SLOPE = 3,
+       MSSTAB_FETCH_PROBE = 4 };
 enum { MSSTAB_FORMAT_SELL = 0, MSSTAB_FORMAT_CSR = 1 };
 enum { MSSTAB_PRECOND_NONE = 0, MSSTAB_PRECOND_ILU0 = 1 };
 
@@ -69,7 +70,16 @@ typedef struct msstab_options {
   int32_t fetch_policy;    /* MSSTAB_FETCH_ONCE (default): fetch U,V in the first solve and reuse
                               them for all later solves; EVERY: pass each solve's final U,V on
                               (Miltenberger, Section 3.1); NEVER: IDRstab with an Arnoldi start
-                              for every system */
+                              for every system.  The fetching point, after the section on
+                              choosing it ("shortly before the residual drops"): ONCE at the
+                              fetch_threshold / fetch_cycle below; SLOPE in the first solve at
+                              the basis of the cycle before the first cycle that lowers log10
+                              relres by >= 1 and by >= twice the mean of the cycles before it
+                              (the final basis if none does); PROBE: the first solve is an
+                              IDRstab probe that writes nothing, and the second, again IDRstab,
+                              fetches at the cycle end before the probe's steepest one-cycle
+                              drop (its final basis if it converges earlier).  SLOPE and PROBE:
+                              FP64 only */
   double fetch_threshold;  /* fetch at the first cycle end with relres <= this; <= 0: sqrt(tol) */
   int32_t fetch_cycle;     /* > 0: fetch at the end of this cycle instead of by threshold */
   int32_t orth_recycle;    /* 1 (default): condition the fetched basis -- V := A U (s products
@@ -125,7 +135,7 @@ typedef struct msstab_stats {
   int32_t guess_used;     /* set by msstab_select_guess */
   int32_t fp64_finish;    /* FP32_INNER: 1 if the FP32 corrections stalled and FP64 IDR(s)stab(l)
                              finished the solve from the current x */
-  int32_t reserved_s;
+  int32_t fetch_at;       /* the cycle whose basis this call wrote to the recycle store (fetched) */
   double relres_orig;     /* ||b - A x|| / ||b|| of the original system (differs from relres_true
                              only with the ILU(0) preconditioner, whose relres_true is that of
                              L^-1 A U^-1 x~ = L^-1 b) */

@@ -55,6 +55,7 @@ struct Timing {
 
 struct SolveOut {
   int64_t mvs = 0, cycles = 0;
+  int64_t fetch_at = 0;     // cycle whose basis was written to the recycle store
   double relres_true = -1.0, relres_rec = 0.0;
   int fetched = 0, used_recycle = 0;
   msstab_status status = MSSTAB_OK;
@@ -97,6 +98,9 @@ struct msstab_s {
   std::vector<CycleGraph> graphs;
   cudaStream_t cap_stream = nullptr;   // private stream the cycle is captured on (replayed on `stream`)
   // ILU(0) split preconditioning: the solver's operator is L^-1 A U^-1
+  int64_t probe_cycle = 0;  // FETCH_PROBE: fetching point estimated by the probe solve (0: none yet)
+  double* Uprev = nullptr;   // FETCH_SLOPE: the basis at the previous cycle end
+  double* Vprev = nullptr;
   bool precond = false;
   IluDesc ilu{};
   double* ilu_t = nullptr;   // U^-1 x of the running product, then L^-1 A U^-1 x
@@ -356,7 +360,40 @@ struct SolveCtl {
   bool stop_on_stagnation;  // stop when the residual has not halved in 4 cycles
   bool continue_basis;    // start from the U, V left in the level slots by the previous solve
   int replace_every;      // > 0: r := b - A x after every replace_every-th cycle
+  bool fetch_slope;       // fetch the basis of the cycle before the residual drops (slope_fires)
+  bool fetch_at_end;      // a converged solve that fetched nothing writes its final basis
 };
+
+// The running drop test of the slope policy at the end of cycle k (hist[0]:
+// relres at the start, hist[i]: after cycle i): a decrease of log10 relres in
+// cycle k of at least one decade and at least twice the mean decrease of
+// cycles 1..k-1 ("shortly before the residual drops", read as a test a solver
+// can apply while it runs).
+bool slope_fires(const std::vector<double>& hist, int64_t k) {
+  if (k < 2 || (int64_t)hist.size() <= k) return false;
+  auto lg = [&](int64_t i) { return std::log10(std::max(hist[i], 1e-300)); };
+  const double drop = lg(k - 1) - lg(k);
+  const double mean = (lg(0) - lg(k - 1)) / (double)(k - 1);
+  return drop >= 1.0 && drop >= 2.0 * mean;
+}
+
+// The fetching point estimated from a probe solve's complete history: the
+// cycle end before the steepest one-cycle decrease (the first of equals), at
+// least 1; 0 if the solve ran no cycle.
+int64_t fetch_estimate(const std::vector<double>& hist) {
+  const int64_t K = (int64_t)hist.size() - 1;
+  if (K < 1) return 0;
+  int64_t best = 1;
+  double best_drop = -1e300;
+  for (int64_t k = 1; k <= K; ++k) {
+    const double d = std::log10(std::max(hist[k - 1], 1e-300)) - std::log10(std::max(hist[k], 1e-300));
+    if (d > best_drop) {
+      best_drop = d;
+      best = k;
+    }
+  }
+  return std::max<int64_t>(1, best - 1);
+}
 
 template <typename T>
 msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, SolveOut& out) {
@@ -396,6 +433,25 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     h->hist.push_back(std::sqrt(rr) / nb);
     h->hist_mvs.push_back(out.mvs);
   }
+  std::vector<double> hrel{std::sqrt(rr) / nb};   // relres at the start and at every cycle end
+  bool have_prev = false;
+  // write U, V (V := A U and Cholesky QR when orth_recycle) to the recycle store
+  auto do_fetch = [&](const T* srcU, const T* srcV, int64_t at) -> msstab_status {
+    CK(cudaMemcpyAsync(w.Urec, srcU, sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+    bool ok = true;
+    if (h->opt.orth_recycle) {
+      CKS(refresh_v<T>(h, w, prec, out));
+      CKS(cholqr2<T>(h, w.Vrec, w.Urec, ld, &ok));
+    } else {
+      CK(cudaMemcpyAsync(w.Vrec, srcV, sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    if (ok) {
+      w.has_rec = true;
+      out.fetched = 1;
+      out.fetch_at = at;
+    }
+    return MSSTAB_OK;
+  };
   bool r_is_true = true, have_basis = ctl.continue_basis, need_proj = true;
   const int64_t cyc_mvs = (int64_t)ell * (s + 1);
   for (;;) {
@@ -546,6 +602,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
       h->hist_mvs.push_back(out.mvs);
     }
     if (!std::isfinite(relres)) continue;  // handled (restore) at the top
+    hrel.push_back(relres);
     std::swap(w.XB, w.XB2);
     r_is_true = replaced;
     out.relres_rec = relres;
@@ -557,23 +614,24 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
         break;  // the FP32 floor is reached: the outer FP64 loop takes over
       }
     }
-    if (ctl.want_fetch && !out.fetched &&
-        ((ctl.fetch_cycle > 0 && out.cycles == ctl.fetch_cycle) ||
-         (ctl.fetch_cycle <= 0 && relres <= ctl.fetch_threshold))) {
-      CK(cudaMemcpyAsync(w.Urec, Vq(-1, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
-      bool ok = true;
-      if (h->opt.orth_recycle) {
-        CKS(refresh_v<T>(h, w, prec, out));
-        CKS(cholqr2<T>(h, w.Vrec, w.Urec, ld, &ok));
-      } else {
-        CK(cudaMemcpyAsync(w.Vrec, Vq(0, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+    if (ctl.want_fetch && !out.fetched && ctl.fetch_slope) {
+      if constexpr (std::is_same<T, double>::value) {
+        if (have_prev && slope_fires(hrel, out.cycles)) {
+          CKS(do_fetch(h->Uprev, h->Vprev, out.cycles - 1));
+        } else {
+          CK(cudaMemcpyAsync(h->Uprev, Vq(-1, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+          CK(cudaMemcpyAsync(h->Vprev, Vq(0, 0), sizeof(T) * ld * s, cudaMemcpyDeviceToDevice, h->stream));
+          have_prev = true;
+        }
       }
-      if (ok) {
-        w.has_rec = true;
-        out.fetched = 1;
-      }
+    } else if (ctl.want_fetch && !out.fetched &&
+               ((ctl.fetch_cycle > 0 && out.cycles == ctl.fetch_cycle) ||
+                (ctl.fetch_cycle <= 0 && relres <= ctl.fetch_threshold))) {
+      CKS(do_fetch(Vq(-1, 0), Vq(0, 0), out.cycles));
     }
   }
+  if (ctl.want_fetch && ctl.fetch_at_end && !out.fetched && out.status == MSSTAB_OK && out.cycles > 0)
+    CKS(do_fetch(Vq(-1, 0), Vq(0, 0), out.cycles));
   if (out.relres_rec == 0.0) out.relres_rec = std::sqrt(rr) / nb;
   if (ctl.true_check && (out.status != MSSTAB_OK || out.relres_true < 0.0)) {
     CKS(amv<T>(h, c, MSSTAB_K_SPMV, w.X, w.Tm, w.B, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
@@ -613,9 +671,16 @@ SolveCtl make_ctl(msstab_t h, double tol, bool first_has_rec) {
   ctl.max_mvs = default_max_mvs(h);
   const int pol = h->opt.fetch_policy;
   ctl.use_recycle = pol != MSSTAB_FETCH_NEVER;
-  ctl.want_fetch = pol == MSSTAB_FETCH_ONCE && !first_has_rec;
+  ctl.want_fetch = (pol == MSSTAB_FETCH_ONCE || pol == MSSTAB_FETCH_SLOPE) && !first_has_rec;
+  ctl.fetch_slope = pol == MSSTAB_FETCH_SLOPE;
+  ctl.fetch_at_end = pol == MSSTAB_FETCH_SLOPE;
+  if (pol == MSSTAB_FETCH_PROBE && !first_has_rec && h->probe_cycle > 0) {
+    // the solve after the probe fetches at the estimated cycle
+    ctl.want_fetch = true;
+    ctl.fetch_at_end = true;
+  }
   ctl.fetch_threshold = h->opt.fetch_threshold > 0 ? h->opt.fetch_threshold : std::sqrt(tol);
-  ctl.fetch_cycle = h->opt.fetch_cycle;
+  ctl.fetch_cycle = pol == MSSTAB_FETCH_PROBE ? (int)h->probe_cycle : h->opt.fetch_cycle;
   ctl.record_history = true;
   ctl.true_check = true;
   ctl.ell = h->ell;
@@ -628,7 +693,9 @@ SolveCtl make_ctl(msstab_t h, double tol, bool first_has_rec) {
 // FP64 solve on w64 (b and x0 already staged in w64.B / w64.X).
 msstab_status solve_fp64(msstab_t h, double tol, SolveOut& o) {
   SolveCtl ctl = make_ctl(h, tol, h->w64.has_rec);
+  const bool probe = h->opt.fetch_policy == MSSTAB_FETCH_PROBE && !h->w64.has_rec && h->probe_cycle <= 0;
   CKS(idrstab<double>(h, h->w64, 0, ctl, o));
+  if (probe && o.status == MSSTAB_OK) h->probe_cycle = fetch_estimate(h->hist);
   CKS(chain_recycle<double>(h, h->w64, 0, o));
   return MSSTAB_OK;
 }
@@ -831,6 +898,7 @@ msstab_status solve_common(msstab_t h, double tol, msstab_stats* st) {
     st->ms = ms;
     st->status = o.status;
     st->fetched = o.fetched;
+    st->fetch_at = (int32_t)o.fetch_at;
     st->used_recycle = o.used_recycle;
     for (int f = 0; f < MSSTAB_K_COUNT; ++f) {
       st->t_ms[f] = h->tm.t_ms[f];
@@ -1054,6 +1122,13 @@ static msstab_status create_impl(msstab_t h, int64_t n, int64_t nnz, const int32
   }
 
   if (h->precond) CKS(ilu_create(h, n, nnz, d_row_ptr, d_col, d_val));
+  if (h->opt.fetch_policy == MSSTAB_FETCH_SLOPE) {
+    const int64_t ldp = round_up(n, 32);
+    CKS(dalloc(h, &p, sizeof(double) * (size_t)ldp * h->s));
+    h->Uprev = (double*)p;
+    CKS(dalloc(h, &p, sizeof(double) * (size_t)ldp * h->s));
+    h->Vprev = (double*)p;
+  }
 
   // workspaces: FP64 levels for the FP64 mode; FP32 levels for the inner mode
   const bool inner = h->opt.precision == MSSTAB_PREC_FP32_INNER;
@@ -1140,6 +1215,15 @@ msstab_status msstab_create(int64_t n, int64_t nnz, const int32_t* d_row_ptr, co
     return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "the ILU(0) preconditioner needs precision MSSTAB_PREC_FP64");
   }
   h->precond = h->opt.precond == MSSTAB_PRECOND_ILU0;
+  if (h->opt.fetch_policy < MSSTAB_FETCH_ONCE || h->opt.fetch_policy > MSSTAB_FETCH_PROBE) {
+    delete h;
+    return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "unknown fetch_policy");
+  }
+  if ((h->opt.fetch_policy == MSSTAB_FETCH_SLOPE || h->opt.fetch_policy == MSSTAB_FETCH_PROBE) &&
+      h->opt.precision != MSSTAB_PREC_FP64) {
+    delete h;
+    return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "the slope and probe fetch policies need precision FP64");
+  }
   h->stream = (cudaStream_t)h->opt.stream;
   msstab_status rc = create_impl(h, n, nnz, d_row_ptr, d_col, d_val, d_p_raw);
   if (rc != MSSTAB_OK) {
@@ -1197,6 +1281,7 @@ msstab_status msstab_reset_recycle(msstab_t h) {
   CKS(check_handle(h));
   h->w64.has_rec = false;
   h->w32.has_rec = false;
+  h->probe_cycle = 0;
   return MSSTAB_OK;
 }
 

@@ -20,7 +20,7 @@ from . import build as _build
 OK, ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_BREAKDOWN, ERR_MAXIT, ERR_NAN = range(7)
 STATUS_NAMES = {0: "ok", 1: "invalid_arg", 2: "cuda", 3: "oom", 4: "breakdown", 5: "maxit", 6: "nan"}
 PREC_FP64, PREC_FP32_INNER = 0, 1
-FETCH_ONCE, FETCH_EVERY, FETCH_NEVER = 0, 1, 2
+FETCH_ONCE, FETCH_EVERY, FETCH_NEVER, FETCH_SLOPE, FETCH_PROBE = 0, 1, 2, 3, 4
 FORMAT_SELL, FORMAT_CSR = 0, 1
 PRECOND_NONE, PRECOND_ILU0 = 0, 1
 KERNEL_FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond"]
@@ -62,7 +62,7 @@ class Stats(ctypes.Structure):
         ("used_recycle", ctypes.c_int32),
         ("guess_used", ctypes.c_int32),
         ("fp64_finish", ctypes.c_int32),
-        ("reserved_s", ctypes.c_int32),
+        ("fetch_at", ctypes.c_int32),
         ("relres_orig", ctypes.c_double),
         ("t_ms", ctypes.c_double * 9),
         ("n_launch", ctypes.c_int64 * 9),

@@ -50,22 +50,23 @@ def _gpu_sequence_p(M, w, A, steps, p_raw, **opt):
         S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
         st = S.solve(b, x, w.tol)
         out.append((st.mvs, st.cycles, st.relres_true, st.fetched, st.used_recycle, x.cpu().numpy().copy(),
-                    S.history()[0]))
+                    S.history()[0], st.fetch_at))
     S.close()
     return out
 
 
-@pytest.mark.parametrize("policy", ["once", "never", "every"])
+@pytest.mark.parametrize("policy", ["once", "never", "every", "slope", "probe"])
 def test_sequence_2d_matches_oracle(M, policy):
     w = pb.WORKLOADS["convdiff2d_32"]
     A = w.matrix()
-    pol = {"once": M.FETCH_ONCE, "never": M.FETCH_NEVER, "every": M.FETCH_EVERY}[policy]
+    pol = {"once": M.FETCH_ONCE, "never": M.FETCH_NEVER, "every": M.FETCH_EVERY, "slope": M.FETCH_SLOPE,
+           "probe": M.FETCH_PROBE}[policy]
     g = _gpu_sequence(M, w, A, w.steps, fetch_policy=pol)
     o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol, policy=policy)
     As = A.to_scipy()
     xprev = w.x0()
     for i, (gs, os_) in enumerate(zip(g, o.solves)):
-        mvs, cycles, relres, fetched, used, x, _ = gs
+        mvs, cycles, relres, fetched, used, x = gs[:6]
         assert _mvs_match(gs, os_, w.tol), (i, mvs, os_.mvs, gs[6], os_.history)
         assert relres <= w.tol
         b = xprev / w.tau + w.f()
@@ -76,6 +77,11 @@ def test_sequence_2d_matches_oracle(M, policy):
         assert g[0][3] == 1 and all(s[4] == 1 for s in g[1:])
     if policy == "never":
         assert not any(s[4] for s in g)
+    if policy in ("slope", "probe"):
+        # the same fetching point as the oracle's rule on its own history
+        i = 0 if policy == "slope" else 1
+        assert g[i][3] == 1 and g[i][7] == o.solves[i].fetch_cycle
+        assert all(s[4] == 1 for s in g[i + 1:])
 
 
 @pytest.mark.parametrize("fmt,re", [(0, 0), (1, 0), (0, 1)])
@@ -87,7 +93,7 @@ def test_sequence_3d_matches_oracle(M, fmt, re):
     As = A.to_scipy()
     xprev = w.x0()
     for i, (gs, os_) in enumerate(zip(g, o.solves)):
-        mvs, cycles, relres, fetched, used, x, _ = gs
+        mvs, cycles, relres, fetched, used, x = gs[:6]
         b = xprev / w.tau + w.f()
         assert np.linalg.norm(b - As @ x) <= w.tol * np.linalg.norm(b) * 1.0001
         assert _mvs_match(gs, os_, w.tol), (i, mvs, os_.mvs, gs[6], os_.history)
@@ -206,6 +212,31 @@ def test_gpu_data_ab_drop_after_m11(M, ell_src, fetch_cycle, ell):
     rel, st = _m_after_fetch(M, 4, ell_src, fetch_cycle, ell)
     c12 = 4 // ell
     assert rel[c12] < 1e-8 and rel[c12 - 1] > 1e-6
+
+
+@pytest.mark.parametrize("s,ell,cycle", [(2, 1, 19), (4, 1, 9), (4, 2, 4)])
+def test_gpu_fetch_policies_find_the_papers_fetching_points(M, s, ell, cycle):
+    # the running drop test and the probe estimate land on the fetching points
+    # of the Section 5.2 experiments (IDR(2)stab(1): 60 MVs; IDR(4)stab(1):
+    # G_9; IDR(4)stab(2): 4 cycles), and the slope policy's data terminates
+    # M(s)stab on the second right-hand side as the paper's does
+    P = pb.randn_cols(40, s, pb.SEED_P)
+    S = M.Solver(TRI, s, ell, P, device=DEV, fetch_policy=M.FETCH_SLOPE, orth_recycle=0, max_mvs=2000)
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(B1), x, 1e-12, check=False)
+    assert st.fetched == 1 and st.fetch_at == cycle
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st2 = S.solve(_t(B2), x, 1e-12)
+    assert st2.used_recycle == 1 and st2.status == 0 and st2.cycles < st.cycles
+    S.close()
+    S = M.Solver(TRI, s, ell, P, device=DEV, fetch_policy=M.FETCH_PROBE, orth_recycle=0, max_mvs=2000)
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(B1), x, 1e-12, check=False)
+    assert st.fetched == 0 and st.used_recycle == 0
+    x = torch.zeros(40, dtype=torch.float64, device=DEV)
+    st = S.solve(_t(B1), x, 1e-12, check=False)
+    assert st.fetched == 1 and st.fetch_at == cycle and st.used_recycle == 0
+    S.close()
 
 
 # ---------------------------------------------------------------------------
@@ -385,7 +416,7 @@ def test_fp32_inner_reaches_fp64_accuracy(M):
     o = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol)
     xprev = w.x0()
     for i, (gs, os_) in enumerate(zip(g, o.solves)):
-        mvs, cycles, relres, fetched, used, x, _ = gs
+        mvs, cycles, relres, fetched, used, x = gs[:6]
         b = xprev / w.tau + w.f()
         assert np.linalg.norm(b - As @ x) <= w.tol * np.linalg.norm(b) * 1.0001
         # both residuals are below tol; the solutions differ by at most cond * tol
@@ -441,7 +472,7 @@ def test_block_partitioned_cut_space_matches_oracle(M):
     As = A.to_scipy()
     xprev = w.x0()
     for i, (gs, os_) in enumerate(zip(g, o.solves)):
-        mvs, cycles, relres, fetched, used, xg, hist = gs
+        mvs, cycles, relres, fetched, used, xg, hist = gs[:7]
         b = xprev / w.tau + w.f()
         assert np.linalg.norm(b - As @ xg) <= w.tol * np.linalg.norm(b) * 1.0001
         assert _mvs_match(gs, os_, w.tol), (i, mvs, os_.mvs, hist, os_.history)
