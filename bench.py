@@ -41,7 +41,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one launch of the dominant kernel of each form,
 # from one ncu capture of the current kernel at 128^3
 # (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md, ..._fp32inner_...).
-NCU_TRAFFIC = {("fp64", "spmv_dot"): 342_601_472, ("fp32_inner", "spmv_dot"): 200_179_712}
+NCU_TRAFFIC = {("fp64", "spmv_dot"): 342_601_472, ("fp32_inner", "spmv_dot"): 200_179_712,
+               ("ilu0", "precond"): 133_184_512}
 
 
 def parse_args(argv=None):
@@ -51,7 +52,7 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--form", choices=["fp64", "fp32_inner", "idrstab"], default="fp64",
+    p.add_argument("--form", choices=["fp64", "fp32_inner", "idrstab", "ilu0"], default="fp64",
                    help="the solver form of the main line: FP64 M(s)stab (default), the FP32-inner "
                         "defect-correction form, or FP64 IDR(s)stab with an Arnoldi start per system")
     p.add_argument("--no-variants", action="store_true", help="skip the IDRstab and FP32-inner runs")
@@ -214,7 +215,9 @@ def workload_config(w, n, nnz, W, K, form, world):
                         f"beta={tuple(w.beta)}, implicit Euler tau={w.tau}, systems {W + 1}..{W + K} of the sequence",
             "method": {"fp64": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
                        "fp32_inner": f"FP32-inner M({w.s})stab(1) with FP64 defect correction, SELL-32",
-                       "idrstab": f"IDR({w.s})stab({w.ell}), Arnoldi start per system, FP64, SELL-32"}[form],
+                       "idrstab": f"IDR({w.s})stab({w.ell}), Arnoldi start per system, FP64, SELL-32",
+                       "ilu0": f"M({w.s})stab({w.ell}) on L^-1 A U^-1 (ILU(0) split preconditioner), fetch once "
+                               f"at sqrt(tol), FP64, SELL-32"}[form],
             "true_residual": "replaced every cycle" if w.replace_every == 1 else "checked at convergence",
             "tol": w.tol, "l2": "inputs larger than L2 (matrix 0.18 GB + ~90 vectors of 16.8 MB), no flush",
             "parallelism": "replicas" if world > 1 else "single GPU"}
@@ -442,9 +445,9 @@ def ilu_report(V, A, tv, create_ms):
             "sweep_alg_bytes": int(sweep_bytes),
             "sweep_GBps": round(sweep_bytes / (us * 1e-6) / 1e9, 1) if us > 0 else None,
             "relres_orig_max": max(t["relres_orig"] for t in tv),
-            "note": "level-scheduled: one cooperative launch per triangular solve, a grid barrier between "
-                    "levels; bound by the levels' latency (about 3n - 2 planes for a 7-point stencil), "
-                    "not by HBM"}
+            "note": "pipelined over row chunks (one per SM, levels in order inside a chunk, block barriers "
+                    "between them, waits only on other chunks' values); bound by one store-to-load trip per "
+                    "level (3n - 2 levels for a 7-point stencil), not by HBM"}
 
 
 
@@ -489,7 +492,8 @@ def main(argv=None):
     f_np, x0_np = w.f(), w.x0()
     K, W = args.steps, args.warmup
 
-    form_opts = {"fp64": {}, "fp32_inner": FP32_INNER_OPTS(M), "idrstab": dict(fetch_policy=M.FETCH_NEVER)}[args.form]
+    form_opts = {"fp64": {}, "fp32_inner": FP32_INNER_OPTS(M), "idrstab": dict(fetch_policy=M.FETCH_NEVER),
+                 "ilu0": dict(precond=M.PRECOND_ILU0)}[args.form]
     # the timed run replays each cycle as a CUDA graph; per-launch event
     # timing (which launches one by one) runs in a second pass over the same
     # systems for the per-kernel roofline
@@ -548,6 +552,12 @@ def main(argv=None):
         model, spmv_b = family_model(A, w.s, 1, cycles, K, 0, vb=4)
     else:
         model, spmv_b = family_model(A, w.s, w.ell, cycles, K, replaced)
+    if args.form == "ilu0":
+        # one triangular sweep: the rows' dependencies (value + column), row
+        # pointer, diagonal position and position index, right-hand side and
+        # solution once (the U x products of each solve are counted with them)
+        model["precond"] = dict(launches=fam_n.get("precond", 0), bytes=12 * (A.nnz - A.n) / 2 + 28 * A.n,
+                                flops=float(A.nnz - A.n))
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -688,7 +698,8 @@ def main(argv=None):
             variants["learned_guess"] = {"error": str(e)[-300:]}
         line["variants"] = variants
 
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    # the oracle sample below is Algorithm 1 without a preconditioner
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and args.form != "ilu0":
         try:
             res = run_cpu_sample(args, 4)
             cyc = cycles / K

@@ -305,7 +305,8 @@ msstab_status msstab_op_tau_solve(msstab_t h, int32_t ell, const double* d_gram,
  * dependencies below it; rows of one level are computed in parallel) to
  * d_lev_lower[n], d_lev_upper[n] (either may be NULL) and writes
  * h_info[0..5] = levels (lower, upper), widest level (lower, upper), blocks of
- * the sweeps (lower, upper).
+ * the solves (lower, upper: one per row chunk of the pipelined sweep, else the
+ * blocks of the level-by-level sweep).
  * msstab_op_ilu_apply: which = 0: d_out = L^-1 d_in; 1: d_out = U^-1 d_in;
  * 2: d_out = U d_in; 3: d_out = L^-1 A U^-1 d_in.  d_out may equal d_in for 0,
  * 1 and 3, not for 2.  All three block until done.  INVALID_ARG without the

@@ -173,6 +173,20 @@ struct IluDesc {
   double* pval[2] = {nullptr, nullptr};
   double* pdiag[2] = {nullptr, nullptr};
   int* pptr[2] = {nullptr, nullptr};   // padded positions of level l: [pptr[l], pptr[l+1])
+  // chunked order of the pipelined solves (CH[u] > 0): rows cut into chunks of
+  // CH rows, one per block; chunk b's local levels are the groups
+  // [gofs[b], gofs[b+1]), group q holds positions [gptr[q], gptr[q+1]);
+  // dependencies inside the chunk are stored as ~(j - first row of the chunk)
+  int CH[2] = {0, 0};
+  int groups[2] = {0, 0};
+  int* gofs[2] = {nullptr, nullptr};
+  int* gptr[2] = {nullptr, nullptr};
+  int* cprow[2] = {nullptr, nullptr};
+  int* cpcnt[2] = {nullptr, nullptr};
+  int* cpcol[2] = {nullptr, nullptr};
+  double* cpval[2] = {nullptr, nullptr};
+  double* cpdiag = nullptr;
+  double* scratch = nullptr;      // copy of the right-hand side of an in-place chunked solve
   GridBar* bar = nullptr;         // grid-barrier state (zero between launches)
   int* flag = nullptr;            // device flag word (FLAG_SYNC_TIMEOUT, FLAG_ZERO_PIVOT)
 };

@@ -1617,7 +1617,8 @@ msstab_status msstab_op_ilu_levels(msstab_t h, int32_t* d_lev_lower, int32_t* d_
     CK(cudaMemcpyAsync(d_lev_upper, F.lev[1], sizeof(int) * h->n, cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   if (h_info) {
-    const int32_t info[6] = {F.nlev[0], F.nlev[1], F.max_width[0], F.max_width[1], F.grid[0], F.grid[1]};
+    auto blocks = [&](int u) { return F.CH[u] > 0 ? (F.n + F.CH[u] - 1) / F.CH[u] : F.grid[u]; };
+    const int32_t info[6] = {F.nlev[0], F.nlev[1], F.max_width[0], F.max_width[1], blocks(0), blocks(1)};
     std::memcpy(h_info, info, sizeof(info));
   }
   return MSSTAB_OK;
