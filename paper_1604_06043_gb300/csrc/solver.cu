@@ -78,7 +78,6 @@ struct msstab_s {
   DevState* st = nullptr;
   RedScratch rs{};
   double* h_small = nullptr;   // pinned readback buffer
-  double* h_stage = nullptr;   // pinned staging for msstab_solve_host
   std::string err;
   std::vector<double> hist;
   std::vector<int64_t> hist_mvs;
@@ -952,7 +951,6 @@ msstab_status msstab_destroy(msstab_t h) {
   if (h->e0) cudaEventDestroy(h->e0);
   if (h->e1) cudaEventDestroy(h->e1);
   if (h->h_small) cudaFreeHost(h->h_small);
-  if (h->h_stage) cudaFreeHost(h->h_stage);
   for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   delete h;
