@@ -133,9 +133,201 @@ __global__ void __launch_bounds__(TV) conv_kernel(const __nv_bfloat16* __restric
   }
 }
 
+// ---------------------------------------------------------------------------
+// The 16 -> 16 channel convolutions on the tensor cores (tcgen05), as an
+// implicit GEMM: an output tile of 128 voxels (8 x-consecutive by 16
+// y-consecutive in one z plane) is the M dimension, the 16 output channels N,
+// and each of the 27 taps one K = 16 step over the input channels:
+// D[m][co] = sum_tap sum_ci A_tap[m][ci] W_tap[ci][co].  Both operands sit in
+// shared memory K-major without swizzle (core matrices of 8 rows x 16 bytes):
+// the input halo (10 x 18 x 3 voxels) as two halves of 8 channels,
+// [half][voxel][8], so that A_tap is the halo shifted by the tap -- 16 bytes
+// between x-consecutive voxels, 160 bytes (one halo row) between the 8-row
+// groups, 8640 bytes (one half) between the two K halves; the weights as
+// [tap][half][co][8] -- 128 bytes between co groups, 256 between halves.
+// One thread issues the 27 MMAs (kind::f16, BF16 operands, FP32 accumulator
+// of 128 lanes x 16 columns in tensor memory; 32 columns allocated) and
+// commits them to an mbarrier; after a bounded wait each warp reads its 32
+// rows with tcgen05.ld for the epilogue (bias, GELU or GELU', bf16 rounding).
+// Blocks are persistent (weights, tensor memory and the mbarrier set up once,
+// tiles taken in a grid-stride loop).  A wait that runs out raises *flag and
+// ends the block's loop; tensor memory is always freed before the block exits.
+// ---------------------------------------------------------------------------
+constexpr int CTX = 8, CTY = 16;
+constexpr int CHX = CTX + 2, CHY = CTY + 2, CHZ = 3, CHV = CHX * CHY * CHZ;   // 540 halo voxels
+constexpr int TC_A_HALF = CHV * 16;                 // bytes of one channel half of the halo
+constexpr int TC_A_BYTES = 17 * 1024;               // 2 halves (17280 bytes), rounded up
+constexpr int TC_B_BYTES = 27 * 512;                // weights of the 27 taps
+constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES;
+constexpr long long TC_WAIT_LIMIT = 1LL << 22;
+static_assert(2 * TC_A_HALF <= TC_A_BYTES, "halo does not fit");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// shared-memory matrix descriptor: start, leading (K) and stride (M/N) byte
+// offsets, descriptor version 1, no swizzle
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __restrict__ in, Dims d, int B,
+                                                      const __nv_bfloat16* __restrict__ w,
+                                                      const float* __restrict__ bias, float* __restrict__ z,
+                                                      __nv_bfloat16* __restrict__ act,
+                                                      const float* __restrict__ zaux, int* flag) {
+  extern __shared__ __align__(1024) unsigned char tsm[];
+  unsigned char* As = tsm;
+  unsigned char* Bs = tsm + TC_A_BYTES;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tilesx = (d.X + CTX - 1) / CTX, tilesy = (d.Y + CTY - 1) / CTY;
+  const int tiles = tilesx * tilesy * d.Z;
+  const int64_t vol = d.vol();
+  // weights once per block: w[co][ci][tap] -> tap * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2
+  for (int i = tid; i < 16 * 16 * 27; i += 128) {
+    const int co = i / (16 * 27), r = i % (16 * 27), ci = r / 27, tap = r % 27;
+    *reinterpret_cast<__nv_bfloat16*>(Bs + tap * 512 + (ci >> 3) * 256 + co * 16 + (ci & 7) * 2) = w[i];
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(32));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  // D f32, A and B bf16, both K-major, N = 16, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int job = blockIdx.x; job < tiles * B && ok; job += gridDim.x, phase ^= 1u) {
+    const int b = job / tiles, tile = job % tiles;
+    const int tz0 = tile / (tilesx * tilesy);
+    const int ty0 = ((tile / tilesx) % tilesy) * CTY;
+    const int tx0 = (tile % tilesx) * CTX;
+    const __nv_bfloat16* inb = in + (int64_t)b * 16 * vol;
+    // halo: the 8 channels of one half of voxel v as one 16-byte store at half * A_HALF + v * 16
+    for (int i = tid; i < 2 * CHV; i += 128) {
+      const int half = i / CHV, v = i % CHV;
+      const int hx = v % CHX, hy = (v / CHX) % CHY, hz = v / (CHX * CHY);
+      const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+      uint4 q = make_uint4(0u, 0u, 0u, 0u);
+      if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z) {
+        const __nv_bfloat16* src = inb + (int64_t)(half * 8) * vol + ((int64_t)gz * d.Y + gy) * d.X + gx;
+        unsigned short e[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) e[c] = __bfloat16_as_ushort(src[(int64_t)c * vol]);
+        q.x = e[0] | ((uint32_t)e[1] << 16);
+        q.y = e[2] | ((uint32_t)e[3] << 16);
+        q.z = e[4] | ((uint32_t)e[5] << 16);
+        q.w = e[6] | ((uint32_t)e[7] << 16);
+      }
+      *reinterpret_cast<uint4*>(As + half * TC_A_HALF + v * 16) = q;
+    }
+    // the tile's smem writes reach the tensor cores; the previous tile's
+    // tensor-memory reads are done before the MMAs overwrite the accumulator
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+      for (int tap = 0; tap < 27; ++tap) {
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const uint64_t ad = umma_desc(a0 + ((dz * CHY + dy) * CHX + dx) * 16, TC_A_HALF, CHX * 16);
+        const uint64_t bd = umma_desc(b0 + tap * 512, 256, 128);
+        const uint32_t accum = tap > 0;
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                     ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mbar)));
+    }
+    uint32_t done = 0;
+    for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+      asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                   "selp.u32 %0, 1, 0, p;\n\t}\n"
+                   : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase));
+    // one decision for the whole block (tcgen05.ld below is warp-collective)
+    const int all_done = __syncthreads_and((int)done);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!all_done) {
+      if (tid == 0) atomicOr(flag, 1);
+      ok = false;
+      break;
+    }
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    const int m = warp * 32 + lane;
+    const int gx = tx0 + (m & 7), gy = ty0 + (m >> 3), gz = tz0;
+    if (gx < d.X && gy < d.Y) {
+      const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
+      const int64_t ob = (int64_t)b * 16 * vol;
+#pragma unroll
+      for (int co = 0; co < 16; ++co) {
+        const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
+        const int64_t o = ob + (int64_t)co * vol + p;
+        if (MODE == FWD_HIDDEN) {
+          z[o] = acc;
+          act[o] = __float2bfloat16_rn(gelu(acc));
+        } else if (MODE == INFER_HIDDEN) {
+          act[o] = __float2bfloat16_rn(gelu(acc));
+        } else {
+          act[o] = __float2bfloat16_rn(acc * gelu_grad(zaux[o]));
+        }
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(32));
+}
+
+template <int MODE>
+static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
+                           const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  static int cap = 0;
+  if (!cap) {
+    int dev = 0, sms = 0, nb = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_tc_kernel<MODE>, 128, TC_SMEM);
+    cap = (nb > 0 ? nb : 1) * (sms > 0 ? sms : 1);
+  }
+  const int64_t jobs = (int64_t)((d.X + CTX - 1) / CTX) * ((d.Y + CTY - 1) / CTY) * d.Z * B;
+  const int grid = (int)(jobs < cap ? jobs : cap);   // persistent blocks, tiles in a grid-stride loop
+  conv_tc_kernel<MODE><<<grid, 128, TC_SMEM, st>>>(in, d, B, w, bias, z, act, zaux, flag);
+  return cudaGetLastError();
+}
+
+// 16 -> 16 channels (not the last layer) on the tensor cores, the others
+// (2 -> 16, 16 -> 1, 1 -> 16) on the CUDA cores: N = 1 or K = 2 per tap do not
+// fill an MMA.
 template <int CI, int CO, int MODE>
 static cudaError_t conv(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
-                        const float* bias, float* z, __nv_bfloat16* act, const float* zaux) {
+                        const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
+  if constexpr (CI == 16 && CO == 16 && MODE != FWD_LAST) return conv_tc<MODE>(st, in, d, B, w, bias, z, act, zaux, flag);
   const size_t smem = sizeof(float) * (CI * HV + CO * CI * 27);
   static bool attr = false;
   if (!attr) {
@@ -459,6 +651,7 @@ struct msstab_cnn_s {
   __nv_bfloat16* dz[NL] = {};   // gradient of the pre-activation of layer l (bf16)
   float* tgt = nullptr;
   float* kst = nullptr;         // operator stencil of the loss (27 floats), or unused
+  int* tcflag = nullptr;        // raised by a tensor-core convolution whose wait ran out
   bool use_stencil = false;
   float* sbuf = nullptr;        // K * (out - t) of the batch
   float* partials = nullptr;
@@ -532,10 +725,10 @@ msstab_status quantize(msstab_cnn_t h) {
 msstab_status forward_batch(msstab_cnn_t h, int B, int D) {
   const Dims d{D, D, D};
   cudaStream_t st = h->stream;
-  CCK((conv<2, 16, FWD_HIDDEN>(st, h->act[0], d, B, h->wq[0], h->bq[0], h->z[0], h->act[1], nullptr)));
-  CCK((conv<16, 16, FWD_HIDDEN>(st, h->act[1], d, B, h->wq[1], h->bq[1], h->z[1], h->act[2], nullptr)));
-  CCK((conv<16, 16, FWD_HIDDEN>(st, h->act[2], d, B, h->wq[2], h->bq[2], h->z[2], h->act[3], nullptr)));
-  CCK((conv<16, 1, FWD_LAST>(st, h->act[3], d, B, h->wq[3], h->bq[3], h->z[3], nullptr, nullptr)));
+  CCK((conv<2, 16, FWD_HIDDEN>(st, h->act[0], d, B, h->wq[0], h->bq[0], h->z[0], h->act[1], nullptr, h->tcflag)));
+  CCK((conv<16, 16, FWD_HIDDEN>(st, h->act[1], d, B, h->wq[1], h->bq[1], h->z[1], h->act[2], nullptr, h->tcflag)));
+  CCK((conv<16, 16, FWD_HIDDEN>(st, h->act[2], d, B, h->wq[2], h->bq[2], h->z[2], h->act[3], nullptr, h->tcflag)));
+  CCK((conv<16, 1, FWD_LAST>(st, h->act[3], d, B, h->wq[3], h->bq[3], h->z[3], nullptr, nullptr, h->tcflag)));
   return MSSTAB_OK;
 }
 
@@ -557,12 +750,12 @@ msstab_status backward_batch(msstab_cnn_t h, int B, int D, double* loss) {
   // layer 3 (16 -> 1)
   CCK((wgrad<16, 1>(st, h->act[3], h->dz[3], d, B, h->partials, &nb)));
   reduce_partials_kernel<<<grid1(16 * 27 + 1), 256, 0, st>>>(h->partials, nb, 16 * 27 + 1, h->grad + w_offset(3));
-  CCK((conv<1, 16, BWD_DATA>(st, h->dz[3], d, B, h->wt[3], nullptr, nullptr, h->dz[2], h->z[2])));
+  CCK((conv<1, 16, BWD_DATA>(st, h->dz[3], d, B, h->wt[3], nullptr, nullptr, h->dz[2], h->z[2], h->tcflag)));
   for (int l = 2; l >= 1; --l) {
     CCK((wgrad<16, 16>(st, h->act[l], h->dz[l], d, B, h->partials, &nb)));
     reduce_partials_kernel<<<grid1(16 * 16 * 27 + 16), 256, 0, st>>>(h->partials, nb, 16 * 16 * 27 + 16,
                                                                      h->grad + w_offset(l));
-    CCK((conv<16, 16, BWD_DATA>(st, h->dz[l], d, B, h->wt[l], nullptr, nullptr, h->dz[l - 1], h->z[l - 1])));
+    CCK((conv<16, 16, BWD_DATA>(st, h->dz[l], d, B, h->wt[l], nullptr, nullptr, h->dz[l - 1], h->z[l - 1], h->tcflag)));
   }
   CCK((wgrad<2, 16>(st, h->act[0], h->dz[0], d, B, h->partials, &nb)));
   reduce_partials_kernel<<<grid1(2 * 16 * 27 + 16), 256, 0, st>>>(h->partials, nb, 2 * 16 * 27 + 16,
@@ -590,6 +783,14 @@ msstab_status sumsq(msstab_cnn_t h, const T* x, int64_t n, double* out) {
   double s = 0.0;
   for (int i = 0; i < g; ++i) s += part[i];
   *out = s;
+  return MSSTAB_OK;
+}
+
+// after a synchronisation: a tensor-core convolution whose wait ran out
+msstab_status tc_check(msstab_cnn_t h) {
+  int f = 0;
+  CCK(cudaMemcpy(&f, h->tcflag, sizeof(int), cudaMemcpyDeviceToHost));
+  if (f) return cfail(h, MSSTAB_ERR_CUDA, "a tensor-core convolution timed out waiting for its MMAs");
   return MSSTAB_OK;
 }
 
@@ -653,6 +854,7 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
   CKC(calloc_(h, &h->tgt, bv));
   CKC(calloc_(h, &h->sbuf, bv));
   CKC(calloc_(h, &h->kst, 27));
+  CKC(calloc_(h, &h->tcflag, 1));
   const int64_t tiles = ((crop + TX - 1) / TX) * (int64_t)((crop + TY - 1) / TY) * ((crop + TZ - 1) / TZ) * max_batch;
   CKC(calloc_(h, &h->partials, (size_t)tiles * (16 * 16 * 27 + 16)));
   CKC(calloc_(h, &h->dpart, 4096));
@@ -672,7 +874,8 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
     h->err = "cudaMallocHost failed";
     return fail_create(MSSTAB_ERR_OOM);
   }
-  if (cudaMemcpyAsync(h->theta, d_params, sizeof(float) * np, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
+  if (cudaMemsetAsync(h->tcflag, 0, sizeof(int), h->stream) != cudaSuccess ||
+      cudaMemcpyAsync(h->theta, d_params, sizeof(float) * np, cudaMemcpyDeviceToDevice, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->m, 0, sizeof(float) * np, h->stream) != cudaSuccess ||
       cudaMemsetAsync(h->v, 0, sizeof(float) * np, h->stream) != cudaSuccess) {
     h->err = "copying the initial parameters failed";
@@ -744,7 +947,7 @@ msstab_status msstab_cnn_forward(msstab_cnn_t h, const float* d_in, int32_t B, i
   CKA(forward_batch(h, B, D));
   CCK(cudaMemcpyAsync(d_out, h->z[3], sizeof(float) * B * D * D * D, cudaMemcpyDeviceToDevice, h->stream));
   CCK(cudaStreamSynchronize(h->stream));
-  return MSSTAB_OK;
+  return tc_check(h);
 }
 
 msstab_status msstab_cnn_grad(msstab_cnn_t h, const float* d_in, const float* d_target, int32_t B, int32_t D,
@@ -759,7 +962,7 @@ msstab_status msstab_cnn_grad(msstab_cnn_t h, const float* d_in, const float* d_
   CKA(backward_batch(h, B, D, loss));
   CCK(cudaMemcpyAsync(d_grad, h->grad, sizeof(float) * n_params(), cudaMemcpyDeviceToDevice, h->stream));
   CCK(cudaStreamSynchronize(h->stream));
-  return MSSTAB_OK;
+  return tc_check(h);
 }
 
 msstab_status msstab_cnn_adam_step(msstab_cnn_t h, const float* d_grad, float lr) {
@@ -834,7 +1037,7 @@ msstab_status msstab_cnn_train(msstab_cnn_t h, int32_t iters, int32_t B, int32_t
     CKA(msstab_cnn_adam_step(h, h->grad, lr));
   }
   CCK(cudaStreamSynchronize(h->stream));
-  return MSSTAB_OK;
+  return tc_check(h);
 }
 
 msstab_status msstab_cnn_infer(msstab_cnn_t h, const double* d_r0, const double* d_x_prev, double* d_delta) {
@@ -846,10 +1049,10 @@ msstab_status msstab_cnn_infer(msstab_cnn_t h, const double* d_r0, const double*
   const float sr = rms > 0.0 && std::isfinite(rms) ? (float)(1.0 / rms) : 1.f;
   infer_in_kernel<<<grid1(h->N), 256, 0, st>>>(d_r0, d_x_prev, h->N, sr, h->scale[0], h->iin);
   CCK(cudaGetLastError());
-  CCK((conv<2, 16, INFER_HIDDEN>(st, h->iin, h->full, 1, h->wq[0], h->bq[0], nullptr, h->ia, nullptr)));
-  CCK((conv<16, 16, INFER_HIDDEN>(st, h->ia, h->full, 1, h->wq[1], h->bq[1], nullptr, h->ib, nullptr)));
-  CCK((conv<16, 16, INFER_HIDDEN>(st, h->ib, h->full, 1, h->wq[2], h->bq[2], nullptr, h->ia, nullptr)));
-  CCK((conv<16, 1, FWD_LAST>(st, h->ia, h->full, 1, h->wq[3], h->bq[3], h->iout, nullptr, nullptr)));
+  CCK((conv<2, 16, INFER_HIDDEN>(st, h->iin, h->full, 1, h->wq[0], h->bq[0], nullptr, h->ia, nullptr, h->tcflag)));
+  CCK((conv<16, 16, INFER_HIDDEN>(st, h->ia, h->full, 1, h->wq[1], h->bq[1], nullptr, h->ib, nullptr, h->tcflag)));
+  CCK((conv<16, 16, INFER_HIDDEN>(st, h->ib, h->full, 1, h->wq[2], h->bq[2], nullptr, h->ia, nullptr, h->tcflag)));
+  CCK((conv<16, 1, FWD_LAST>(st, h->ia, h->full, 1, h->wq[3], h->bq[3], h->iout, nullptr, nullptr, h->tcflag)));
   infer_out_kernel<<<grid1(h->N), 256, 0, st>>>(h->iout, h->N, 1.0 / ((double)h->scale[1] * (double)sr), d_delta);
   CCK(cudaGetLastError());
   return MSSTAB_OK;
