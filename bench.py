@@ -58,6 +58,8 @@ def parse_args(argv=None):
     p.add_argument("--no-variants", action="store_true", help="skip the IDRstab and FP32-inner runs")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--cnn", action="store_true",
+                   help="time only the learned-guess network: inference on the full grid and training iterations")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-level-steps", type=int, default=4, help=argparse.SUPPRESS)
     p.add_argument("--cpu-k0", type=int, default=0, help=argparse.SUPPRESS)
@@ -451,6 +453,57 @@ def ilu_report(V, A, tv, create_ms):
 
 
 
+def cnn_bench(args):
+    """The learned-guess network alone on the 128^3 grid: inference (2 -> 16
+    -> 16 -> 16 -> 1, 3x3x3; the two 16 -> 16 layers on the tensor cores) and
+    training iterations (8 crops of 32^3, forward + backward + Adam), synthetic
+    residual and solution fields, CUDA events around K calls after W."""
+    import numpy as np
+    import torch
+    from paper_1604_06043_gb300 import build, msstab as M, problems as pb
+    build.build()
+    w = pb.WORKLOADS[args.workload]
+    n = w.n
+    dev = "cuda:0"
+    W, K = max(3, args.warmup), args.steps
+    net = M.CNN(w.shape, pb.cnn_init_params(), max_pairs=2, max_batch=8, crop=32, device=dev)
+    g = torch.Generator(device=dev).manual_seed(pb.SEED_CNN)
+    r0 = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    xp = torch.randn(n, dtype=torch.float64, device=dev, generator=g)
+    out = torch.empty_like(r0)
+    net.add_pair(r0, xp, xp + 1e-2 * r0)
+    net.add_pair(xp, r0, r0 + 1e-2 * xp)
+    net.fit_scales()
+    for _ in range(W):
+        net.infer(r0, xp, out)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(K):
+        net.infer(r0, xp, out)
+    e1.record()
+    torch.cuda.synchronize()
+    inf_ms = e0.elapsed_time(e1) / K
+    batches = pb.cnn_crop_batches(2, w.shape, 32, 8, W + K)
+    net.train(batches[:8 * W], 8, 32, 1e-3)
+    torch.cuda.synchronize()
+    e0.record()
+    net.train(batches[8 * W:], 8, 32, 1e-3)
+    e1.record()
+    torch.cuda.synchronize()
+    tr_ms = e0.elapsed_time(e1) / K
+    taps = 27
+    fl = [2 * n * ci * co * taps for ci, co in ((2, 16), (16, 16), (16, 16), (16, 1))]
+    line = {"metric": "learned-guess CNN inference on the full grid", "value": round(inf_ms, 4), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": K, "warmup": W, "dtype": "bf16 (fp32 accumulation)",
+            "data": "synthetic", "config": {"workload": w.name, "grid": list(w.shape),
+                                            "layers": "2->16->16->16->1, 3x3x3, GELU"},
+            "inference_tflops": round(sum(fl) / (inf_ms * 1e-3) / 1e12, 2),
+            "tensor_core_layer_gflop": [round(fl[1] / 1e9, 2), round(fl[2] / 1e9, 2)],
+            "train_iter_ms": round(tr_ms, 4), "train_batch": "8 crops of 32^3"}
+    print(json.dumps(line), flush=True)
+
+
 def run_sequence(M, torch, S, f, x, b, tau, tol, count, collect=None, check=True):
     out = []
     for _ in range(count):
@@ -469,6 +522,9 @@ def main(argv=None):
         return
     if args.impl == "reference":
         reference_arm(args)
+        return
+    if args.cnn:
+        cnn_bench(args)
         return
 
     import numpy as np

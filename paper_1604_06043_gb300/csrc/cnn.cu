@@ -18,6 +18,7 @@
 
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -57,87 +58,11 @@ struct Dims {
 };
 
 // ---------------------------------------------------------------------------
-// 3x3x3 convolution of a CI-channel bf16 volume to CO channels, FP32 sums.
-// w: [CO][CI][27] bf16, bias: CO floats (bf16 values) or NULL.
-// MODE FWD_HIDDEN: z (FP32) and act = bf16(gelu(z)); FWD_LAST: z only;
-// INFER_HIDDEN: act only; BWD_DATA: act = bf16(sum * gelu'(zaux)) (the
-// gradient of the previous layer's pre-activation; w holds that layer's
-// weights transposed and flipped).
-// ---------------------------------------------------------------------------
-template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(TV) conv_kernel(const __nv_bfloat16* __restrict__ in, Dims d,
-                                                  const __nv_bfloat16* __restrict__ w,
-                                                  const float* __restrict__ bias, float* __restrict__ z,
-                                                  __nv_bfloat16* __restrict__ act,
-                                                  const float* __restrict__ zaux) {
-  extern __shared__ float smem[];
-  float* in_s = smem;                 // [CI][HV]
-  float* w_s = smem + CI * HV;        // [CI][27][CO]
-  const int tilesx = (d.X + TX - 1) / TX, tilesy = (d.Y + TY - 1) / TY;
-  const int tz0 = (blockIdx.x / (tilesx * tilesy)) * TZ;
-  const int ty0 = ((blockIdx.x / tilesx) % tilesy) * TY;
-  const int tx0 = (blockIdx.x % tilesx) * TX;
-  const int b = blockIdx.y;
-  const int64_t vol = d.vol();
-  const __nv_bfloat16* inb = in + (int64_t)b * CI * vol;
-  for (int i = threadIdx.x; i < CI * HV; i += TV) {
-    const int c = i / HV, h = i % HV;
-    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-    const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-    float v = 0.f;
-    if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z)
-      v = __bfloat162float(inb[(int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
-    in_s[i] = v;
-  }
-  for (int i = threadIdx.x; i < CO * CI * 27; i += TV) {
-    const int co = i / (CI * 27), r = i % (CI * 27);   // r = ci*27 + tap
-    w_s[r * CO + co] = __bfloat162float(w[i]);
-  }
-  __syncthreads();
-  const int lx = threadIdx.x % TX, ly = (threadIdx.x / TX) % TY, lz = threadIdx.x / (TX * TY);
-  const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
-  float acc[CO];
-#pragma unroll
-  for (int co = 0; co < CO; ++co) acc[co] = bias ? bias[co] : 0.f;
-  for (int ci = 0; ci < CI; ++ci) {
-    const float* src = in_s + ci * HV;
-    const float* wc = w_s + ci * 27 * CO;
-#pragma unroll
-    for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-      for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 3; ++dx) {
-          const float v = src[((lz + dz) * HY + (ly + dy)) * HX + (lx + dx)];
-          const float* wt = wc + ((dz * 3 + dy) * 3 + dx) * CO;
-#pragma unroll
-          for (int co = 0; co < CO; ++co) acc[co] = fmaf(wt[co], v, acc[co]);
-        }
-  }
-  if (gx >= d.X || gy >= d.Y || gz >= d.Z) return;
-  const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
-  const int64_t ob = (int64_t)b * CO * vol;
-#pragma unroll
-  for (int co = 0; co < CO; ++co) {
-    const int64_t o = ob + (int64_t)co * vol + p;
-    if (MODE == FWD_HIDDEN) {
-      z[o] = acc[co];
-      act[o] = __float2bfloat16_rn(gelu(acc[co]));
-    } else if (MODE == FWD_LAST) {
-      z[o] = acc[co];
-    } else if (MODE == INFER_HIDDEN) {
-      act[o] = __float2bfloat16_rn(gelu(acc[co]));
-    } else {
-      act[o] = __float2bfloat16_rn(acc[co] * gelu_grad(zaux[o]));
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// The 16 -> 16 channel convolutions on the tensor cores (tcgen05), as an
-// implicit GEMM: an output tile of 128 voxels (8 x-consecutive by 16
-// y-consecutive in one z plane) is the M dimension, the 16 output channels N,
-// and each of the 27 taps one K = 16 step over the input channels:
+// The 3x3x3 convolutions on the tensor cores (tcgen05), as an implicit GEMM:
+// an output tile of 128 voxels (8 x-consecutive by 16 y-consecutive in one z
+// plane) is the M dimension, the 16 output channels N, and each of the 27
+// taps one K = 16 step over the 16 input channels (layers with fewer channels
+// are padded with zero channels):
 // D[m][co] = sum_tap sum_ci A_tap[m][ci] W_tap[ci][co].  Both operands sit in
 // shared memory K-major without swizzle (core matrices of 8 rows x 16 bytes):
 // the input halo (10 x 18 x 3 voxels) as two halves of 8 channels,
@@ -171,7 +96,7 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
-template <int MODE>
+template <int CI, int CO, int MODE>
 __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __restrict__ in, Dims d, int B,
                                                       const __nv_bfloat16* __restrict__ w,
                                                       const float* __restrict__ bias, float* __restrict__ z,
@@ -186,10 +111,12 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
   const int tilesx = (d.X + CTX - 1) / CTX, tilesy = (d.Y + CTY - 1) / CTY;
   const int tiles = tilesx * tilesy * d.Z;
   const int64_t vol = d.vol();
-  // weights once per block: w[co][ci][tap] -> tap * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2
+  // weights once per block: w[co][ci][tap] -> tap * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2,
+  // zero for the padding channels (ci >= CI or co >= CO)
   for (int i = tid; i < 16 * 16 * 27; i += 128) {
     const int co = i / (16 * 27), r = i % (16 * 27), ci = r / 27, tap = r % 27;
-    *reinterpret_cast<__nv_bfloat16*>(Bs + tap * 512 + (ci >> 3) * 256 + co * 16 + (ci & 7) * 2) = w[i];
+    const __nv_bfloat16 v = (co < CO && ci < CI) ? w[(co * CI + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
+    *reinterpret_cast<__nv_bfloat16*>(Bs + tap * 512 + (ci >> 3) * 256 + co * 16 + (ci & 7) * 2) = v;
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
@@ -213,24 +140,38 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
     const int tz0 = tile / (tilesx * tilesy);
     const int ty0 = ((tile / tilesx) % tilesy) * CTY;
     const int tx0 = (tile % tilesx) * CTX;
-    const __nv_bfloat16* inb = in + (int64_t)b * 16 * vol;
-    // halo: the 8 channels of one half of voxel v as one 16-byte store at half * A_HALF + v * 16
-    for (int i = tid; i < 2 * CHV; i += 128) {
-      const int half = i / CHV, v = i % CHV;
-      const int hx = v % CHX, hy = (v / CHX) % CHY, hz = v / (CHX * CHY);
-      const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-      uint4 q = make_uint4(0u, 0u, 0u, 0u);
-      if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z) {
-        const __nv_bfloat16* src = inb + (int64_t)(half * 8) * vol + ((int64_t)gz * d.Y + gy) * d.X + gx;
-        unsigned short e[8];
+    const __nv_bfloat16* inb = in + (int64_t)b * CI * vol;
+    // halo: the 8 channels of one half of voxel v as one 16-byte store at
+    // half * A_HALF + v * 16; all of a thread's loads are issued before the
+    // first store (the loads are independent, their latency overlaps)
+    constexpr int HALO_ITEMS = 2 * CHV, HALO_PER_T = (HALO_ITEMS + 127) / 128;
+    uint32_t q[HALO_PER_T][4];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) e[c] = __bfloat16_as_ushort(src[(int64_t)c * vol]);
-        q.x = e[0] | ((uint32_t)e[1] << 16);
-        q.y = e[2] | ((uint32_t)e[3] << 16);
-        q.z = e[4] | ((uint32_t)e[5] << 16);
-        q.w = e[6] | ((uint32_t)e[7] << 16);
+    for (int k = 0; k < HALO_PER_T; ++k) {
+      const int i = tid + k * 128;
+      q[k][0] = q[k][1] = q[k][2] = q[k][3] = 0u;
+      if (i < HALO_ITEMS) {
+        const int half = i / CHV, v = i % CHV;
+        const int hx = v % CHX, hy = (v / CHX) % CHY, hz = v / (CHX * CHY);
+        const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+        if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z && half * 8 < CI) {
+          const unsigned short* src = reinterpret_cast<const unsigned short*>(inb) + (int64_t)(half * 8) * vol +
+                                      ((int64_t)gz * d.Y + gy) * d.X + gx;
+#pragma unroll
+          for (int c = 0; c < 8; c += 2) {
+            const uint32_t lo = half * 8 + c < CI ? (uint32_t)__ldg(src + (int64_t)c * vol) : 0u;
+            const uint32_t hi = half * 8 + c + 1 < CI ? (uint32_t)__ldg(src + (int64_t)(c + 1) * vol) : 0u;
+            q[k][c / 2] = lo | (hi << 16);
+          }
+        }
       }
-      *reinterpret_cast<uint4*>(As + half * TC_A_HALF + v * 16) = q;
+    }
+#pragma unroll
+    for (int k = 0; k < HALO_PER_T; ++k) {
+      const int i = tid + k * 128;
+      if (i < HALO_ITEMS)
+        *reinterpret_cast<uint4*>(As + (i / CHV) * TC_A_HALF + (i % CHV) * 16) =
+            make_uint4(q[k][0], q[k][1], q[k][2], q[k][3]);
     }
     // the tile's smem writes reach the tensor cores; the previous tile's
     // tensor-memory reads are done before the MMAs overwrite the accumulator
@@ -251,6 +192,18 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
       }
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
                    ::"r"(smem_u32(&mbar)));
+    }
+    // this thread's output voxel; the backward mode's pre-activations are
+    // loaded while the MMAs run
+    const int m = warp * 32 + lane;
+    const int gx = tx0 + (m & 7), gy = ty0 + (m >> 3), gz = tz0;
+    const bool inside = gx < d.X && gy < d.Y;
+    const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
+    const int64_t ob = (int64_t)b * CO * vol;
+    float za[MODE == BWD_DATA ? CO : 1];
+    if constexpr (MODE == BWD_DATA) {
+#pragma unroll
+      for (int co = 0; co < CO; ++co) za[co] = inside ? __ldg(zaux + ob + (int64_t)co * vol + p) : 0.f;
     }
     uint32_t done = 0;
     for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it)
@@ -273,22 +226,20 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
                    "=r"(r[15])
                  : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
     asm volatile("tcgen05.wait::ld.sync.aligned;");
-    const int m = warp * 32 + lane;
-    const int gx = tx0 + (m & 7), gy = ty0 + (m >> 3), gz = tz0;
-    if (gx < d.X && gy < d.Y) {
-      const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
-      const int64_t ob = (int64_t)b * 16 * vol;
+    if (inside) {
 #pragma unroll
-      for (int co = 0; co < 16; ++co) {
+      for (int co = 0; co < CO; ++co) {
         const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
         const int64_t o = ob + (int64_t)co * vol + p;
         if (MODE == FWD_HIDDEN) {
           z[o] = acc;
           act[o] = __float2bfloat16_rn(gelu(acc));
+        } else if (MODE == FWD_LAST) {
+          z[o] = acc;
         } else if (MODE == INFER_HIDDEN) {
           act[o] = __float2bfloat16_rn(gelu(acc));
         } else {
-          act[o] = __float2bfloat16_rn(acc * gelu_grad(zaux[o]));
+          act[o] = __float2bfloat16_rn(acc * gelu_grad(za[MODE == BWD_DATA ? co : 0]));
         }
       }
     }
@@ -298,47 +249,50 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(32));
 }
 
-template <int MODE>
+template <int CI, int CO, int MODE>
 static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
                            const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
   static bool attr = false;
   if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
+    cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
     if (e != cudaSuccess) return e;
     attr = true;
   }
   static int cap = 0;
   if (!cap) {
     int dev = 0, sms = 0, nb = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_tc_kernel<MODE>, 128, TC_SMEM);
-    cap = (nb > 0 ? nb : 1) * (sms > 0 ? sms : 1);
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_tc_kernel<CI, CO, MODE>, 128, (size_t)TC_SMEM);
+    if (e != cudaSuccess) return e;
+    // the occupancy query answers one block per SM for this kernel, although
+    // shared memory (the binding limit) admits seven; blocks beyond the
+    // resident ones only queue (no block waits on another), so launch as many
+    // as shared memory admits
+    const int by_smem = (227 * 1024) / (TC_SMEM + 2048);
+    nb = std::max(nb, std::min(8, by_smem));
+    cap = nb * (sms > 0 ? sms : 1);
   }
   const int64_t jobs = (int64_t)((d.X + CTX - 1) / CTX) * ((d.Y + CTY - 1) / CTY) * d.Z * B;
   const int grid = (int)(jobs < cap ? jobs : cap);   // persistent blocks, tiles in a grid-stride loop
-  conv_tc_kernel<MODE><<<grid, 128, TC_SMEM, st>>>(in, d, B, w, bias, z, act, zaux, flag);
+  conv_tc_kernel<CI, CO, MODE><<<grid, 128, TC_SMEM, st>>>(in, d, B, w, bias, z, act, zaux, flag);
   return cudaGetLastError();
 }
 
-// 16 -> 16 channels (not the last layer) on the tensor cores, the others
-// (2 -> 16, 16 -> 1, 1 -> 16) on the CUDA cores: N = 1 or K = 2 per tap do not
-// fill an MMA.
+// Every layer on the tensor cores: fewer than 16 input or output channels
+// (2 -> 16, 16 -> 1, 1 -> 16) are padded with zero channels to K = 16 per tap
+// and N = 16 (the MMAs cost little; the halo loads and the stores skip the
+// padding).  Modes: FWD_HIDDEN writes z (FP32) and act = bf16(gelu(z));
+// FWD_LAST z only; INFER_HIDDEN act only; BWD_DATA act = bf16(sum *
+// gelu'(zaux)) (the gradient of the previous layer's pre-activation; w then
+// holds that layer's weights transposed and flipped).  w: [CO][CI][27] bf16,
+// bias: CO floats or NULL.
 template <int CI, int CO, int MODE>
 static cudaError_t conv(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
                         const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
-  if constexpr (CI == 16 && CO == 16 && MODE != FWD_LAST) return conv_tc<MODE>(st, in, d, B, w, bias, z, act, zaux, flag);
-  const size_t smem = sizeof(float) * (CI * HV + CO * CI * 27);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(conv_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
-  const int tiles = ((d.X + TX - 1) / TX) * ((d.Y + TY - 1) / TY) * ((d.Z + TZ - 1) / TZ);
-  conv_kernel<CI, CO, MODE><<<dim3(tiles, B), TV, smem, st>>>(in, d, w, bias, z, act, zaux);
-  return cudaGetLastError();
+  static_assert(CI <= 16 && CO <= 16, "the tensor-core convolution takes up to 16 channels");
+  return conv_tc<CI, CO, MODE>(st, in, d, B, w, bias, z, act, zaux, flag);
 }
 
 // ---------------------------------------------------------------------------
