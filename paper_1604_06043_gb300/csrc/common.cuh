@@ -363,18 +363,16 @@ __device__ inline bool warp_lu_solve(double* a, double* z, int n, double* lbuf) 
   bool ok = !__any_sync(FULL, bad);
   __syncwarp();
   for (int k = 0; ok && k < n; ++k) {
-    // first row p >= k with the largest |a_pk|
-    long long key = (lane >= k && lane < n) ? (__double_as_longlong(a[lane * n + k]) & MAG) : -1LL;
-    int idx = lane;
-#pragma unroll
-    for (int o = 16; o >= 1; o >>= 1) {
-      const long long ok_ = __shfl_xor_sync(FULL, key, o);
-      const int oi = __shfl_xor_sync(FULL, idx, o);
-      if (ok_ > key || (ok_ == key && oi < idx)) {
-        key = ok_;
-        idx = oi;
-      }
-    }
+    // first row p >= k with the largest |a_pk|: the 63-bit magnitude compared
+    // as (high word, low word) with warp max-reductions, then the lowest lane
+    // holding that maximum
+    const bool valid = lane >= k && lane < n;
+    const long long mag = valid ? (__double_as_longlong(a[lane * n + k]) & MAG) : 0LL;
+    const unsigned hi = (unsigned)((unsigned long long)mag >> 32), lo = (unsigned)mag;
+    const unsigned mhi = __reduce_max_sync(FULL, valid ? hi : 0u);
+    const unsigned mlo = __reduce_max_sync(FULL, (valid && hi == mhi) ? lo : 0u);
+    const int idx = (int)__reduce_min_sync(FULL, (valid && hi == mhi && lo == mlo) ? (unsigned)lane : 32u);
+    const long long key = (long long)(((unsigned long long)mhi << 32) | mlo);
     if (key < thr_key[k]) {
       ok = false;
       break;

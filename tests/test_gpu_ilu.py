@@ -258,3 +258,32 @@ def test_128_factor_closed_form_every_row(M):
     print("128^3 ILU(0): first system %d MVs, %d cycles, %.1f ms, preconditioned relres %.2e, original %.2e"
           % (st.mvs, st.cycles, st.ms, st.relres_true, st.relres_orig))
     S.close()
+
+
+def test_csr_format_and_zero_rhs(M):
+    # the operator with the CSR product (the factor and sweeps are format-independent)
+    w = pb.WORKLOADS["convdiff3d_24"]
+    A = w.matrix()
+    b = w.x0() / w.tau + w.f()
+    F = I.Factors.from_values(A, I.ilu0(A))
+    ref, xo, _ = I.precond_solve(A, F, b, w.x0(), w.s, w.ell, O.orthonormalize_mgs2(w.p_raw()), tol=w.tol)
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, precond=M.PRECOND_ILU0, replace_every=1,
+                 fetch_policy=M.FETCH_NEVER, spmv_format=M.FORMAT_CSR)
+    x = _t(w.x0())
+    st = S.solve(_t(b), x, w.tol)
+    hist, _ = S.history()
+    assert st.status == 0 and mvs_match(st.mvs, ref.mvs, hist, ref.history, w.tol)
+    assert np.linalg.norm(x.cpu().numpy() - xo) <= 1e-6 * np.linalg.norm(xo)
+    # b = 0: x = 0 without a product
+    x = _t(w.x0())
+    st = S.solve(torch.zeros(A.n, dtype=torch.float64, device=DEV), x, w.tol)
+    assert st.status == 0 and st.mvs == 0 and not x.cpu().numpy().any()
+    # entry-point argument checks
+    y = torch.empty_like(x)
+    with pytest.raises(M.MsstabError) as e:
+        S.op_ilu_apply(4, x, y)
+    assert e.value.status == M.ERR_INVALID_ARG
+    with pytest.raises(M.MsstabError) as e:
+        S.op_ilu_apply(2, x, x)
+    assert e.value.status == M.ERR_INVALID_ARG
+    S.close()
