@@ -41,8 +41,9 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one launch of the dominant kernel of each form,
 # from one ncu capture of the current kernel at 128^3
 # (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md, ..._fp32inner_...).
-NCU_TRAFFIC = {("fp64", "spmv_dot"): 342_601_472, ("fp32_inner", "spmv_dot"): 200_179_712,
-               ("ilu0", "precond"): 133_184_512}
+NCU_TRAFFIC = {("convdiff3d_128", "fp64", "spmv_dot"): 342_601_472,
+               ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_179_712,
+               ("convdiff3d_128", "ilu0", "precond"): 133_184_512}
 
 
 def parse_args(argv=None):
@@ -210,10 +211,17 @@ def FP32_INNER_OPTS(M):
     return dict(precision=M.PREC_FP32_INNER, inner_ell=1, fetch_policy=M.FETCH_NEVER, max_outer=40)
 
 
+def s_ell_cols(w):
+    """Vector columns of the FP64 workspace: (s+1)(l+2) + 3s + 4."""
+    return (w.s + 1) * (w.ell + 2) + 3 * w.s + 4
+
+
 def workload_config(w, n, nnz, W, K, form, world):
     """The `config` object of both arms' JSON lines."""
     dims = "x".join(str(d) for d in w.shape)
-    return {"workload": f"{w.name}: 3D convection-diffusion, 7-point FD on a {dims} grid (N={n}, nnz={nnz}), "
+    kind = ("variable-coefficient convection-diffusion (lognormal kappa, sigma 1, correlation 8 cells)"
+            if getattr(w, "variable_kappa", False) else "convection-diffusion")
+    return {"workload": f"{w.name}: 3D {kind}, 7-point FD on a {dims} grid (N={n}, nnz={nnz}), "
                         f"beta={tuple(w.beta)}, implicit Euler tau={w.tau}, systems {W + 1}..{W + K} of the sequence",
             "method": {"fp64": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
                        "fp32_inner": f"FP32-inner M({w.s})stab(1) with FP64 defect correction, SELL-32",
@@ -221,7 +229,8 @@ def workload_config(w, n, nnz, W, K, form, world):
                        "ilu0": f"M({w.s})stab({w.ell}) on L^-1 A U^-1 (ILU(0) split preconditioner), fetch once "
                                f"at sqrt(tol), FP64, SELL-32"}[form],
             "true_residual": "replaced every cycle" if w.replace_every == 1 else "checked at convergence",
-            "tol": w.tol, "l2": "inputs larger than L2 (matrix 0.18 GB + ~90 vectors of 16.8 MB), no flush",
+            "tol": w.tol, "l2": f"inputs larger than L2 (matrix {12 * nnz / 1e9:.2f} GB + {(s_ell_cols(w))} vectors "
+                               f"of {8 * n / 1e6:.1f} MB), no flush",
             "parallelism": "replicas" if world > 1 else "single GPU"}
 
 
@@ -639,13 +648,13 @@ def main(argv=None):
         # FP64 FMA throughput, not HBM, binds this kernel on GB300
         roofline = {"kernel": dom, "bound": "alu", "achieved": kd["fp64_tflops"], "peak": FP64_NOMINAL_TFLOPS,
                     "unit": "TFLOP/s (FP64)", "frac": kd["fp64_frac_nominal"],
-                    "traffic": NCU_TRAFFIC.get((args.form, dom)),
+                    "traffic": NCU_TRAFFIC.get((args.workload, args.form, dom)),
                     "peak_source": "nominal GB300 FP64 rate (no measured FP64 peak in MEASURED_PEAKS.json)",
                     "hbm": {"achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s", "frac": kd["hbm_frac"]},
                     "share_of_step": share}
     else:
         roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s",
-                    "frac": kd["hbm_frac"], "traffic": NCU_TRAFFIC.get((args.form, dom)),
+                    "frac": kd["hbm_frac"], "traffic": NCU_TRAFFIC.get((args.workload, args.form, dom)),
                     "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                     "fp64_frac_of_nominal": kd["fp64_frac_nominal"], "share_of_step": share}
 

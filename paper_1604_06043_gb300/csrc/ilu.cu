@@ -747,10 +747,18 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
     for (int W : {4, 8}) {
       if (!ok) break;
       const void* k = W == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
-      ICK(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CH)));
       int nbk = 0;
-      ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-          &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, sizeof(double) * CH));
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CH)) !=
+              cudaSuccess ||
+          cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, sizeof(double) * CH) !=
+              cudaSuccess) {
+        cudaGetLastError();   // not this GPU's shape: the level-by-level sweeps serve
+        ok = false;
+        break;
+      }
+      // one wave: every chunk's block resident at once (several chunks per
+      // block in turn measured 1.36x slower than the level sweeps at 256^3)
       if ((int64_t)nbk * c.sms < (n + CH - 1) / CH) ok = false;
     }
     if (ok) {
