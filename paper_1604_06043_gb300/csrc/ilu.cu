@@ -290,6 +290,10 @@ __global__ void ilu_pad_counts_kernel(int nlev, const int* lptr, int* cnt) {
 // the sweep completes; every wait is bounded (BAR_SPIN_LIMIT polls, then
 // FLAG_SYNC_TIMEOUT and NaN), and a thread that sees the flag stops waiting.
 // Lanes of a warp wait only on other blocks, never on each other.
+// A chunk too large for shared memory (more than 28k rows) reads its own
+// values back through L2 like the others: they are final once the block
+// barrier after their group has passed (2.1 ms per triangle at 256^3, against
+// 3.4 ms level by level).
 // What bounds it: a chunk is smaller than a grid plane, so nearly every row
 // needs a value the neighbouring chunk produced one level earlier; the chunks
 // settle into a lockstep of one store-to-load trip per level (2.3 us at
@@ -326,6 +330,7 @@ __device__ __noinline__ unsigned long long wait_value(const double* p, int* flag
 struct ChunkArgs {
   int npos;              // positions (= rows); column stride of pcol / pval
   int CH;                // rows per chunk
+  int in_smem;           // 1: the chunk's values also kept in shared memory
   const int* gofs;       // chunk b's local levels: groups [gofs[b], gofs[b+1])
   const int* gptr;       // positions of group q: [gptr[q], gptr[q+1])
   const int* prow;
@@ -377,7 +382,7 @@ __global__ void __launch_bounds__(CTS, 1) ilu_sweep_chunk_kernel(ChunkArgs a) {
       }
       if (a.pdiag) sum = sum / dia;
       if ((unsigned long long)__double_as_longlong(sum) == SENTINEL) sum = __longlong_as_double(0x7FFFFFFFFFFFFFFFLL);
-      sv[row - r0] = sum;
+      if (a.in_smem) sv[row - r0] = sum;
       st_relaxed(a.out + row, sum);
     }
     __syncthreads();
@@ -405,9 +410,11 @@ __global__ void ilu_chunk_key_kernel(int n, int CH, const int* lev, const int* l
 }
 
 // the packed dependencies of the positions of the chunked order
-__global__ void ilu_chunk_pack_kernel(int n, int CH, int upper, const int* prow, const int* rp, const int* col,
-                                      const int* dg, const double* lu, int* pcnt, int* pcol, double* pval,
-                                      double* pdiag) {
+// (in_smem == 0: every dependency as its global row index; the chunk's own
+// values are then read back through L2 like the others)
+__global__ void ilu_chunk_pack_kernel(int n, int CH, int upper, int in_smem, const int* prow, const int* rp,
+                                      const int* col, const int* dg, const double* lu, int* pcnt, int* pcol,
+                                      double* pval, double* pdiag) {
   const int stride = gridDim.x * blockDim.x;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
     const int i = prow[idx];
@@ -416,7 +423,7 @@ __global__ void ilu_chunk_pack_kernel(int n, int CH, int upper, const int* prow,
     pcnt[idx] = e - b;
     for (int p = b; p < e; ++p) {
       const int j = col[p];
-      pcol[(int64_t)(p - b) * n + idx] = (j / CH == i / CH) ? ~(j - r0) : j;
+      pcol[(int64_t)(p - b) * n + idx] = (in_smem && j / CH == i / CH) ? ~(j - r0) : j;
       pval[(int64_t)(p - b) * n + idx] = lu[p];
     }
     if (upper) pdiag[idx] = lu[dg[i]];
@@ -544,11 +551,11 @@ static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const doub
     }
     e = cudaMemsetAsync(out, 0xFF, sizeof(double) * F.n, c.stream);
     if (e != cudaSuccess) return e;
-    ChunkArgs ca{F.n, F.CH[u], F.gofs[u], F.gptr[u], F.cprow[u], F.cpcnt[u], F.cpcol[u], F.cpval[u],
-                 u == 1 ? F.cpdiag : nullptr, in, out, F.flag};
+    ChunkArgs ca{F.n, F.CH[u], F.csmem ? 1 : 0, F.gofs[u], F.gptr[u], F.cprow[u], F.cpcnt[u], F.cpcol[u],
+                 F.cpval[u], u == 1 ? F.cpdiag : nullptr, in, out, F.flag};
     void* cargs[] = {&ca};
     const int P = (F.n + F.CH[u] - 1) / F.CH[u];
-    const size_t smem = sizeof(double) * (size_t)F.CH[u];
+    const size_t smem = F.csmem ? sizeof(double) * (size_t)F.CH[u] : 0;
     const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
     return cudaLaunchCooperativeKernel(k, dim3(P), dim3(CTS), cargs, smem, c.stream);
   }
@@ -741,24 +748,29 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
   // chunked order for the pipelined solves: one chunk of rows per SM, its
   // values in shared memory (at most CHUNK_SMEM bytes)
   {
-    const size_t CHUNK_SMEM = 227 * 1024;
+    const size_t CHUNK_SMEM = 224 * 1024;
     const int CH = (n + c.sms - 1) / c.sms;
-    bool ok = sizeof(double) * (size_t)CH <= CHUNK_SMEM && (F.W[0] > 0 || F.W[1] > 0);
+    // a chunk too large for shared memory reads its own values back through
+    // L2 (they are final once their group's block barrier has passed)
+    F.csmem = sizeof(double) * (size_t)CH <= CHUNK_SMEM;
+    const size_t csm = F.csmem ? sizeof(double) * (size_t)CH : 0;
+    bool ok = F.W[0] > 0 || F.W[1] > 0;
     for (int W : {4, 8}) {
       if (!ok) break;
       const void* k = W == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
       int nbk = 0;
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(sizeof(double) * CH)) !=
-              cudaSuccess ||
+      // the attribute is the kernel's (every handle of the process shares it):
+      // always the largest chunk size, so that no handle's launches exceed it
+      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHUNK_SMEM) != cudaSuccess ||
           cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, sizeof(double) * CH) !=
-              cudaSuccess) {
+              &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, csm) != cudaSuccess) {
         cudaGetLastError();   // not this GPU's shape: the level-by-level sweeps serve
         ok = false;
         break;
       }
       // one wave: every chunk's block resident at once (several chunks per
-      // block in turn measured 1.36x slower than the level sweeps at 256^3)
+      // block in turn, with the chunks in shared memory, measured 1.36x slower
+      // than the level sweeps at 256^3)
       if ((int64_t)nbk * c.sms < (n + CH - 1) / CH) ok = false;
     }
     if (ok) {
@@ -806,8 +818,8 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
       ilu_level_scan_kernel<<<1, 1024, 0, c.stream>>>(TG, cnt, F.gptr[u], scratch + 2);
       ICK(cudaMemcpyAsync(cnt, F.gptr[u], sizeof(int) * (size_t)TG, cudaMemcpyDeviceToDevice, c.stream));
       ilu_level_scatter_kernel<<<g, NT, 0, c.stream>>>(n, key, cnt, F.cprow[u]);
-      ilu_chunk_pack_kernel<<<g, NT, 0, c.stream>>>(n, CH, u, F.cprow[u], F.row_ptr, F.col, F.diag, F.lu,
-                                                    F.cpcnt[u], F.cpcol[u], F.cpval[u], F.cpdiag);
+      ilu_chunk_pack_kernel<<<g, NT, 0, c.stream>>>(n, CH, u, F.csmem ? 1 : 0, F.cprow[u], F.row_ptr, F.col,
+                                                    F.diag, F.lu, F.cpcnt[u], F.cpcol[u], F.cpval[u], F.cpdiag);
       ICK(cudaGetLastError());
       F.CH[u] = CH;
       F.groups[u] = TG;
