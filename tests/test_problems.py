@@ -90,3 +90,21 @@ def test_seeds_are_reproducible():
 def test_tridiag_orientation():
     T = pb.tridiag(5, 2.0, 3.0, 1.0).to_dense()
     assert T[1, 0] == 2.0 and T[1, 1] == 3.0 and T[1, 2] == 1.0
+
+
+def test_random_sparse_pattern():
+    for band in (None, 7):
+        A = pb.random_sparse(300, 6, seed=9, band=band)
+        rp, col, val = A.row_ptr, A.col, A.val
+        assert rp[0] == 0 and rp[-1] == col.size == val.size
+        for i in range(A.n):
+            c = col[rp[i]:rp[i + 1]]
+            v = val[rp[i]:rp[i + 1]]
+            assert np.all(np.diff(c) > 0) and i in c                 # sorted, unique, diagonal present
+            if band is not None:
+                assert np.all(np.abs(c - i) <= band)
+            d = v[c == i][0]
+            assert d > np.abs(v[c != i]).sum()                        # strict diagonal dominance
+    B = pb.random_sparse(300, 6, seed=9)
+    C = pb.random_sparse(300, 6, seed=9)
+    assert np.array_equal(B.col, C.col) and np.array_equal(B.val, C.val)
