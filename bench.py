@@ -41,8 +41,8 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one launch of the dominant kernel of each form,
 # from one ncu capture of the current kernel at 128^3
 # (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md, ..._fp32inner_...).
-NCU_TRAFFIC = {("convdiff3d_128", "fp64", "spmv_dot"): 342_601_472,
-               ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_179_712,
+NCU_TRAFFIC = {("convdiff3d_128", "fp64", "spmv_dot"): 342_305_280,
+               ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_367_872,
                ("convdiff3d_128", "ilu0", "precond"): 133_184_512}
 
 
