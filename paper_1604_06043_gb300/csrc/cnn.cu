@@ -34,6 +34,7 @@ constexpr int CI_[NL] = {2, 16, 16, 16};
 constexpr int CO_[NL] = {16, 16, 16, 1};
 constexpr int TX = 8, TY = 8, TZ = 4, TV = TX * TY * TZ;   // output tile, one voxel per thread
 constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HV = HX * HY * HZ;
+constexpr int HVP = HV + 1;   // 601: channel planes in shared memory start in distinct banks
 
 __host__ __device__ constexpr int n_params() {
   return 2 * 16 * 27 + 16 + 16 * 16 * 27 + 16 + 16 * 16 * 27 + 16 + 16 * 1 * 27 + 1;
@@ -306,8 +307,9 @@ __global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restri
   constexpr int GROUPS = TV / PAIRS >= 1 ? TV / PAIRS : 1;
   constexpr int NV = PAIRS * 27 + CO;
   extern __shared__ float smem[];
-  float* a_s = smem;                  // [CI][HV]
-  float* g_s = smem + CI * HV;        // [CO][TV]
+  float* a_s = smem;                  // [CI][HVP]: planes one word longer than HV, so that the
+                                      // lanes' 16 channels fall in distinct banks
+  float* g_s = smem + CI * HVP;       // [CO][TV]
   float* r_s = g_s + CO * TV;         // [GROUPS][PAIRS][28]
   const int tilesx = (d.X + TX - 1) / TX, tilesy = (d.Y + TY - 1) / TY;
   const int tz0 = (blockIdx.x / (tilesx * tilesy)) * TZ;
@@ -322,7 +324,7 @@ __global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restri
     float v = 0.f;
     if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z)
       v = __bfloat162float(a[(int64_t)b * CI * vol + (int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
-    a_s[i] = v;
+    a_s[c * HVP + h] = v;
   }
   for (int i = threadIdx.x; i < CO * TV; i += TV) {
     const int c = i / TV, t = i % TV;
@@ -344,7 +346,7 @@ __global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restri
     for (int t = grp; t < TV; t += GROUPS) {
       const float gv = g_s[co * TV + t];
       const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-      const float* src = a_s + ci * HV;
+      const float* src = a_s + ci * HVP;
 #pragma unroll
       for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
@@ -378,7 +380,7 @@ static cudaError_t wgrad(cudaStream_t st, const __nv_bfloat16* a, const __nv_bfl
                          float* partials, int* nblocks) {
   constexpr int PAIRS = CO * CI;
   constexpr int GROUPS = TV / PAIRS >= 1 ? TV / PAIRS : 1;
-  const size_t smem = sizeof(float) * (CI * HV + CO * TV + GROUPS * PAIRS * 28);
+  const size_t smem = sizeof(float) * (CI * HVP + CO * TV + GROUPS * PAIRS * 28);
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -391,12 +393,25 @@ static cudaError_t wgrad(cudaStream_t st, const __nv_bfloat16* a, const __nv_bfl
   return cudaGetLastError();
 }
 
-// grad[i] = sum over blocks of partials[blk][i], in block order (FP64 sum)
-__global__ void reduce_partials_kernel(const float* partials, int nblocks, int nv, float* grad) {
+// grad[i] = sum over blocks of partials[blk][i] (FP64), in a fixed order: the
+// blocks in RED_CHUNKS consecutive ranges summed in block order (one
+// grid row per range), then the range sums in range order
+constexpr int RED_CHUNKS = 32;
+__global__ void reduce_partials_chunk_kernel(const float* partials, int nblocks, int nv, double* chunk_sums) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nv) return;
+  const int per = (nblocks + RED_CHUNKS - 1) / RED_CHUNKS;
+  const int b0 = blockIdx.y * per, b1 = min(nblocks, b0 + per);
+  double s = 0.0;
+  for (int b = b0; b < b1; ++b) s += (double)partials[(size_t)b * nv + i];
+  chunk_sums[(size_t)blockIdx.y * nv + i] = s;
+}
+
+__global__ void reduce_partials_kernel(const double* chunk_sums, int nv, float* grad) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nv) return;
   double s = 0.0;
-  for (int b = 0; b < nblocks; ++b) s += (double)partials[(size_t)b * nv + i];
+  for (int c = 0; c < RED_CHUNKS; ++c) s += chunk_sums[(size_t)c * nv + i];
   grad[i] = (float)s;
 }
 
@@ -610,6 +625,7 @@ struct msstab_cnn_s {
   float* sbuf = nullptr;        // K * (out - t) of the batch
   float* partials = nullptr;
   double* dpart = nullptr;
+  double* chunk_sums = nullptr; // [RED_CHUNKS][values] of the weight-gradient reduction
   double* h_small = nullptr;
   int* origins = nullptr;
   // inference buffers (full grid)
@@ -687,6 +703,14 @@ msstab_status forward_batch(msstab_cnn_t h, int B, int D) {
 }
 
 // loss of z[3] against tgt, gradient into h->grad; *loss on the host
+// weight and bias gradients of one layer from the wgrad partials
+msstab_status reduce_partials(msstab_cnn_t h, int nb, int nv, float* grad) {
+  reduce_partials_chunk_kernel<<<dim3(grid1(nv), RED_CHUNKS), 256, 0, h->stream>>>(h->partials, nb, nv, h->chunk_sums);
+  reduce_partials_kernel<<<grid1(nv), 256, 0, h->stream>>>(h->chunk_sums, nv, grad);
+  CCK(cudaGetLastError());
+  return MSSTAB_OK;
+}
+
 msstab_status backward_batch(msstab_cnn_t h, int B, int D, double* loss) {
   const Dims d{D, D, D};
   cudaStream_t st = h->stream;
@@ -703,17 +727,15 @@ msstab_status backward_batch(msstab_cnn_t h, int B, int D, double* loss) {
   int nb = 0;
   // layer 3 (16 -> 1)
   CCK((wgrad<16, 1>(st, h->act[3], h->dz[3], d, B, h->partials, &nb)));
-  reduce_partials_kernel<<<grid1(16 * 27 + 1), 256, 0, st>>>(h->partials, nb, 16 * 27 + 1, h->grad + w_offset(3));
+  CKA(reduce_partials(h, nb, 16 * 27 + 1, h->grad + w_offset(3)));
   CCK((conv<1, 16, BWD_DATA>(st, h->dz[3], d, B, h->wt[3], nullptr, nullptr, h->dz[2], h->z[2], h->tcflag)));
   for (int l = 2; l >= 1; --l) {
     CCK((wgrad<16, 16>(st, h->act[l], h->dz[l], d, B, h->partials, &nb)));
-    reduce_partials_kernel<<<grid1(16 * 16 * 27 + 16), 256, 0, st>>>(h->partials, nb, 16 * 16 * 27 + 16,
-                                                                     h->grad + w_offset(l));
+    CKA(reduce_partials(h, nb, 16 * 16 * 27 + 16, h->grad + w_offset(l)));
     CCK((conv<16, 16, BWD_DATA>(st, h->dz[l], d, B, h->wt[l], nullptr, nullptr, h->dz[l - 1], h->z[l - 1], h->tcflag)));
   }
   CCK((wgrad<2, 16>(st, h->act[0], h->dz[0], d, B, h->partials, &nb)));
-  reduce_partials_kernel<<<grid1(2 * 16 * 27 + 16), 256, 0, st>>>(h->partials, nb, 2 * 16 * 27 + 16,
-                                                                  h->grad + w_offset(0));
+  CKA(reduce_partials(h, nb, 2 * 16 * 27 + 16, h->grad + w_offset(0)));
   CCK(cudaGetLastError());
   if (loss) {
     std::vector<double> part(lg);
@@ -812,6 +834,7 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
   const int64_t tiles = ((crop + TX - 1) / TX) * (int64_t)((crop + TY - 1) / TY) * ((crop + TZ - 1) / TZ) * max_batch;
   CKC(calloc_(h, &h->partials, (size_t)tiles * (16 * 16 * 27 + 16)));
   CKC(calloc_(h, &h->dpart, 4096));
+  CKC(calloc_(h, &h->chunk_sums, (size_t)RED_CHUNKS * (16 * 16 * 27 + 16)));
   CKC(calloc_(h, &h->origins, 4 * (size_t)max_batch));
   if (max_pairs > 0) {
     CKC(calloc_(h, &h->pin, (size_t)max_pairs * 2 * h->N));
