@@ -35,6 +35,7 @@
 // stale L1 line.
 
 #include <algorithm>
+#include <cstdlib>
 #include <vector>
 
 #include "launch.h"
@@ -327,15 +328,16 @@ __device__ __noinline__ unsigned long long wait_value(const double* p, int* flag
   }
 }
 
+constexpr int GMAX = 1024;   // rows of one group kept in shared memory for the next group
+
 struct ChunkArgs {
   int npos;              // positions (= rows); column stride of pcol / pval
-  int CH;                // rows per chunk
-  int in_smem;           // 1: the chunk's values also kept in shared memory
-  const int* gofs;       // chunk b's local levels: groups [gofs[b], gofs[b+1])
+  const int* gofs;       // chunk b's groups (its rows' levels, in order): [gofs[b], gofs[b+1])
   const int* gptr;       // positions of group q: [gptr[q], gptr[q+1])
   const int* prow;
   const int* pcnt;
-  const int* pcol;       // dependency: ~(j - first row of the chunk) within the chunk, else j
+  const int* pcol;       // dependency: -1 - (its position in the previous group of the same chunk),
+                         // when it is there and within the first GMAX positions; else its row
   const double* pval;
   const double* pdiag;   // upper solve: u_ii by position; NULL: unit diagonal
   const double* in;
@@ -345,11 +347,12 @@ struct ChunkArgs {
 
 template <int W>
 __global__ void __launch_bounds__(CTS, 1) ilu_sweep_chunk_kernel(ChunkArgs a) {
-  extern __shared__ double sv[];
-  const int r0 = blockIdx.x * a.CH;
+  __shared__ double sv[2 * GMAX];   // the values of the previous and of the current group
   const int q0 = a.gofs[blockIdx.x], q1 = a.gofs[blockIdx.x + 1];
   for (int q = q0; q < q1; ++q) {
     const int beg = a.gptr[q], end = a.gptr[q + 1];
+    const double* prev = sv + ((q - 1) & 1) * GMAX;
+    double* cur = sv + (q & 1) * GMAX;
     for (int idx = beg + threadIdx.x; idx < end; idx += CTS) {
       const int row = __ldg(a.prow + idx);
       const int cnt = __ldg(a.pcnt + idx);
@@ -376,13 +379,13 @@ __global__ void __launch_bounds__(CTS, 1) ilu_sweep_chunk_kernel(ChunkArgs a) {
 #pragma unroll
       for (int j = 0; j < W; ++j) {
         if (j < cnt) {
-          const double xv = d[j] < 0 ? sv[~d[j]] : __longlong_as_double((long long)x[j]);
+          const double xv = d[j] < 0 ? prev[-1 - d[j]] : __longlong_as_double((long long)x[j]);
           sum = fma(-val[j], xv, sum);
         }
       }
       if (a.pdiag) sum = sum / dia;
       if ((unsigned long long)__double_as_longlong(sum) == SENTINEL) sum = __longlong_as_double(0x7FFFFFFFFFFFFFFFLL);
-      if (a.in_smem) sv[row - r0] = sum;
+      if (idx - beg < GMAX) cur[idx - beg] = sum;
       st_relaxed(a.out + row, sum);
     }
     __syncthreads();
@@ -409,21 +412,32 @@ __global__ void ilu_chunk_key_kernel(int n, int CH, const int* lev, const int* l
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) key[i] = gofs[i / CH] + lev[i] - lo[i / CH];
 }
 
-// the packed dependencies of the positions of the chunked order
-// (in_smem == 0: every dependency as its global row index; the chunk's own
-// values are then read back through L2 like the others)
-__global__ void ilu_chunk_pack_kernel(int n, int CH, int upper, int in_smem, const int* prow, const int* rp,
-                                      const int* col, const int* dg, const double* lu, int* pcnt, int* pcol,
-                                      double* pval, double* pdiag) {
+// position of each row in the chunked order
+__global__ void ilu_chunk_posof_kernel(int n, const int* prow, int* posof) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) posof[prow[idx]] = idx;
+}
+
+// the packed dependencies of the positions of the chunked order: a dependency
+// in the previous group of the same chunk (within its first GMAX positions)
+// as -1 - its position there, any other as its row
+__global__ void ilu_chunk_pack_kernel(int n, int CH, int upper, const int* prow, const int* key, const int* posof,
+                                      const int* gptr, const int* rp, const int* col, const int* dg,
+                                      const double* lu, int* pcnt, int* pcol, double* pval, double* pdiag) {
   const int stride = gridDim.x * blockDim.x;
   for (int idx = blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += stride) {
     const int i = prow[idx];
-    const int r0 = i / CH * CH;
+    const int ki = key[i];
     const int b = upper ? dg[i] + 1 : rp[i], e = upper ? rp[i + 1] : dg[i];
     pcnt[idx] = e - b;
     for (int p = b; p < e; ++p) {
       const int j = col[p];
-      pcol[(int64_t)(p - b) * n + idx] = (in_smem && j / CH == i / CH) ? ~(j - r0) : j;
+      int enc = j;
+      if (j / CH == i / CH && key[j] == ki - 1) {
+        const int s = posof[j] - gptr[ki - 1];
+        if (s < GMAX) enc = -1 - s;
+      }
+      pcol[(int64_t)(p - b) * n + idx] = enc;
       pval[(int64_t)(p - b) * n + idx] = lu[p];
     }
     if (upper) pdiag[idx] = lu[dg[i]];
@@ -551,13 +565,12 @@ static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const doub
     }
     e = cudaMemsetAsync(out, 0xFF, sizeof(double) * F.n, c.stream);
     if (e != cudaSuccess) return e;
-    ChunkArgs ca{F.n, F.CH[u], F.csmem ? 1 : 0, F.gofs[u], F.gptr[u], F.cprow[u], F.cpcnt[u], F.cpcol[u],
-                 F.cpval[u], u == 1 ? F.cpdiag : nullptr, in, out, F.flag};
+    ChunkArgs ca{F.n, F.gofs[u], F.gptr[u], F.cprow[u], F.cpcnt[u], F.cpcol[u], F.cpval[u],
+                 u == 1 ? F.cpdiag : nullptr, in, out, F.flag};
     void* cargs[] = {&ca};
     const int P = (F.n + F.CH[u] - 1) / F.CH[u];
-    const size_t smem = F.csmem ? sizeof(double) * (size_t)F.CH[u] : 0;
     const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
-    return cudaLaunchCooperativeKernel(k, dim3(P), dim3(CTS), cargs, smem, c.stream);
+    return cudaLaunchCooperativeKernel(k, dim3(P), dim3(CTS), cargs, 0, c.stream);
   }
   e = cudaMemsetAsync(&F.bar->count, 0, sizeof(unsigned int), c.stream);
   if (e != cudaSuccess) return e;
@@ -745,33 +758,24 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
     ICK(cudaGetLastError());
     F.W[u] = W;
   }
-  // chunked order for the pipelined solves: one chunk of rows per SM, its
-  // values in shared memory (at most CHUNK_SMEM bytes)
+  // chunked order for the pipelined solves: contiguous row chunks, one block
+  // each, all resident at once
   {
-    const size_t CHUNK_SMEM = 224 * 1024;
-    const int CH = (n + c.sms - 1) / c.sms;
-    // a chunk too large for shared memory reads its own values back through
-    // L2 (they are final once their group's block barrier has passed)
-    F.csmem = sizeof(double) * (size_t)CH <= CHUNK_SMEM;
-    const size_t csm = F.csmem ? sizeof(double) * (size_t)CH : 0;
+    int nch = c.sms;
+    if (const char* m = getenv("MSSTAB_ILU_NCH")) nch = std::max(1, atoi(m));
+    const int CH = std::max(1, (n + nch - 1) / nch);
+    const int P = (n + CH - 1) / CH;
     bool ok = F.W[0] > 0 || F.W[1] > 0;
     for (int W : {4, 8}) {
       if (!ok) break;
-      const void* k = W == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
       int nbk = 0;
-      // the attribute is the kernel's (every handle of the process shares it):
-      // always the largest chunk size, so that no handle's launches exceed it
-      if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)CHUNK_SMEM) != cudaSuccess ||
-          cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, csm) != cudaSuccess) {
-        cudaGetLastError();   // not this GPU's shape: the level-by-level sweeps serve
+      if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+              &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, 0) != cudaSuccess) {
+        cudaGetLastError();
         ok = false;
         break;
       }
-      // one wave: every chunk's block resident at once (several chunks per
-      // block in turn, with the chunks in shared memory, measured 1.36x slower
-      // than the level sweeps at 256^3)
-      if ((int64_t)nbk * c.sms < (n + CH - 1) / CH) ok = false;
+      if ((int64_t)nbk * c.sms < P) ok = false;   // one wave: every chunk's block resident
     }
     if (ok) {
       F.scratch = (double*)alloc(actx, sizeof(double) * (size_t)n);
@@ -780,7 +784,6 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
         return R;
       }
     }
-    const int P = (n + CH - 1) / CH;
     for (int u = 0; ok && u < 2; ++u) {
       F.CH[u] = 0;
       if (F.W[u] == 0) continue;
@@ -789,7 +792,8 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
       int* gcount = (int*)alloc(actx, sizeof(int) * (size_t)(P + 1));
       F.gofs[u] = (int*)alloc(actx, sizeof(int) * (size_t)(P + 1));
       int* key = (int*)alloc(actx, sizeof(int) * (size_t)n);
-      if (!lo || !hi || !gcount || !F.gofs[u] || !key) {
+      int* posof = (int*)alloc(actx, sizeof(int) * (size_t)n);
+      if (!lo || !hi || !gcount || !F.gofs[u] || !key || !posof) {
         R.code = 4;
         return R;
       }
@@ -818,7 +822,8 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
       ilu_level_scan_kernel<<<1, 1024, 0, c.stream>>>(TG, cnt, F.gptr[u], scratch + 2);
       ICK(cudaMemcpyAsync(cnt, F.gptr[u], sizeof(int) * (size_t)TG, cudaMemcpyDeviceToDevice, c.stream));
       ilu_level_scatter_kernel<<<g, NT, 0, c.stream>>>(n, key, cnt, F.cprow[u]);
-      ilu_chunk_pack_kernel<<<g, NT, 0, c.stream>>>(n, CH, u, F.csmem ? 1 : 0, F.cprow[u], F.row_ptr, F.col,
+      ilu_chunk_posof_kernel<<<g, NT, 0, c.stream>>>(n, F.cprow[u], posof);
+      ilu_chunk_pack_kernel<<<g, NT, 0, c.stream>>>(n, CH, u, F.cprow[u], key, posof, F.gptr[u], F.row_ptr, F.col,
                                                     F.diag, F.lu, F.cpcnt[u], F.cpcol[u], F.cpval[u], F.cpdiag);
       ICK(cudaGetLastError());
       F.CH[u] = CH;

@@ -178,7 +178,6 @@ struct IluDesc {
   // [gofs[b], gofs[b+1]), group q holds positions [gptr[q], gptr[q+1]);
   // dependencies inside the chunk are stored as ~(j - first row of the chunk)
   int CH[2] = {0, 0};
-  bool csmem = true;              // chunk values also in shared memory (else read back through L2)
   int groups[2] = {0, 0};
   int* gofs[2] = {nullptr, nullptr};
   int* gptr[2] = {nullptr, nullptr};
