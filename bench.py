@@ -43,7 +43,7 @@ FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 # (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md, ..._fp32inner_...).
 NCU_TRAFFIC = {("convdiff3d_128", "fp64", "spmv_dot"): 342_305_280,
                ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_367_872,
-               ("convdiff3d_128", "ilu0", "precond"): 133_597_440}
+               ("convdiff3d_128", "ilu0", "precond"): 161_049_344}
 
 
 def parse_args(argv=None):
