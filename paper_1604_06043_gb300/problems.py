@@ -136,6 +136,18 @@ def tridiag(n: int, sub: float, diag: float, sup: float) -> CSR:
     return _from_stencil(cols, vals, mask)
 
 
+def offset_coupled(n: int, offset: int, sub: float, diag: float, sup: float) -> CSR:
+    """Row i: sub in column i - offset, diag on the diagonal, sup in column
+    i + offset (where those exist).  The rows split into runs of `offset`
+    mutually independent rows, each coupled only to the runs beside it."""
+    idx = np.arange(n, dtype=np.int64)
+    cols = np.stack([idx - offset, idx, idx + offset], axis=1)
+    vals = np.tile(np.array([sub, diag, sup], dtype=np.float64), (n, 1))
+    mask = (cols >= 0) & (cols < n)
+    cols = np.where(mask, cols, 0)
+    return _from_stencil(cols, vals, mask)
+
+
 def random_sparse(n: int, per_row: int, seed: int, band: Optional[int] = None) -> CSR:
     """A random sparse matrix with a general (non-stencil) pattern: each row
     holds its diagonal and up to per_row distinct off-diagonal columns drawn

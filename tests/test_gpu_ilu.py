@@ -152,6 +152,30 @@ def test_triangular_solves_and_operator(M, name):
     S.close()
 
 
+def test_large_level_groups_in_a_chunk(M):
+    """Runs of 1400 independent rows coupled to the runs beside them: with one
+    row chunk per SM (about 3000 rows) a chunk's level holds more rows than the
+    1024 values the sweep keeps in shared memory and than the 512 threads of a
+    block, so that dependencies beyond the buffer come from the global vector
+    and threads take several positions of one level; chunk borders fall inside
+    levels."""
+    A = pb.offset_coupled(152 * 3000, 1400, -1.0, 4.0, -1.5)
+    F = I.Factors.from_values(A, I.ilu0(A))
+    S = _solver(M, A, s=2)
+    lev = S.op_ilu_levels()
+    assert lev[0] == lev[1] == -(-A.n // 1400) and lev[2] == lev[3] == 1400   # the runs are the levels
+    z = np.random.default_rng(8).standard_normal(A.n)
+    zt = _t(z)
+    y = torch.empty_like(zt)
+    for which, low in ((0, True), (1, False)):
+        S.op_ilu_apply(which, zt, y)
+        ref = F.lower_solve(z) if low else F.upper_solve(z)
+        sc = I.comparison_scale(F, ref, lower=low)
+        err = np.abs(y.cpu().numpy() - ref)
+        assert np.all(err <= 1e-12 * sc), (which, float((err / sc).max()))
+    S.close()
+
+
 def test_exact_factor_gives_the_identity(M):
     A = MATRICES["tridiag_40"]()
     S = _solver(M, A, s=2)

@@ -108,3 +108,15 @@ def test_random_sparse_pattern():
     B = pb.random_sparse(300, 6, seed=9)
     C = pb.random_sparse(300, 6, seed=9)
     assert np.array_equal(B.col, C.col) and np.array_equal(B.val, C.val)
+
+
+def test_offset_coupled_pattern():
+    A = pb.offset_coupled(50, 7, -1.0, 4.0, -1.5)
+    D = A.to_scipy().toarray()
+    i = np.arange(50)
+    ref = 4.0 * np.eye(50) - np.eye(50, k=-7) - 1.5 * np.eye(50, k=7)
+    assert np.array_equal(D, ref)
+    for r in range(A.n):
+        c = A.col[A.row_ptr[r]:A.row_ptr[r + 1]]
+        assert np.all(np.diff(c) > 0) and r in c
+    assert A.nnz == 50 + 2 * (50 - 7) and i.size == 50
