@@ -273,33 +273,39 @@ __global__ void ilu_pad_counts_kernel(int nlev, const int* lptr, int* cnt) {
 // Pipelined solves over row chunks.  Rows are cut into contiguous chunks, one
 // per block (one block per SM).  Inside a chunk the rows are grouped by their
 // level (the same levels as the level-by-level sweep); the block runs its
-// groups in level order with a block barrier between them, holding the
-// chunk's solution values in shared memory.  Keeping the global level order
-// inside every chunk is what makes the pipeline short: a row of level l needs
-// values of levels below l only, which the neighbouring chunk produces early
-// in its own order (ordering a chunk by levels counted inside the chunk alone
-// made a chunk wait for the end of its neighbour: 30x slower).  A dependency in
-// another chunk (an earlier one for the lower solve, a later one for the
-// upper) is read from the global solution vector, which starts filled with a
-// sentinel bit pattern (all ones: a NaN no arithmetic produces; the GPU's NaN
-// results are the positive canonical one), polled with relaxed loads until
-// the owning block has written it.  The chunks thus run as a pipeline, each a
-// little behind the chunk it depends on, and no grid-wide barrier is needed.
-// A chunk waits only on chunks on one side of it, the first chunk on that
-// side waits on none, and a cooperative launch keeps every block resident, so
-// the sweep completes; every wait is bounded (BAR_SPIN_LIMIT polls, then
-// FLAG_SYNC_TIMEOUT and NaN), and a thread that sees the flag stops waiting.
-// Lanes of a warp wait only on other blocks, never on each other.
-// A chunk too large for shared memory (more than 28k rows) reads its own
-// values back through L2 like the others: they are final once the block
-// barrier after their group has passed (2.1 ms per triangle at 256^3, against
-// 3.4 ms level by level).
+// groups in level order with a block barrier between them.  Keeping the
+// global level order inside every chunk is what makes the pipeline short: a
+// row of level l needs values of levels below l only, which the neighbouring
+// chunk produces early in its own order (ordering a chunk by levels counted
+// inside the chunk alone made a chunk wait for the end of its neighbour: 30x
+// slower).
+// Values.  The block keeps the values of the group just solved and of the one
+// being solved in a shared-memory double buffer (GMAX each); a dependency in
+// the previous group of the same chunk is packed as its offset there.  Every
+// other dependency -- in another chunk (an earlier one for the lower solve, a
+// later one for the upper) or in an older group of the same chunk -- is read
+// from the global solution vector, which starts filled with a sentinel bit
+// pattern (all ones: a NaN no arithmetic produces; the GPU's NaN results are
+// the positive canonical one) and is polled with relaxed loads until the
+// owning block has written it; values of the block's own older groups are
+// final there once the barrier after their group has passed.  In natural
+// order every dependency of a stencil row is exactly one level below it, so
+// nearly all in-chunk dependencies come from the buffer, and the chunk size
+// does not depend on shared memory.
+// Termination.  A chunk waits only on chunks on one side of it, the first
+// chunk on that side waits on none, and a cooperative launch keeps every block
+// resident, so the sweep completes; every wait is bounded (BAR_SPIN_LIMIT
+// polls, then FLAG_SYNC_TIMEOUT and NaN), and a thread that sees the flag
+// stops waiting.  Rows of one group never depend on each other, so lanes of a
+// warp wait only on other blocks.
 // What bounds it: a chunk is smaller than a grid plane, so nearly every row
 // needs a value the neighbouring chunk produced one level earlier; the chunks
-// settle into a lockstep of one store-to-load trip per level (2.3 us at
-// 128^3: 0.87 ms per triangle, against 1.38 ms for the level-by-level sweep).
-// Loading the next group's data early (1.5 % slower) or chunks of twice the
-// rows on half the SMs (24 % slower) did not help.
+// settle into a lockstep of one store-to-load trip per level (1.9 us at
+// 128^3: 0.72 ms per triangle, against 1.38 ms for the level-by-level sweep).
+// Each position loads all of its dependency slots whatever its count, so that
+// no load waits for the count.  Loading a thread's first position of the next
+// group during the current one (869 against 731 us) or chunks of twice the
+// rows on half the SMs (836 against 801 us) did not help.
 // ---------------------------------------------------------------------------
 constexpr int CTS = 512;                       // threads per block of the chunked sweeps
 constexpr unsigned long long SENTINEL = 0xFFFFFFFFFFFFFFFFull;
