@@ -174,9 +174,10 @@ struct IluDesc {
   double* pdiag[2] = {nullptr, nullptr};
   int* pptr[2] = {nullptr, nullptr};   // padded positions of level l: [pptr[l], pptr[l+1])
   // chunked order of the pipelined solves (CH[u] > 0): rows cut into chunks of
-  // CH rows, one per block; chunk b's local levels are the groups
-  // [gofs[b], gofs[b+1]), group q holds positions [gptr[q], gptr[q+1]);
-  // dependencies inside the chunk are stored as ~(j - first row of the chunk)
+  // CH rows, one per block; chunk b's levels are the groups [gofs[b],
+  // gofs[b+1]), group q holds positions [gptr[q], gptr[q+1]); a dependency in
+  // the previous group of the same chunk (within its first 1024 positions) is
+  // stored as -1 - its offset in that group, any other as its row
   int CH[2] = {0, 0};
   int groups[2] = {0, 0};
   int* gofs[2] = {nullptr, nullptr};
