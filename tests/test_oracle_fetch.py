@@ -10,7 +10,9 @@ applied while the solve runs pick exactly these cycles, and the data fetched by
 the running test is the data of a fixed fetch at that cycle, bit for bit.
 """
 
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -26,7 +28,26 @@ def _P(s):
     return O.orthonormalize_mgs2(pb.randn_cols(40, s, pb.SEED_P))
 
 
-PAPER_POINTS = [(2, 1, 19), (4, 1, 9), (4, 2, 4)]
+FT = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                 "paper_finite_termination.json")))
+
+
+def _paper_points():
+    """(s, l, fetching cycle) of the paper's fetches: IDR(2)stab(1) after 60 MVs
+    (G_19), IDR(4)stab(1) from G_9 (the l = 1 figure; its data A from G_8 is the
+    same run fetched one cycle earlier) and IDR(4)stab(2) from G_8 (data B)."""
+    f = FT["fetch_after_mvs"]
+    pts = [(f["s"], f["ell"], f["G"] // f["ell"])]
+    for m in FT["msstab"]:
+        for d in m["data"]:
+            if d.get("name") == "A":
+                continue
+            pts.append((m["s"], d["ell"], d["G"] // d["ell"]))
+    return sorted(set(pts))
+
+
+PAPER_POINTS = _paper_points()
+assert PAPER_POINTS == [(2, 1, 19), (4, 1, 9), (4, 2, 4)]
 
 
 @pytest.mark.parametrize("s,ell,cycle", PAPER_POINTS)

@@ -7,7 +7,9 @@ of Sonneveld and M-spaces.  The mutation tests at the end plant plausible
 mistakes into the oracle and check that these pins catch them.
 """
 
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -109,11 +111,15 @@ def test_arnoldi_start_is_krylov_basis():
 
 
 # ---------------------------------------------------------------------------
-# Section 5.2: finite termination on A = tridiag(2, 3, 1), N = 40
+# Section 5.2: finite termination on A = tridiag(2, 3, 1), N = 40; the paper's
+# printed values are in tests/golden/paper_finite_termination.json
 # ---------------------------------------------------------------------------
 
-TRI = pb.tridiag(40, 2.0, 3.0, 1.0)
-B1, B2 = pb.termination_rhs(40)
+FT = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                                 "paper_finite_termination.json")))
+_MT = FT["matrix"]
+TRI = pb.tridiag(_MT["N"], _MT["sub"], _MT["diag"], _MT["sup"])
+B1, B2 = pb.termination_rhs(_MT["N"])
 
 
 def _P(s):
@@ -127,13 +133,29 @@ def _first_cycle_below(hist, thr):
     return None
 
 
+def test_fixture_values_follow_the_printed_bounds():
+    """The fixture's numbers are those of the paper's dimension bounds."""
+    N = _MT["N"]
+    for g in FT["idrstab"]:
+        assert N - (g["last_nonzero_G"] + 1) * g["s"] <= 0 < N - g["last_nonzero_G"] * g["s"]
+    for m in FT["msstab"]:
+        s, G = m["s"], m["data"][0]["G"]
+        assert all(d["G"] == G for d in m["data"])
+        assert m["dim_G"] == N - G * s and m["dim_M"] == m["dim_G"] + G
+        last = m["last_nonzero_M"]
+        assert m["dim_M"] - (last - G) * s > 0 >= m["dim_M"] - (last + 1 - G) * s
+    f = FT["fetch_after_mvs"]
+    assert f["mvs"] == 1 + f["s"] + f["G"] * f["ell"] * (f["s"] + 1)     # r0 + Arnoldi + G cycles (c3)
+
+
 def test_termination_rhs_orthogonal():
-    assert abs(B1 @ B2) < 1e-12
+    assert FT["rhs"]["orthogonal"] and abs(B1 @ B2) < 1e-12
 
 
-@pytest.mark.parametrize("s,ell,level", [(2, 1, 20), (4, 1, 10), (4, 2, 10)])
-def test_idrstab_terminates_when_sonneveld_space_vanishes(s, ell, level):
-    # dim G_j <= N - j s (canonical case): G_j = {0} from j = N/s on
+@pytest.mark.parametrize("g", FT["idrstab"], ids=lambda g: f"s{g['s']}l{g['ell']}")
+def test_idrstab_terminates_when_sonneveld_space_vanishes(g):
+    # G_j = {0} from the level after the last non-zero one on
+    s, ell, level = g["s"], g["ell"], g["last_nonzero_G"] + 1
     res = O.idrstab(TRI, B1, np.zeros(40), s, ell, _P(s), tol=1e-13, max_mvs=2000)
     c = _first_cycle_below(res.history, 1e-10)
     assert c is not None and c * ell <= level + ell      # one extra cycle for rounding
@@ -142,9 +164,11 @@ def test_idrstab_terminates_when_sonneveld_space_vanishes(s, ell, level):
 
 def test_fetch_after_60_mvs_is_level_19():
     # 1 (r0) + 2 (Arnoldi) + 19 cycles x 3 MVs = 60 MVs <=> range(V) in G_19
-    res = O.idrstab(TRI, B1, np.zeros(40), 2, 1, _P(2), tol=1e-14, max_mvs=2000, fetch_cycle=19)
-    assert res.fetch_cycle == 19
-    assert res.mv_history[19] == 60
+    f = FT["fetch_after_mvs"]
+    res = O.idrstab(TRI, B1, np.zeros(40), f["s"], f["ell"], _P(f["s"]), tol=1e-14, max_mvs=2000,
+                    fetch_cycle=f["G"] // f["ell"])
+    assert res.fetch_cycle == f["G"]
+    assert res.mv_history[f["G"]] == f["mvs"]
 
 
 def _m_solve(s, ell_src, fetch_cycle, ell):
@@ -155,33 +179,20 @@ def _m_solve(s, ell_src, fetch_cycle, ell):
     return O.idrstab(TRI, B2, np.zeros(40), s, ell, P, U, V, tol=1e-13, max_mvs=2000)
 
 
-def test_m2stab1_terminates_after_m29():
-    # dim M_19 <= 2 + 19; minus 2 per level: M_29 is the last non-zero space
-    res = _m_solve(2, 1, 19, 1)
+M_CASES = [(m, d, ell) for m in FT["msstab"] for d in m["data"] for ell in m["ell"]]
+
+
+@pytest.mark.parametrize("m,d,ell", M_CASES,
+                         ids=[f"s{m['s']}_G{d['G']}_src_l{d['ell']}_l{ell}" for m, d, ell in M_CASES])
+def test_msstab_terminates_after_the_last_nonzero_m_space(m, d, ell):
+    # the M-space levels continue from the fetch level G; the residual is zero
+    # once a residual of the level after the last non-zero M-space is computed
+    s, G, last = m["s"], d["G"], m["last_nonzero_M"]
+    res = _m_solve(s, d["ell"], G // d["ell"], ell)
+    cz = -(-(last + 1 - G) // ell)             # cycles to reach level last + 1
     c = _first_cycle_below(res.history, 1e-10)
-    assert c is not None and 11 <= c <= 12
-    assert res.history[9] > 1e-8
-
-
-def test_m4stab1_terminates_after_m12():
-    # data from G_9: dim M_9 <= 4 + 9 = 13; minus 4 per level: M_12 last non-zero
-    res = _m_solve(4, 1, 9, 1)
-    c = _first_cycle_below(res.history, 1e-10)
-    assert c is not None and 4 <= c <= 5
-    assert res.history[2] > 1e-6
-
-
-@pytest.mark.parametrize("ell_src,fetch_cycle", [(1, 8), (2, 4)])   # data A, data B
-@pytest.mark.parametrize("ell", [1, 2])
-def test_m4stab_data_ab_drops_after_m11(ell_src, fetch_cycle, ell):
-    # data from G_8 of IDR(4)stab(1) (A) or IDR(4)stab(2) (B): dim M_8 <= 16,
-    # minus 4 per level, so M_11 is the last non-zero space, whatever l
-    res = _m_solve(4, ell_src, fetch_cycle, ell)
-    c12 = (12 - 8) // ell            # the M-space levels continue from level 8
-    assert res.history[c12] < 1e-8
-    assert res.history[c12 - 1] > 1e-6
-    c = _first_cycle_below(res.history, 1e-10)
-    assert c is not None and c <= c12 + 1
+    assert c is not None and cz <= c <= cz + 1  # one extra cycle for rounding
+    assert res.history[cz - 1] > 1e-8           # not a cycle earlier
 
 
 # ---------------------------------------------------------------------------
@@ -416,8 +427,9 @@ def test_planted_mistakes_are_caught(monkeypatch, name, fn):
         test_invariants_hold_every_cycle(2, 2)
     except AssertionError:
         caught = True
+    m = next(m for m in FT["msstab"] if m["s"] == 4 and m["data"][0]["G"] == 9)   # M(4)stab(1), data from G_9
     try:
-        test_m4stab1_terminates_after_m12()
+        test_msstab_terminates_after_the_last_nonzero_m_space(m, m["data"][0], 1)
     except AssertionError:
         caught = True
     assert caught
