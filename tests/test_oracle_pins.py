@@ -148,6 +148,17 @@ def test_fixture_values_follow_the_printed_bounds():
     assert f["mvs"] == 1 + f["s"] + f["G"] * f["ell"] * (f["s"] + 1)     # r0 + Arnoldi + G cycles (c3)
 
 
+def test_table1_reduced_dimensions_agree_with_the_m_space_bounds():
+    """Table 1's count of reduced dimensions, j s + J (s - 1) after j level
+    steps from data of G_J, reaches N at the level after the last non-zero
+    M-space of Section 5.2 (two statements of the paper, one termination)."""
+    N = _MT["N"]
+    for m in FT["msstab"]:
+        s, G = m["s"], m["data"][0]["G"]
+        j = next(j for j in range(1, N + 1) if j * s + G * (s - 1) >= N)
+        assert G + j == m["last_nonzero_M"] + 1
+
+
 def test_termination_rhs_orthogonal():
     assert FT["rhs"]["orthogonal"] and abs(B1 @ B2) < 1e-12
 
