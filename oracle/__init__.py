@@ -19,7 +19,8 @@ ilu       ILU(0) split preconditioning (Section 5.1): the factor by its
           solves, the preconditioned operator and the preconditioned sequence.
 
 Parity pins (see tests/test_oracle_*.py): dense LU on tiny systems, BiCGStab
-equivalence for s = l = 1, the finite-termination levels of Section 5.2, the
+equivalence for s = l = 1, the finite-termination levels of Section 5.2 (the
+printed values in tests/golden/paper_finite_termination.json), the
 invariants V = AU, P^T r^(i) = 0, Z^T r = 0, true = recursive residual, the MV
 counts of Table 1, and for the CNN central finite differences, scipy's
 correlate, tabulated normal-CDF values and the closed form of the first Adam
