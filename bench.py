@@ -53,10 +53,12 @@ def parse_args(argv=None):
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=["native", "reference"], default="native")
     p.add_argument("--workload", default=WORKLOAD)
-    p.add_argument("--form", choices=["fp64", "fp32_inner", "idrstab", "ilu0"], default="fp64",
+    p.add_argument("--form", choices=["fp64", "fp32_inner", "fp32_inner_recycled", "idrstab", "ilu0"],
+                   default="fp64",
                    help="the solver form of the main line: FP64 M(s)stab (default), the FP32-inner "
                         "defect-correction form, or FP64 IDR(s)stab with an Arnoldi start per system")
     p.add_argument("--no-variants", action="store_true", help="skip the IDRstab and FP32-inner runs")
+    p.add_argument("--variants", default="", help="comma-separated subset of the variants (default: all)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--cnn", action="store_true",
@@ -206,11 +208,18 @@ def golden_cycles(first, count, workload="convdiff3d_128"):
 
 
 def FP32_INNER_OPTS(M):
-    """The FP32-inner form as measured: inner M(s)stab(1) (FP32 level vectors
-    drift for l > 1 on these systems), a fresh Arnoldi start per inner solve
-    with the basis continued across defect-correction steps, inner tolerance
-    1e-2 (the library default)."""
+    """The FP32-inner form without recycling: inner IDR(s)stab(1) (FP32 level
+    vectors drift for l > 1 on these systems), an Arnoldi start for the first
+    inner solve of every system, the basis continued across its
+    defect-correction steps, inner tolerance 1e-2 (the library default)."""
     return dict(precision=M.PREC_FP32_INNER, inner_ell=1, fetch_policy=M.FETCH_NEVER, max_outer=40)
+
+
+def FP32_INNER_RECYCLED_OPTS(M):
+    """The FP32-inner form as M(s)stab: the same inner M(s)stab(1), with U, V
+    fetched once (first system, relative inner residual <= sqrt(inner tol))
+    and passed to the first inner solve of every later system."""
+    return dict(precision=M.PREC_FP32_INNER, inner_ell=1, fetch_policy=M.FETCH_ONCE, max_outer=40)
 
 
 def s_ell_cols(w):
@@ -226,7 +235,10 @@ def workload_config(w, n, nnz, W, K, form, world):
     return {"workload": f"{w.name}: 3D {kind}, 7-point FD on a {dims} grid (N={n}, nnz={nnz}), "
                         f"beta={tuple(w.beta)}, implicit Euler tau={w.tau}, systems {W + 1}..{W + K} of the sequence",
             "method": {"fp64": f"M({w.s})stab({w.ell}), fetch once at sqrt(tol), FP64, SELL-32",
-                       "fp32_inner": f"FP32-inner M({w.s})stab(1) with FP64 defect correction, SELL-32",
+                       "fp32_inner": f"FP32-inner IDR({w.s})stab(1) (no recycling) with FP64 defect correction, "
+                                     f"SELL-32",
+                       "fp32_inner_recycled": f"FP32-inner M({w.s})stab(1), fetch once, with FP64 defect "
+                                              f"correction, SELL-32",
                        "idrstab": f"IDR({w.s})stab({w.ell}), Arnoldi start per system, FP64, SELL-32",
                        "ilu0": f"M({w.s})stab({w.ell}) on L^-1 A U^-1 (ILU(0) split preconditioner), fetch once "
                                f"at sqrt(tol), FP64, SELL-32"}[form],
@@ -351,13 +363,17 @@ def reference_arm(args):
 # the GPU arm
 # ---------------------------------------------------------------------------
 
-def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300, batch=8, lr=2e-3):
-    """The learned initial guess: the plain FP64 solver produces the pairs of
-    systems 1..train_steps, the CNN is trained on them with the library's own
-    kernels, and systems train_steps+1..train_steps+K are solved (a) with the
-    guess under the keep-if-smaller-residual rule, (b) with the optimally
-    scaled guess, (c) as (a) on the FP32-inner solver, each against the plain
-    solver on the same systems."""
+def learned_guess_variants(M, torch, A, w, dev, f, train_steps=20, apply_steps=80, iters=300, batch=8, lr=2e-3):
+    """The learned initial guess on the 100-step sequence: the plain FP64
+    solver produces the pairs of systems 1..train_steps, the CNN is trained on
+    them with the library's own kernels, and systems train_steps+1 ..
+    train_steps+apply_steps are solved from the same state with x0 from
+    (plain) x^(i); (rule) x^(i) + network correction, kept only if its
+    residual is smaller, else x^(i); (extrap) the residual-minimising point of
+    x^(i) + span{x^(i) - x^(i-1)}; (net) of x^(i) + span{network correction};
+    (net_extrap) of x^(i) + span{both}; FP64 and FP32-inner solvers.  Products
+    with A count the selection's (r0 for the network, 1 + m for the span, 2 for
+    the rule)."""
     from paper_1604_06043_gb300 import problems as pb
     import numpy as np
     S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
@@ -366,92 +382,102 @@ def learned_guess_variants(M, torch, A, w, K, dev, f, train_steps=20, iters=300,
     r0 = torch.empty_like(x)
     nrm = torch.zeros(2, dtype=torch.float64, device=dev)
     D = min(32, w.shape[0])
-    nets = {}
-    for loss in ("mse", "operator"):
-        nets[loss] = M.CNN(w.shape, pb.cnn_init_params(), max_pairs=train_steps, max_batch=batch, crop=D, device=dev)
-    # the operator-weighted loss uses the 7-point row of A at the grid centre
-    Kst = pb.row_stencil(A, w.shape, tuple(n // 2 for n in w.shape))
-    nets["operator"].set_loss_stencil(Kst / np.abs(Kst).max())
+    net = M.CNN(w.shape, pb.cnn_init_params(), max_pairs=train_steps, max_batch=batch, crop=D, device=dev)
     for _ in range(train_steps):
         S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
         xp = x.clone()
         S.op_residual(b, x, r0, nrm)
         S.solve(b, x, w.tol)
-        for net_ in nets.values():
-            net_.add_pair(r0, xp, x)
-    train = {}
-    for name_, net_ in nets.items():
-        net_.fit_scales()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        hist = net_.train(pb.cnn_crop_batches(train_steps, w.shape, D, batch, iters), batch, D, lr)
-        torch.cuda.synchronize()
-        train[name_] = {"seconds": round(time.perf_counter() - t0, 3), "loss_first": float(np.mean(hist[:5])),
-                        "loss_last": float(np.mean(hist[-20:]))}
+        net.add_pair(r0, xp, x)
     S.close()
-    out = {"train": {"pairs": train_steps, "iters": iters, "batch": batch, "crop": D, "losses": train},
-           "systems": f"{train_steps + 1}..{train_steps + K}"}
-    net = nets["mse"]
+    net.fit_scales()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = net.train(pb.cnn_crop_batches(train_steps, w.shape, D, batch, iters), batch, D, lr)
+    torch.cuda.synchronize()
+    out = {"train": {"pairs": train_steps, "iters": iters, "batch": batch, "crop": D, "loss": "mse",
+                     "seconds": round(time.perf_counter() - t0, 3), "loss_first": float(np.mean(hist[:5])),
+                     "loss_last": float(np.mean(hist[-20:]))},
+           "systems": f"{train_steps + 1}..{train_steps + apply_steps}"}
 
     def run(precision, mode):
         opts = FP32_INNER_OPTS(M) if precision == M.PREC_FP32_INNER else {}
         V = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every, **opts)
         xs = torch.tensor(w.x0(), device=dev)
+        xprev = torch.empty_like(xs)
         for _ in range(train_steps):             # the same history (and recycle store) as the plain run
+            xprev.copy_(xs)
             V.op_axpby(1.0 / w.tau, xs, 1.0, f, b)
             V.solve(b, xs, w.tol, check=False)
         xg = torch.empty_like(xs)
-        delta = torch.empty_like(xs)
-        mv, used, red, fails = [], 0, [], 0
+        dirs = torch.empty((2, A.n), dtype=torch.float64, device=dev)
+        mv, used, red, fails, worst = [], 0, [], 0, 0.0
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         e0.record()
-        for _ in range(K):
+        for _ in range(apply_steps):
             V.op_axpby(1.0 / w.tau, xs, 1.0, f, b)
             extra = 0
-            if mode != "plain":
+            if mode == "rule":
                 V.op_residual(b, xs, r0, nrm)
-                (nets["operator"] if mode.endswith("_op") else net).infer(r0, xs, delta)
-                if mode.startswith("rule"):
-                    u = V.select_guess(b, xs, delta, xg)
-                else:
-                    u, a, rr = V.select_guess_scaled(b, xs, delta, xg)
-                    red.append(rr)
-                used += int(u)
-                xs.copy_(xg)
+                net.infer(r0, xs, dirs[0])
+                u = V.select_guess(b, xs, dirs[0], xg)
                 extra = 3
+            elif mode != "plain":
+                m = 0
+                if mode in ("net", "net_extrap"):
+                    V.op_residual(b, xs, r0, nrm)
+                    net.infer(r0, xs, dirs[m])
+                    m += 1
+                    extra += 1
+                if mode in ("extrap", "net_extrap"):
+                    torch.sub(xs, xprev, out=dirs[m])
+                    m += 1
+                u, a, rr = V.select_guess_span(b, xs, dirs[:m], xg)
+                red.append(rr)
+                extra += 1 + m
+            if mode != "plain":
+                used += int(u)
+                xprev.copy_(xs)
+                xs.copy_(xg)
+            else:
+                xprev.copy_(xs)
             st = V.solve(b, xs, w.tol, check=False)
             fails += int(st.status != 0)
+            worst = max(worst, st.relres_true)
             mv.append(st.mvs + extra)
         e1.record()
         torch.cuda.synchronize()
         V.close()
-        d = {"ms_per_system": round(e0.elapsed_time(e1) / K, 3), "mvs_per_system": round(float(np.mean(mv)), 2),
-             "failed_solves": fails}
+        d = {"ms_per_system": round(e0.elapsed_time(e1) / apply_steps, 3),
+             "mvs_per_system": round(float(np.mean(mv)), 2), "failed_solves": fails, "relres_true_max": worst}
         if mode != "plain":
             d["guess_kept"] = used
-            d["fallback_rate"] = round(1.0 - used / K, 3)
+            d["fallback_rate"] = round(1.0 - used / apply_steps, 3)
         if red:
-            d["residual_reduction_mean"] = round(float(np.mean(red)), 4)
+            d["start_residual_ratio_mean"] = round(float(np.mean(red)), 4)
         return d
 
-    plain = run(M.PREC_FP64, "plain")
-    out["fp64_plain"] = plain
-    out["fp64_guess_rule"] = run(M.PREC_FP64, "rule")
-    out["fp64_guess_scaled"] = run(M.PREC_FP64, "scaled")
-    out["fp64_guess_rule_op"] = run(M.PREC_FP64, "rule_op")
-    out["fp64_guess_scaled_op"] = run(M.PREC_FP64, "scaled_op")
-    out["fp32_inner_plain"] = run(M.PREC_FP32_INNER, "plain")
-    out["fp32_inner_guess_rule"] = run(M.PREC_FP32_INNER, "rule")
-    out["fp32_inner_guess_rule_op"] = run(M.PREC_FP32_INNER, "rule_op")
-    for k in list(out):
-        if k.startswith("fp64_guess"):
-            out[k]["mvs_saved_per_system"] = round(plain["mvs_per_system"] - out[k]["mvs_per_system"], 2)
-        if k.startswith("fp32_inner_guess"):
-            out[k]["mvs_saved_per_system"] = round(out["fp32_inner_plain"]["mvs_per_system"] - out[k]["mvs_per_system"], 2)
-    for net_ in nets.values():
-        net_.close()
+    for prec, tag, modes in ((M.PREC_FP64, "fp64", ("plain", "rule", "extrap", "net", "net_extrap")),
+                             (M.PREC_FP32_INNER, "fp32_inner", ("plain", "extrap", "net_extrap"))):
+        base = None
+        for mode in modes:
+            d = run(prec, mode)
+            if mode == "plain":
+                base = d
+            else:
+                d["mvs_saved_per_system"] = round(base["mvs_per_system"] - d["mvs_per_system"], 2)
+                d["ms_saved_per_system"] = round(base["ms_per_system"] - d["ms_per_system"], 3)
+            out[f"{tag}_{mode}"] = d
+    # what the trained network gains over the method without it (the same
+    # selection with and without the network's direction)
+    out["network_gain_mvs_per_system"] = {
+        "fp64_over_plain": out["fp64_net"]["mvs_saved_per_system"],
+        "fp64_over_extrapolation": round(out["fp64_extrap"]["mvs_per_system"] - out["fp64_net_extrap"]["mvs_per_system"], 2),
+        "fp32_inner_over_extrapolation": round(out["fp32_inner_extrap"]["mvs_per_system"]
+                                               - out["fp32_inner_net_extrap"]["mvs_per_system"], 2)}
+    net.close()
     return out
 
 
@@ -579,8 +605,8 @@ def main(argv=None):
     f_np, x0_np = w.f(), w.x0()
     K, W = args.steps, args.warmup
 
-    form_opts = {"fp64": {}, "fp32_inner": FP32_INNER_OPTS(M), "idrstab": dict(fetch_policy=M.FETCH_NEVER),
-                 "ilu0": dict(precond=M.PRECOND_ILU0)}[args.form]
+    form_opts = {"fp64": {}, "fp32_inner": FP32_INNER_OPTS(M), "fp32_inner_recycled": FP32_INNER_RECYCLED_OPTS(M),
+                 "idrstab": dict(fetch_policy=M.FETCH_NEVER), "ilu0": dict(precond=M.PRECOND_ILU0)}[args.form]
     # the timed run replays each cycle as a CUDA graph; per-launch event
     # timing (which launches one by one) runs in a second pass over the same
     # systems for the per-kernel roofline
@@ -635,7 +661,7 @@ def main(argv=None):
     fam_n = {f_: sum(t["n_launch"][f_] for t in ktimed) for f_ in FAMILIES}
     replaced = sum(t["cycles"] for t in ktimed) if w.replace_every == 1 else \
         sum(t["cycles"] // w.replace_every for t in ktimed) if w.replace_every > 1 else 0
-    if args.form == "fp32_inner":     # inner cycles of M(s)stab(1) on FP32 vectors dominate the launches
+    if args.form.startswith("fp32_inner"):     # inner cycles of degree 1 on FP32 vectors dominate the launches
         model, spmv_b = family_model(A, w.s, 1, cycles, K, 0, vb=4)
     else:
         model, spmv_b = family_model(A, w.s, w.ell, cycles, K, replaced)
@@ -682,7 +708,7 @@ def main(argv=None):
 
     line = {"metric": METRIC, "value": round(value, 4), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
             "ms_per_step": round(T / K, 4), "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
-            "dtype": "f32+f64" if args.form == "fp32_inner" else "f64",
+            "dtype": "f32+f64" if args.form.startswith("fp32_inner") else "f64",
             "data": "synthetic (seeded generators; the paper's ocean data is not available)",
             "config": workload_config(w, A.n, A.nnz, W, K, args.form, world),
             "mvs_per_system": round(statistics.mean(mvs), 2),
@@ -726,15 +752,21 @@ def main(argv=None):
         xs = torch.tensor(x0_np, device=dev)
         variants = {}
         p_block = pb.randn_block_partitioned(A.n, w.s, pb.SEED_P)
-        for name, opts, praw in (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER), None),
-                                 ("msstab_fp32_inner", FP32_INNER_OPTS(M), None),
-                                 ("msstab_fp64_block_p", {}, p_block),
-                                 ("msstab_fp32_inner_block_p", FP32_INNER_OPTS(M), p_block),
-                                 ("msstab_fp64_fetch_slope", dict(fetch_policy=M.FETCH_SLOPE), None),
-                                 ("msstab_fp64_fetch_probe", dict(fetch_policy=M.FETCH_PROBE), None),
-                                 ("msstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1), None),
-                                 ("idrstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1,
-                                                            fetch_policy=M.FETCH_NEVER), None)):
+        todo = (("idrstab_fp64", dict(fetch_policy=M.FETCH_NEVER), None),
+                ("fp32_inner_idrstab1_dc", FP32_INNER_OPTS(M), None),
+                ("msstab_fp32_inner_recycled", FP32_INNER_RECYCLED_OPTS(M), None),
+                ("msstab_fp64_fetch_every", dict(fetch_policy=M.FETCH_EVERY), None),
+                ("msstab_fp64_no_orth", dict(orth_recycle=0), None),
+                ("msstab_fp64_block_p", {}, p_block),
+                ("msstab_fp64_fetch_slope", dict(fetch_policy=M.FETCH_SLOPE), None),
+                ("msstab_fp64_fetch_probe", dict(fetch_policy=M.FETCH_PROBE), None),
+                ("msstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1), None),
+                ("idrstab_fp64_ilu0", dict(precond=M.PRECOND_ILU0, kernel_timing=1, fetch_policy=M.FETCH_NEVER),
+                 None))
+        only = set(args.variants.split(",")) if args.variants else None
+        for name, opts, praw in todo:
+          if only is not None and name not in only:
+              continue
           try:
             c0 = time.perf_counter()
             V = M.Solver(A, w.s, w.ell, w.p_raw() if praw is None else praw, device=dev,
@@ -748,7 +780,7 @@ def main(argv=None):
             xs_list = []
             v0.record(stream)
             tv = run_sequence(M, torch, V, f, xv, b, w.tau, w.tol, K,
-                              collect=xs_list if name == "msstab_fp32_inner" else None, check=False)
+                              collect=xs_list if "fp32_inner" in name else None, check=False)
             v1.record(stream)
             torch.cuda.synchronize()
             variants[name] = {"ms_per_system": round(v0.elapsed_time(v1) / K, 4),
@@ -759,8 +791,10 @@ def main(argv=None):
                 variants[name]["mvs_fp32_per_system"] = round(statistics.mean(t["mvs_fp32"] for t in tv), 2)
                 variants[name]["outer_per_system"] = round(statistics.mean(t["outer"] for t in tv), 2)
                 variants[name]["fp64_finishes"] = sum(t["fp64_finish"] for t in tv)
-            if name == "msstab_fp32_inner":
+            if "fp32_inner" in name:
                 variants[name]["_xs"] = xs_list
+            if "fetch_" in name or "no_orth" in name or name == "idrstab_fp64":
+                variants[name]["mvs_total"] = int(sum(t["mvs"] for t in tv))
             if praw is not None:
                 variants[name]["cut_space"] = "block-partitioned N(0,1), seed 3 (rows (i // 32) mod s)"
             if "ilu0" in name:
@@ -773,22 +807,28 @@ def main(argv=None):
             V.close()
           except Exception as e:  # a failing variant is reported, the main line still stands
             variants[name] = {"error": str(e)[-300:]}
-        # error of the FP32-inner solutions against the FP64 solutions of the same systems
-        P64 = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
-        x64 = torch.tensor(x0_np, device=dev)
-        run_sequence(M, torch, P64, f, x64, b, w.tau, w.tol, W)
-        errs = []
-        for xv32 in variants["msstab_fp32_inner"].pop("_xs", []):
-            P64.op_axpby(1.0 / w.tau, x64, 1.0, f, b)
-            P64.solve(b, x64, w.tol)
-            errs.append(float(torch.linalg.norm(xv32 - x64) / torch.linalg.norm(x64)))
-        P64.close()
-        if errs:
-            variants["msstab_fp32_inner"]["rel_err_vs_fp64_max"] = max(errs)
-        try:
-            variants["learned_guess"] = learned_guess_variants(M, torch, A, w, K, dev, f)
-        except Exception as e:
-            variants["learned_guess"] = {"error": str(e)[-300:]}
+        # error of the FP32-inner solutions against the FP64 solutions of the
+        # same systems (each FP32 sequence runs on its own solutions; the FP64
+        # reference is the main line's handle type from the same x^(0))
+        for name in [k for k in variants if "fp32_inner" in k and "_xs" in variants[k]]:
+            P64 = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
+            x64 = torch.tensor(x0_np, device=dev)
+            run_sequence(M, torch, P64, f, x64, b, w.tau, w.tol, W)
+            errs = []
+            for xv32 in variants[name].pop("_xs"):
+                P64.op_axpby(1.0 / w.tau, x64, 1.0, f, b)
+                P64.solve(b, x64, w.tol)
+                errs.append(float(torch.linalg.norm(xv32 - x64) / torch.linalg.norm(x64)))
+            P64.close()
+            if errs:
+                variants[name]["rel_err_vs_fp64_per_system"] = [float("%.3g" % e) for e in errs]
+                variants[name]["rel_err_vs_fp64_max"] = max(errs)
+        if only is None or "learned_guess" in only:
+            try:
+                wl = pb.WORKLOADS["convdiff3d_128_long"] if args.workload == "convdiff3d_128" else w
+                variants["learned_guess"] = learned_guess_variants(M, torch, A, wl, dev, f)
+            except Exception as e:
+                variants["learned_guess"] = {"error": str(e)[-300:]}
         line["variants"] = variants
 
     # the oracle sample below is Algorithm 1 without a preconditioner

@@ -150,8 +150,9 @@ void msstab_default_options(msstab_options* opt);
  * Create a solver for the n x n matrix A (CSR: d_row_ptr[n+1], d_col[nnz],
  * d_val[nnz], int32 indices, FP64 values) with cut-space dimension s and
  * stabilisation degree l (Algorithm 1's s and l; 1 <= s <= 16, 1 <= l <= 8,
- * s <= n).  d_p_raw (s columns of length n, ld = n) is the raw random basis of
- * the cut space P; it is orthonormalised on the device (Cholesky QR, twice) and
+ * s <= n; 1 <= n <= 2^31 - 2^22, 0 <= nnz < 2^31).  d_p_raw (s columns of
+ * length n, ld = n) is the raw random basis of the cut space P; it is
+ * orthonormalised on the device (Cholesky QR, twice) and
  * kept, with an FP32 copy, for the lifetime of the handle (Section 2.4: the
  * basis of P may be random; Section 4.2: P stays fixed over the sequence).
  * The matrix is copied (the caller may free its arrays afterwards), converted
@@ -219,6 +220,22 @@ msstab_status msstab_select_guess(msstab_t h, const double* d_b, const double* d
 msstab_status msstab_select_guess_scaled(msstab_t h, const double* d_b, const double* d_xprev,
                                          const double* d_delta, double* d_x, int32_t* used, double* alpha,
                                          double* reduction);
+
+/* The residual-minimising combination of up to four directions (a workload
+ * form, not in the paper): with r0 = b - A x_prev and W = [A dir_1 .. A dir_m]
+ * (dir_j at d_dirs + (j-1) ld, ld >= n, 1 <= m <= min(4, s (l + 2))),
+ *   d_x = d_xprev + sum_j a_j dir_j,  a = argmin ||r0 - W a||,
+ * computed from the normal equations scaled by diag(W^T W)^-1/2 (Cholesky; a
+ * zero direction gets a_j = 0; for numerically dependent directions the best
+ * single one is taken).  Uses 1 + m products with A (FP64) and the handle's
+ * level workspace (free between solves).  *used = 1 if the combination lowers
+ * the residual, else d_x = d_xprev and a = 0.  coef (host, m entries) and
+ * *reduction (host, ||b - A x|| / ||r0||) may be NULL.  For time-stepping
+ * sequences the directions are the network's correction (msstab_cnn_infer)
+ * and the previous step's change x^(i) - x^(i-1). */
+msstab_status msstab_select_guess_span(msstab_t h, const double* d_b, const double* d_xprev, const double* d_dirs,
+                                       int64_t ld, int32_t ndir, double* d_x, int32_t* used, double* coef,
+                                       double* reduction);
 
 /* ---------------------------------------------------------------------------
  * Kernel-level entry points on a handle (for testing and measuring single
@@ -407,13 +424,19 @@ msstab_status msstab_cnn_infer(msstab_cnn_t h, const double* d_r0, const double*
  * as msstab_op_spmv_dot on a CSR handle, without a handle.  The caller passes
  * all inputs and outputs; the reduction scratch is a fixed device array inside
  * the library (about 160 KB, one per GPU that loads the library, held until the
- * process exits).  Limits: 1 <= n < 2^31 - 64, 0 <= nnz < 2^31, 0 <= s <= 16;
- * other sizes are rejected with MSSTAB_ERR_INVALID_ARG and a message in
- * msstab_last_error(NULL).  The call allocates nothing (no cudaMalloc, no
+ * process exits).  Limits: 1 <= n <= 2^31 - 2^22, 0 <= nnz < 2^31,
+ * 0 <= s <= 16 (d_P may be NULL when s = 0); other sizes are rejected with
+ * MSSTAB_ERR_INVALID_ARG and a message in msstab_last_error(NULL).  A CUDA
+ * error left pending by earlier work on the calling thread makes the call
+ * return MSSTAB_ERR_CUDA before it launches anything; that error is left
+ * pending for its owner.  The call allocates nothing (no cudaMalloc, no
  * cudaFree, no allocating library routine); it is asynchronous on `stream`
  * (a cudaStream_t; NULL = the legacy default stream).  The first call on a
  * device looks up the device address of the scratch array (once per device,
  * with that device current); make that first call before any stream capture.
+ * The address is kept for the rest of the process: it assumes that the
+ * device's primary context lives until the process exits (after a
+ * cudaDeviceReset the kept address is stale and the call must not be used).
  * Every call shares the one scratch array, which keeps the last call's
  * contents (the call clears what must start at zero): calls that overlap on
  * the GPU -- concurrent streams, or several host threads -- race and must be

@@ -14,6 +14,8 @@ idrstab   Algorithm 1 (IDRstab) step by step, the Arnoldi start of level s, the
           (the s = l = 1 special case), and the small dense solves.
 cnn       the 3D CNN used for the learned initial guess: convolution forward and
           backward, GELU, MSE loss and one Adam step, in FP64.
+guess     the selection of a learned initial guess: the residual-minimising
+          point of x_prev + span(directions), by its definition.
 ilu       ILU(0) split preconditioning (Section 5.1): the factor by its
           definition (IKJ elimination restricted to A's pattern), triangular
           solves, the preconditioned operator and the preconditioned sequence.
@@ -24,7 +26,9 @@ printed values in tests/golden/paper_finite_termination.json), the
 invariants V = AU, P^T r^(i) = 0, Z^T r = 0, true = recursive residual, the MV
 counts of Table 1, and for the CNN central finite differences, scipy's
 correlate, tabulated normal-CDF values and the closed form of the first Adam
-step; for ILU(0) its defining equations checked by dense products, the exact
+step; for the guess selection the exact correction in the span, the
+closed form of a single direction and the orthogonality of the optimal
+residual to A times the directions; for ILU(0) its defining equations checked by dense products, the exact
 LU of a tridiagonal matrix, the known fill positions of the 5-point stencil
 and dense triangular solves.  Parity unpinned: the MV counts on the synthetic convection-diffusion
 sequences (the paper prints none for them) and the choice of fetching point

@@ -23,6 +23,14 @@ constexpr int MAXBLK = 2048;        // blocks of one reduction group
 constexpr double PIVOT_REL_TOL = 1e-14;
 constexpr double CHOLQR_REL_TOL = 1e-14;   // rank test of the Cholesky QR
 
+// Largest vector length (rows of A) the library accepts.  The grid-stride
+// loops keep their row index in a signed 32-bit int and advance it by at most
+// 2 * gridDim.x * blockDim.x <= 2 * MAXBLK * 1024 = 2^22 (no launch of the
+// library has more than MAXBLK blocks of more than 1024 threads), so for
+// n <= MAX_ROWS the index of the step after the last row stays below 2^31.
+constexpr int64_t MAX_ROWS = (1LL << 31) - (1LL << 22);
+static_assert(2LL * MAXBLK * 1024 <= (1LL << 22), "grid strides must stay within the MAX_ROWS margin");
+
 // Flags raised on the device and read by the host at the cycle end.
 constexpr int FLAG_BREAKDOWN = 1;
 constexpr int FLAG_CHOL = 2;

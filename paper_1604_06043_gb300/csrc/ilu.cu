@@ -562,6 +562,7 @@ __global__ void ilu_level_scatter_kernel(int n, const int* lev, int* cursor, int
 static int stream_grid(const Ctx& c, int64_t n) {
   int64_t g = (n + NT - 1) / NT;
   if (g > (int64_t)c.sms * 8) g = (int64_t)c.sms * 8;
+  if (g > MAXBLK) g = MAXBLK;
   return (int)(g < 1 ? 1 : g);
 }
 

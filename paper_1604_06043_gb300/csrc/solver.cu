@@ -1185,7 +1185,7 @@ msstab_status msstab_create(int64_t n, int64_t nnz, const int32_t* d_row_ptr, co
   g_create_error.clear();
   if (!out) return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
-  if (n < 1 || n >= (1LL << 31) - 64) return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "n out of range");
+  if (n < 1 || n > MAX_ROWS) return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "n must be in [1, 2^31 - 2^22]");
   if (nnz < 0 || nnz >= (1LL << 31)) return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "nnz out of range");
   if (s < 1 || s > SMAX || s > n) return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "s must satisfy 1 <= s <= min(16, n)");
   if (ell < 1 || ell > LMAX) return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "l must satisfy 1 <= l <= 8");
@@ -1367,6 +1367,131 @@ msstab_status msstab_select_guess_scaled(msstab_t h, const double* d_b, const do
   if (used) *used = keep ? 1 : 0;
   if (alpha) *alpha = keep ? a : 0.0;
   if (reduction) *reduction = keep ? std::sqrt(std::max(0.0, 1.0 - (wr * wr) / (ww * rr))) : 1.0;
+  return MSSTAB_OK;
+}
+
+// Coefficients a minimising ||r0 - W a|| from G = W^T W (row-major, m x m),
+// c = W^T r0 and rr = ||r0||^2: the normal equations scaled by
+// D = diag(G)^-1/2 and solved by Cholesky; a direction with W_j = 0 gets
+// a_j = 0.  If the scaled Gram is not numerically positive definite (nearly
+// dependent directions), the best single direction is taken.  Returns the
+// squared residual ratio ||r0 - W a||^2 / rr (clamped to [0, 1]).
+static double span_coefficients(const double* G, const double* c, double rr, int m, double* a) {
+  double d[4], M[16], y[4];
+  int idx[4], k = 0;
+  for (int j = 0; j < m; ++j) {
+    a[j] = 0.0;
+    if (G[j * m + j] > 0.0 && std::isfinite(G[j * m + j])) idx[k++] = j;
+  }
+  if (k == 0 || !(rr > 0.0)) return 1.0;
+  for (int i = 0; i < k; ++i) d[i] = 1.0 / std::sqrt(G[idx[i] * m + idx[i]]);
+  for (int i = 0; i < k; ++i) {
+    for (int j = 0; j < k; ++j) M[i * k + j] = d[i] * G[idx[i] * m + idx[j]] * d[j];
+    y[i] = d[i] * c[idx[i]];
+  }
+  // Cholesky M = R^T R (upper R in place of M's upper triangle), pivots above 1e-12
+  bool ok = true;
+  double R[16] = {};
+  for (int j = 0; j < k && ok; ++j) {
+    double s = M[j * k + j];
+    for (int i = 0; i < j; ++i) s -= R[i * k + j] * R[i * k + j];
+    if (!(s > 1e-12)) {
+      ok = false;
+      break;
+    }
+    R[j * k + j] = std::sqrt(s);
+    for (int l = j + 1; l < k; ++l) {
+      double v = M[j * k + l];
+      for (int i = 0; i < j; ++i) v -= R[i * k + j] * R[i * k + l];
+      R[j * k + l] = v / R[j * k + j];
+    }
+  }
+  if (ok) {
+    for (int i = 0; i < k; ++i) {          // R^T w = y
+      double v = y[i];
+      for (int l = 0; l < i; ++l) v -= R[l * k + i] * y[l];
+      y[i] = v / R[i * k + i];
+    }
+    for (int i = k - 1; i >= 0; --i) {     // R z = w
+      double v = y[i];
+      for (int l = i + 1; l < k; ++l) v -= R[i * k + l] * y[l];
+      y[i] = v / R[i * k + i];
+    }
+    for (int i = 0; i < k; ++i) a[idx[i]] = d[i] * y[i];
+  } else {
+    int best = 0;
+    double gain = -1.0;
+    for (int i = 0; i < k; ++i) {
+      const double g = y[i] * y[i];       // (c_j^2 / G_jj): the reduction of ||r||^2 by direction j alone
+      if (g > gain) {
+        gain = g;
+        best = i;
+      }
+    }
+    a[idx[best]] = d[best] * d[best] * c[idx[best]];
+  }
+  double ca = 0.0;
+  for (int j = 0; j < m; ++j) ca += c[j] * a[j];
+  const double ratio = 1.0 - ca / rr;
+  return ratio < 0.0 ? 0.0 : (ratio > 1.0 ? 1.0 : ratio);
+}
+
+msstab_status msstab_select_guess_span(msstab_t h, const double* d_b, const double* d_xprev, const double* d_dirs,
+                                       int64_t ld, int32_t ndir, double* d_x, int32_t* used, double* coef,
+                                       double* reduction) {
+  CKS(check_handle(h));
+  CKS(check_ptr(h, d_b, "b"));
+  CKS(check_ptr(h, d_xprev, "xprev"));
+  CKS(check_ptr(h, d_dirs, "dirs"));
+  CKS(check_ptr(h, d_x, "x"));
+  if (ndir < 1 || ndir > 4 || ndir > h->s * (h->ell + 2))
+    return fail(h, MSSTAB_ERR_INVALID_ARG, "ndir must be in [1, min(4, s (l + 2))]");
+  if (ld < h->n) return fail(h, MSSTAB_ERR_INVALID_ARG, "ld < n");
+  const Ctx c = h->ctx();
+  const int n = h->n;
+  DevState* st = h->st;
+  Work<double>& w = h->w64;
+  // r0 = b - A x_prev into Tm; W_j = A dir_j into level columns of the
+  // workspace (free between solves); then W^T W, W^T r0 and ||r0||^2
+  LAUNCH(MSSTAB_K_SPMV, spmv<double>(c, h->A, d_xprev, w.Tm, d_b, nullptr, 0, 0, 1, 0, &st->scal[0], epi_none(h)));
+  MdCols<double> cols{};
+  for (int j = 0; j < ndir; ++j) {
+    double* Wj = w.V + (int64_t)j * w.ld;
+    LAUNCH(MSSTAB_K_SPMV, spmv<double>(c, h->A, d_dirs + (int64_t)j * ld, Wj, nullptr, nullptr, 0, 0, 0, 0,
+                                       nullptr, epi_none(h)));
+    cols.x[j] = Wj;
+    cols.y[j] = Wj;
+  }
+  cols.y[ndir] = w.Tm;
+  // out[t * 8 + col]: t < ndir targets, columns W_0 .. W_{ndir-1}, r0
+  LAUNCH(MSSTAB_K_OTHER, multidot<double>(c, n, cols, ndir, ndir + 1, 0, &st->scal[8], 8, epi_none(h)));
+  CK(cudaMemcpyAsync(h->h_small, &st->scal[0], sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaMemcpyAsync(h->h_small + 8, &st->scal[8], 8 * ndir * sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  const double rr = h->h_small[0];
+  double G[16], cv[4], a[4];
+  for (int i = 0; i < ndir; ++i) {
+    for (int j = 0; j < ndir; ++j) G[i * ndir + j] = h->h_small[8 + i * 8 + j];
+    cv[i] = h->h_small[8 + i * 8 + ndir];
+  }
+  const double ratio = span_coefficients(G, cv, rr, ndir, a);
+  bool keep = ratio < 1.0;
+  for (int j = 0; j < ndir; ++j) keep = keep && std::isfinite(a[j]);
+  if (keep) {
+    // x = x_prev + sum_j a_j dir_j (d_x may alias neither input nor be
+    // written before the last read: the combination goes through XB2)
+    LAUNCH(MSSTAB_K_OTHER, axpby_f64(c, n, 1.0, d_xprev, a[0], d_dirs, w.XB2));
+    for (int j = 1; j < ndir; ++j)
+      LAUNCH(MSSTAB_K_OTHER, axpby_f64(c, n, 1.0, w.XB2, a[j], d_dirs + (int64_t)j * ld, w.XB2));
+    CK(cudaMemcpyAsync(d_x, w.XB2, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  } else {
+    CK(cudaMemcpyAsync(d_x, d_xprev, sizeof(double) * n, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  CK(cudaStreamSynchronize(h->stream));
+  if (used) *used = keep ? 1 : 0;
+  if (coef)
+    for (int j = 0; j < ndir; ++j) coef[j] = keep ? a[j] : 0.0;
+  if (reduction) *reduction = keep ? std::sqrt(ratio) : 1.0;
   return MSSTAB_OK;
 }
 

@@ -549,8 +549,8 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
                                                  double* d_y, const double* d_P, int64_t ldp, int32_t s,
                                                  double* d_dots, void* stream) {
   using namespace msk;
-  if (n < 1 || n >= (1LL << 31) - 64 || nnz < 0 || nnz >= (1LL << 31)) {
-    set_global_error("msstab_spmv_dot_noalloc: n must be in [1, 2^31 - 64) and nnz in [0, 2^31)");
+  if (n < 1 || n > MAX_ROWS || nnz < 0 || nnz >= (1LL << 31)) {
+    set_global_error("msstab_spmv_dot_noalloc: n must be in [1, 2^31 - 2^22] and nnz in [0, 2^31)");
     return MSSTAB_ERR_INVALID_ARG;
   }
   if (s < 0 || s > SMAX) {
@@ -590,6 +590,15 @@ extern "C" msstab_status msstab_spmv_dot_noalloc(int64_t n, int64_t nnz, const i
       sms[dev] = m;
       addr[dev] = ptr;
     }
+  }
+  // An error left pending by earlier, unrelated work on this thread is
+  // reported as such and left pending for its owner, so that the status of
+  // the launch below is this call's own.
+  e = cudaPeekAtLastError();
+  if (e != cudaSuccess) {
+    set_global_error(std::string("msstab_spmv_dot_noalloc: a CUDA error from earlier work is pending (not "
+                                 "cleared): ") + cudaGetErrorString(e));
+    return MSSTAB_ERR_CUDA;
   }
   double* base = (double*)addr[dev];
   RedScratch rs{base, nullptr, (unsigned int*)(base + (size_t)NOALLOC_MAX_BLOCKS * MAXRED), NOALLOC_MAX_BLOCKS};

@@ -99,6 +99,8 @@ _SIGS = {
     "msstab_select_guess": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I32)]),
     "msstab_select_guess_scaled": (_I32, [_P, _P, _P, _P, _P, ctypes.POINTER(_I32), ctypes.POINTER(_D),
                                           ctypes.POINTER(_D)]),
+    "msstab_select_guess_span": (_I32, [_P, _P, _P, _P, _I64, _I32, _P, ctypes.POINTER(_I32), _P,
+                                        ctypes.POINTER(_D)]),
     "msstab_op_spmv": (_I32, [_P, _I32, _P, _P]),
     "msstab_op_residual": (_I32, [_P, _P, _P, _P, _P]),
     "msstab_op_spmv_dot": (_I32, [_P, _I32, _P, _P, _P]),
@@ -300,6 +302,16 @@ class Solver:
         _check(load().msstab_select_guess_scaled(self._h, _ptr(b), _ptr(xprev), _ptr(delta), _ptr(x),
                                                  ctypes.byref(used), ctypes.byref(a), ctypes.byref(red)), self._h)
         return bool(used.value), a.value, red.value
+
+    def select_guess_span(self, b, xprev, dirs, x):
+        """x = xprev + sum_j a_j dirs[j] with the residual-minimising a (dirs:
+        (m, n) CUDA float64, m <= 4); returns (used, a, ||b - A x|| / ||b - A xprev||)."""
+        m = dirs.shape[0]
+        used, red = ctypes.c_int32(), ctypes.c_double()
+        coef = (ctypes.c_double * m)()
+        _check(load().msstab_select_guess_span(self._h, _ptr(b), _ptr(xprev), _ptr(dirs), dirs.shape[1], m,
+                                               _ptr(x), ctypes.byref(used), coef, ctypes.byref(red)), self._h)
+        return bool(used.value), list(coef), red.value
 
     # -- kernel-level entry points -----------------------------------------
     def op_spmv(self, x, y, prec: int = 0):

@@ -79,3 +79,21 @@ def test_product_path_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(from|import)\s+oracle", text, flags=re.M), f
+
+
+@needs_nvcc
+def test_row_bound_is_checked_before_any_device_work():
+    # n above 2^31 - 2^22 would let a signed 32-bit grid-stride row index
+    # overflow; both entry points reject it on the host, before any CUDA call
+    from paper_1604_06043_gb300 import msstab
+    B.build()
+    lib = msstab.load()
+    big = (1 << 31) - (1 << 22) + 1
+    dummy = ctypes.c_void_p(256)             # never dereferenced: the size check comes first
+    h = ctypes.c_void_p()
+    rc = lib.msstab_create(big, 0, dummy, None, None, 4, 2, dummy, None, ctypes.byref(h))
+    assert rc == msstab.ERR_INVALID_ARG and not h.value
+    assert b"n must be" in lib.msstab_last_error(None)
+    rc = lib.msstab_spmv_dot_noalloc(big, 0, dummy, None, None, dummy, dummy, dummy, big, 4, dummy, None)
+    assert rc == msstab.ERR_INVALID_ARG
+    assert b"n must be" in lib.msstab_last_error(None)
