@@ -36,12 +36,13 @@ METRIC = "ms/system & #MVs for 128³ implicit-Euler seq at 1e-8 rel res; SpMV HB
 UNIT = "ms/system"
 WORKLOAD = "convdiff3d_128"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_128.json")
-FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond"]
+FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond", "level"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
 # DRAM bytes (read + write) of one launch of the dominant kernel of each form,
 # from one ncu capture of the current kernel at 128^3
-# (profiles/ncu_spmv_dot_fp64_convdiff3d_128.md, ..._fp32inner_...).
-NCU_TRAFFIC = {("convdiff3d_128", "fp64", "spmv_dot"): 342_305_280,
+# (profiles/ncu_level_fp64_convdiff3d_128.md, ncu_spmv_dot_*_convdiff3d_128.md).
+NCU_TRAFFIC = {("convdiff3d_128", "fp64", "level"): 4_600_564_224,
+               ("convdiff3d_128", "fp64", "spmv_dot"): 342_305_280,
                ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_367_872,
                ("convdiff3d_128", "ilu0", "precond"): 161_049_344}
 
@@ -177,6 +178,9 @@ def family_model(A, s, ell, cycles, solves, replaced=0, vb=8):
     lazy_b = sum((s + 1) + (k + 1) * (2 * s + 2) for k in range(ell)) * v
     lazy_f = sum((k + 1) * (s * s + s) for k in range(ell)) * 2 * n
     m["lazy"] = dict(launches=cycles * ell, bytes=lazy_b / ell, flops=lazy_f / ell)
+    # the persistent level step: the gamma step, s + 1 fused products, s eta steps
+    m["level"] = dict(launches=cycles * ell, bytes=(s + 2) * v + (s + 1) * (spmv + s * v) + s * (s + 2) * v,
+                      flops=2 * s * n + (s + 1) * 2 * (A.nnz + s * n) + s * 2 * s * n)
     tau_cycle_b = (ell + 1) * v + ((ell + 1) + 1 + s * (ell + 2) + s + 3 + 2 * s) * v
     tau_cycle_f = 2 * (ell + 1) ** 2 * n + 2 * ((2 * s + 2) * ell + s * (s + 1) + 1) * n
     tau_b = cycles * tau_cycle_b + solves * (2 * s + 1) * v

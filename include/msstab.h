@@ -61,7 +61,9 @@ enum {
   MSSTAB_K_OTHER = 6,    /* Arnoldi start, orthonormalisation, conversions, copies */
   MSSTAB_K_CNN = 7,      /* learned initial guess */
   MSSTAB_K_PRECOND = 8,  /* ILU(0) triangular solves and U x (the preconditioned operator) */
-  MSSTAB_K_COUNT = 9
+  MSSTAB_K_LEVEL = 9,    /* persistent level step: gamma step, the s + 1 products with A and the
+                            eta steps of one level, with their small solves, in one launch */
+  MSSTAB_K_COUNT = 10
 };
 
 typedef struct msstab_options {
@@ -116,8 +118,19 @@ typedef struct msstab_options {
                               point, the recycled U, V and replace_every refer to that system (its
                               true residual is L^-1 (b - A U^-1 x~)).  FP64 only; A must hold every
                               diagonal entry and strictly increasing columns in each row */
-  int32_t reserved;
+  int32_t persistent;      /* 1 (default): each level step of a cycle (the gamma step, the s + 1
+                              products with A with their projections and small solves, the eta
+                              steps) runs as ONE cooperative launch of one 1024-thread block per SM
+                              whose blocks meet at grid barriers; results are those of 0 bit for
+                              bit.  0: one launch per step.  Used with the SELL format and without
+                              the preconditioner (else 0 applies) */
   void* stream;            /* cudaStream_t for all work of the handle; NULL = default stream */
+  int64_t spin_limit;      /* polls after which a device-side wait of the library gives up (the
+                              grid barriers of the level steps and of the ILU(0) sweeps, the
+                              sweeps' waits on other blocks' values): the kernel raises a flag,
+                              every block leaves, and the call returns MSSTAB_ERR_CUDA ("timed
+                              out") with d_x untouched; the handle stays usable.  <= 0: 2^22
+                              (seconds; a wait that long means a block is not running) */
 } msstab_options;
 
 typedef struct msstab_stats {
@@ -190,6 +203,10 @@ const char* msstab_last_error(msstab_t h);
 /* The per-cycle relative recursive residuals of the last solve (the start value
  * first) and the MV count at each of those points; copies min(cap, count). */
 msstab_status msstab_history(msstab_t h, double* relres, int64_t* mvs, int32_t cap, int32_t* count);
+
+/* Set options.spin_limit of an existing handle (polls before a device-side
+ * wait gives up; <= 0: the default 2^22).  Takes effect from the next call. */
+msstab_status msstab_set_spin_limit(msstab_t h, int64_t polls);
 
 /* Drop the recycled U, V (the next solve starts from an Arnoldi basis again). */
 msstab_status msstab_reset_recycle(msstab_t h);

@@ -219,6 +219,30 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], int m, double* smem
   __syncthreads();
 }
 
+// Sum the m values of the nblk per-block partials at base (partial b, value i
+// at base[b * MAXRED + i]) into red[0..m) in a fixed order: warp w takes
+// values w, w + nwarps, ...; its lanes stride over the blocks with four
+// independent chains (four loads in flight per lane), then a warp sum.  The
+// result depends only on the partials, never on which block sums them.  Reads
+// through L2 (the partials come from other blocks).  Ends with __syncthreads.
+__device__ __forceinline__ void sum_partials(const double* base, int nblk, int m, double* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int i = w; i < m; i += nw) {
+    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    int b = lane;
+    for (; b + 96 < nblk; b += 128) {
+      v0 += __ldcg(base + (size_t)b * MAXRED + i);
+      v1 += __ldcg(base + (size_t)(b + 32) * MAXRED + i);
+      v2 += __ldcg(base + (size_t)(b + 64) * MAXRED + i);
+      v3 += __ldcg(base + (size_t)(b + 96) * MAXRED + i);
+    }
+    for (; b < nblk; b += 32) v0 += __ldcg(base + (size_t)b * MAXRED + i);
+    double v = warp_sum((v0 + v1) + (v2 + v3));
+    if (lane == 0) red[i] = v;
+  }
+  __syncthreads();
+}
+
 // Publish this block's m values as partial `blk` of group `grp` (nblk blocks in
 // the group) and take a ticket.  Returns true in the last block of the group,
 // which then holds the group's sums (in block order) in red[0..m).  The group's
@@ -236,25 +260,54 @@ __device__ __forceinline__ bool grid_reduce(RedScratch rs, int grp, int blk, int
   __syncthreads();
   if (!*s_last) return false;
   __threadfence();
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const double* base = rs.partials + (size_t)grp * rs.max_blocks * MAXRED;
-  for (int i = w; i < m; i += nw) {
-    // four independent partial sums keep four loads in flight per lane
-    double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
-    int b = lane;
-    for (; b + 96 < nblk; b += 128) {
-      v0 += __ldcg(base + (size_t)b * MAXRED + i);
-      v1 += __ldcg(base + (size_t)(b + 32) * MAXRED + i);
-      v2 += __ldcg(base + (size_t)(b + 64) * MAXRED + i);
-      v3 += __ldcg(base + (size_t)(b + 96) * MAXRED + i);
-    }
-    for (; b < nblk; b += 32) v0 += __ldcg(base + (size_t)b * MAXRED + i);
-    double v = warp_sum((v0 + v1) + (v2 + v3));
-    if (lane == 0) red[i] = v;
-  }
-  __syncthreads();
+  sum_partials(rs.partials + (size_t)grp * rs.max_blocks * MAXRED, nblk, m, red);
   if (threadIdx.x == 0) rs.tickets[grp] = 0u;
   return true;
+}
+
+// ---------------------------------------------------------------------------
+// bounded grid barrier of the persistent (cooperative) kernels
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void red_release_add_u32(unsigned int* p, unsigned int v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+__device__ __forceinline__ unsigned int ld_acquire_u32(const unsigned int* p) {
+  unsigned int v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// All blocks of a cooperative launch meet here.  *count is zero at launch; the
+// barrier numbered `gen` (1, 2, ...) completes when it reaches gen * gridDim.x.
+// Thread 0 raises the counter with release semantics (after the block's
+// __syncthreads, so the stores of every thread of the block are ordered
+// before it) and polls with acquire loads.  Bounded: after spin_limit polls it
+// raises FLAG_SYNC_TIMEOUT in *flag and gives up; a block that sees the flag
+// gives up too.  Returns false (in every thread of the block) on giving up:
+// the caller must then leave the kernel.
+__device__ __forceinline__ bool grid_sync(unsigned int* count, unsigned int gen, int* flag, long long spin_limit,
+                                          int* s_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    const unsigned int target = gen * gridDim.x;
+    red_release_add_u32(count, 1u);
+    for (long long it = 0; ld_acquire_u32(count) < target; ++it) {
+      if ((it & 63) == 63 && (*(const volatile int*)flag & FLAG_SYNC_TIMEOUT)) {
+        ok = 0;
+        break;
+      }
+      if (it >= spin_limit) {
+        atomicOr(flag, FLAG_SYNC_TIMEOUT);
+        ok = 0;
+        break;
+      }
+    }
+    *s_ok = ok;
+  }
+  __syncthreads();
+  return *s_ok != 0;
 }
 
 // Second level: after the last block of group grp has its sums, publish them

@@ -28,7 +28,8 @@
 // launch, that thread 0 of every block raises by one with release semantics
 // after its block's rows (so the rows' stores are visible first) and then polls
 // with acquire loads until it reaches (level + 1) x blocks.  Every wait is
-// bounded: after BAR_SPIN_LIMIT polls the block raises FLAG_SYNC_TIMEOUT in
+// bounded: after spin_limit polls (IluDesc::spin_limit, 2^22 unless the
+// handle's options set it) the block raises FLAG_SYNC_TIMEOUT in
 // the device flag word and leaves, the blocks still waiting see the flag and
 // leave too, and the host reads the flag at the next cycle end.  Values
 // written by other blocks are read through L2 (__ldcg), never from a possibly
@@ -43,7 +44,6 @@
 namespace msk {
 
 constexpr int ITS = 256;                       // threads per block of the level sweeps
-constexpr long long BAR_SPIN_LIMIT = 1LL << 22;
 
 __device__ __forceinline__ void red_release_add(unsigned int* p, unsigned int v) {
   asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -56,7 +56,8 @@ __device__ __forceinline__ unsigned int ld_acquire(const unsigned int* p) {
 }
 
 // The barrier after level l (see the file comment): false if it timed out.
-__device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned int target, int* flag) {
+__device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned int target, int* flag,
+                                              long long spin_limit) {
   __shared__ int s_ok;
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -67,7 +68,7 @@ __device__ __forceinline__ bool level_barrier(unsigned int* count, unsigned int 
         ok = 0;
         break;
       }
-      if (it > BAR_SPIN_LIMIT) {
+      if (it > spin_limit) {
         atomicOr(flag, FLAG_SYNC_TIMEOUT);
         ok = 0;
         break;
@@ -93,6 +94,7 @@ struct SweepArgs {
   double* out;         // solution (may equal in)
   unsigned int* count; // barrier counter (zero at launch)
   int* flag;
+  long long spin_limit;
 };
 
 template <int MODE>
@@ -136,7 +138,7 @@ __global__ void __launch_bounds__(ITS) ilu_sweep_kernel(SweepArgs a) {
         __stcg(a.out + i, sum / a.lu[d]);
       }
     }
-    if (l + 1 < a.nlev && !level_barrier(a.count, (unsigned)(l + 1) * gridDim.x, a.flag)) return;
+    if (l + 1 < a.nlev && !level_barrier(a.count, (unsigned)(l + 1) * gridDim.x, a.flag, a.spin_limit)) return;
   }
 }
 
@@ -158,6 +160,7 @@ struct PackedArgs {
   const double* in;
   double* out;           // may equal in
   int* flag;
+  long long spin_limit;
 };
 
 template <int W>
@@ -230,7 +233,7 @@ __global__ void __launch_bounds__(ITS) ilu_sweep_level_kernel(LevelArgs L) {
         level_row<W>(a, r);
       }
     }
-    if (l + 1 < L.nlev && !level_barrier(L.count, (unsigned)(l + 1) * gridDim.x, a.flag)) return;
+    if (l + 1 < L.nlev && !level_barrier(L.count, (unsigned)(l + 1) * gridDim.x, a.flag, a.spin_limit)) return;
   }
 }
 
@@ -294,7 +297,7 @@ __global__ void ilu_pad_counts_kernel(int nlev, const int* lptr, int* cnt) {
 // does not depend on shared memory.
 // Termination.  A chunk waits only on chunks on one side of it, the first
 // chunk on that side waits on none, and a cooperative launch keeps every block
-// resident, so the sweep completes; every wait is bounded (BAR_SPIN_LIMIT
+// resident, so the sweep completes; every wait is bounded (spin_limit
 // polls, then FLAG_SYNC_TIMEOUT and NaN), and a thread that sees the flag
 // stops waiting.  Rows of one group never depend on each other, so lanes of a
 // warp wait only on other blocks.
@@ -321,10 +324,10 @@ __device__ __forceinline__ void st_relaxed(double* p, double x) {
 }
 
 // poll p until it no longer holds the sentinel (canonical NaN after a timeout)
-__device__ __noinline__ unsigned long long wait_value(const double* p, int* flag) {
+__device__ __noinline__ unsigned long long wait_value(const double* p, int* flag, long long spin_limit) {
   for (long long it = 1;; ++it) {
     if ((it & 255) == 0 && (*(const volatile int*)flag & FLAG_SYNC_TIMEOUT)) return 0x7FFFFFFFFFFFFFFFull;
-    if (it > BAR_SPIN_LIMIT) {
+    if (it > spin_limit) {
       atomicOr(flag, FLAG_SYNC_TIMEOUT);
       return 0x7FFFFFFFFFFFFFFFull;
     }
@@ -348,6 +351,7 @@ struct ChunkArgs {
   const double* in;
   double* out;           // filled with SENTINEL before the launch; distinct from in
   int* flag;
+  long long spin_limit;
 };
 
 // The static data of one position and its right-hand side.  All W dependency
@@ -383,7 +387,7 @@ __device__ __forceinline__ double chunk_solve(const ChunkArgs& a, const ChunkRow
   for (int j = 0; j < W; ++j) x[j] = (j < r.cnt && r.d[j] >= 0) ? ld_relaxed(a.out + r.d[j]) : 0ull;
 #pragma unroll
   for (int j = 0; j < W; ++j)
-    if (j < r.cnt && r.d[j] >= 0 && x[j] == SENTINEL) x[j] = wait_value(a.out + r.d[j], a.flag);
+    if (j < r.cnt && r.d[j] >= 0 && x[j] == SENTINEL) x[j] = wait_value(a.out + r.d[j], a.flag, a.spin_limit);
   double sum = r.rhs;
 #pragma unroll
   for (int j = 0; j < W; ++j) {
@@ -570,7 +574,8 @@ template <int MODE>
 static cudaError_t launch_sweep(const Ctx& c, const IluDesc& F, int u, const double* in, double* out) {
   cudaError_t e = cudaMemsetAsync(&F.bar->count, 0, sizeof(unsigned int), c.stream);
   if (e != cudaSuccess) return e;
-  SweepArgs a{F.nlev[u], F.lptr[u], F.lrows[u], F.row_ptr, F.col, F.diag, F.lu, in, out, &F.bar->count, F.flag};
+  SweepArgs a{F.nlev[u], F.lptr[u], F.lrows[u], F.row_ptr, F.col, F.diag, F.lu, in, out, &F.bar->count, F.flag,
+              F.spin_limit};
   void* args[] = {&a};
   return cudaLaunchCooperativeKernel((const void*)ilu_sweep_kernel<MODE>, dim3(F.grid[u]), dim3(ITS), args, 0,
                                      c.stream);
@@ -591,7 +596,7 @@ static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const doub
     e = cudaMemsetAsync(out, 0xFF, sizeof(double) * F.n, c.stream);
     if (e != cudaSuccess) return e;
     ChunkArgs ca{F.n, F.gofs[u], F.gptr[u], F.cprow[u], F.cpcnt[u], F.cpcol[u], F.cpval[u],
-                 u == 1 ? F.cpdiag : nullptr, in, out, F.flag};
+                 u == 1 ? F.cpdiag : nullptr, in, out, F.flag, F.spin_limit};
     void* cargs[] = {&ca};
     const int P = (F.n + F.CH[u] - 1) / F.CH[u];
     const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
@@ -600,7 +605,7 @@ static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const doub
   e = cudaMemsetAsync(&F.bar->count, 0, sizeof(unsigned int), c.stream);
   if (e != cudaSuccess) return e;
   PackedArgs p{F.npad[u], F.prow[u], F.pcnt[u], F.pcol[u], F.pval[u], u == 1 ? F.pdiag[1] : nullptr, in, out,
-               F.flag};
+               F.flag, F.spin_limit};
   LevelArgs L{p, F.nlev[u], F.pptr[u], &F.bar->count};
   void* largs[] = {&L};
   const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_level_kernel<4> : (const void*)ilu_sweep_level_kernel<8>;

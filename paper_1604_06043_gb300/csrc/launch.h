@@ -136,6 +136,18 @@ cudaError_t csr_max_diag(const Ctx& c, int n, const int* row_ptr, const int* col
 cudaError_t sell_fill(const Ctx& c, int n, int nslices, const int* row_ptr, const int* col, const double* val,
                       const int* slice_ptr, const int* slice_w, const int* perm, int* scol, double* sval);
 
+// Persistent level step k of Algorithm 1 (one cooperative launch, SELL only):
+// the gamma step on r^(k) (gamma_k from st->gamma), r^(k+1) = A r^(k), and for
+// q = 0..s-1 the eta step and v_q^(k+1) = A v_q^(k), with the projections
+// (st->projR[k+1], st->projV[k+1]), eta (st->eta[k]) and, if next_gamma,
+// gamma_{k+1} stored in st.  bar: one device counter (zeroed here before the
+// launch); every grid barrier gives up after spin_limit polls with
+// FLAG_SYNC_TIMEOUT in st->flag.
+template <typename T>
+cudaError_t level_step(const Ctx& c, const MatDesc& A, T* R, T* V, int64_t ld, int s, int k, int next_gamma,
+                       const T* P, int64_t ldp, const T* Pil, int sp, const T* Pb, DevState* st,
+                       unsigned int* bar, long long spin_limit);
+
 // y = z (b == NULL) or y = b - z, with the reductions and the epilogue of the
 // fused product (the same out layout as spmv): the tail of a product with a
 // preconditioned operator whose last stage produced z.
@@ -190,6 +202,7 @@ struct IluDesc {
   double* scratch = nullptr;      // copy of the right-hand side of an in-place chunked solve
   GridBar* bar = nullptr;         // grid-barrier state (zero between launches)
   int* flag = nullptr;            // device flag word (FLAG_SYNC_TIMEOUT, FLAG_ZERO_PIVOT)
+  long long spin_limit = 1LL << 22;   // polls before a wait on another block gives up
 };
 struct IluSetupResult {
   int code = 0;                   // 0 ok, 1 CUDA error, 2 bad structure, 3 zero pivot, 4 out of memory

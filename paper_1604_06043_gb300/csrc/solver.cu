@@ -105,6 +105,10 @@ struct msstab_s {
   double* ilu_t = nullptr;   // U^-1 x of the running product, then L^-1 A U^-1 x
   double* ilu_z = nullptr;   // A U^-1 x
   double* borig = nullptr;   // the caller's b of the running solve
+  // persistent level steps (options.persistent): one cooperative launch per level step
+  bool level = false;
+  unsigned int* level_bar = nullptr;   // grid-barrier counter of the level kernel
+  long long spin_limit = 1LL << 22;    // polls before a device-side wait gives up
 
   Ctx ctx() const { return Ctx{stream, sms, rs}; }
 };
@@ -510,6 +514,14 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     const bool replaced = ctl.replace_every > 0 && (out.cycles + 1) % ctl.replace_every == 0;
     auto launch_cycle = [&](const Ctx& c) -> msstab_status {
       for (int k = 0; k < ell; ++k) {
+        if (h->level) {
+          // the gamma step, the s + 1 products and the eta steps of level k in one launch
+          LAUNCH(MSSTAB_K_LEVEL, level_step<T>(c, h->A, w.R, w.V, ld, s, k, k + 1 < ell ? 1 : 0, P, ld, w.Pil,
+                                               w.sp, w.Pb, st, h->level_bar, h->spin_limit));
+          LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
+                                                 &st->eta[k * SMAX * SMAX], SMAX));
+          continue;
+        }
         LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
         CKS(amv<T>(h, c, MSSTAB_K_SPMV_DOT, Rk(k), Rk(k + 1), nullptr, P, ld, s, 0, 0,
                                           &st->projR[(k + 1) * SMAX], epi_of(EPI_ETA, k, 0), w.Pil, w.sp, w.Pb));
@@ -586,9 +598,12 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     int flag = 0;
     std::memcpy(&flag, h->h_small + 1, sizeof(int));
     if (flag & FLAG_SYNC_TIMEOUT) {
-      CK(cudaMemsetAsync(h->ilu.bar, 0, sizeof(GridBar), h->stream));
+      if (h->precond) CK(cudaMemsetAsync(h->ilu.bar, 0, sizeof(GridBar), h->stream));
       CK(cudaMemsetAsync(&st->flag, 0, sizeof(int), h->stream));
-      return fail(h, MSSTAB_ERR_CUDA, "a grid barrier of the ILU(0) level sweeps timed out");
+      CK(cudaStreamSynchronize(h->stream));
+      return fail(h, MSSTAB_ERR_CUDA,
+                  h->precond ? "a device-side wait of the ILU(0) sweeps timed out"
+                             : "a grid barrier of the persistent level step timed out");
     }
     if (flag & FLAG_BREAKDOWN) {
       out.status = MSSTAB_ERR_BREAKDOWN;
@@ -938,7 +953,9 @@ void msstab_default_options(msstab_options* opt) {
   opt->max_outer = 0;
   opt->inner_ell = 0;
   opt->replace_every = 0;
+  opt->persistent = 1;
   opt->stream = nullptr;
+  opt->spin_limit = 0;
 }
 
 const char* msstab_last_error(msstab_t h) { return h ? h->err.c_str() : g_create_error.c_str(); }
@@ -985,6 +1002,7 @@ static msstab_status ilu_create(msstab_t h, int64_t n, int64_t nnz, const int32_
   CKS(dalloc(h, &p, sizeof(GridBar)));
   F.bar = (GridBar*)p;
   F.flag = &h->st->flag;
+  F.spin_limit = h->spin_limit;
   CK(cudaMemsetAsync(F.flag, 0, sizeof(int), h->stream));
   const IluSetupResult r = ilu_setup(h->ctx(), F, ilu_alloc, h, (int*)h->h_small);
   if (r.code == 4) return MSSTAB_ERR_OOM;   // dalloc wrote the message
@@ -1020,6 +1038,10 @@ static msstab_status create_impl(msstab_t h, int64_t n, int64_t nnz, const int32
   h->rs.group_out = (double*)p;
   CKS(dalloc(h, &p, sizeof(unsigned) * (MAXGRP + 1)));
   h->rs.tickets = (unsigned*)p;
+  CKS(dalloc(h, &p, 256));
+  h->level_bar = (unsigned int*)p;
+  CK(cudaMemsetAsync(h->level_bar, 0, 256, h->stream));
+  h->spin_limit = h->opt.spin_limit > 0 ? (long long)h->opt.spin_limit : (1LL << 22);
   CK(cudaMemsetAsync(h->rs.tickets, 0, sizeof(unsigned) * (MAXGRP + 1), h->stream));
   h->rs.max_blocks = MAXBLK;
   const Ctx c = h->ctx();
@@ -1213,6 +1235,7 @@ msstab_status msstab_create(int64_t n, int64_t nnz, const int32_t* d_row_ptr, co
     return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "the ILU(0) preconditioner needs precision MSSTAB_PREC_FP64");
   }
   h->precond = h->opt.precond == MSSTAB_PRECOND_ILU0;
+  h->level = h->opt.persistent != 0 && !h->precond && h->opt.spmv_format != MSSTAB_FORMAT_CSR;
   if (h->opt.fetch_policy < MSSTAB_FETCH_ONCE || h->opt.fetch_policy > MSSTAB_FETCH_PROBE) {
     delete h;
     return fail(nullptr, MSSTAB_ERR_INVALID_ARG, "unknown fetch_policy");
@@ -1262,6 +1285,17 @@ msstab_status msstab_solve_host(msstab_t h, const double* b, double* x, double t
     CK(cudaStreamSynchronize(h->stream));
   }
   return rc;
+}
+
+msstab_status msstab_set_spin_limit(msstab_t h, int64_t polls) {
+  CKS(check_handle(h));
+  h->opt.spin_limit = polls;
+  h->spin_limit = polls > 0 ? (long long)polls : (1LL << 22);
+  h->ilu.spin_limit = h->spin_limit;
+  // the cycle graphs hold the old limit in their launch arguments
+  for (auto& g : h->graphs) cudaGraphExecDestroy(g.exec);
+  h->graphs.clear();
+  return MSSTAB_OK;
 }
 
 msstab_status msstab_history(msstab_t h, double* relres, int64_t* mvs, int32_t cap, int32_t* count) {

@@ -166,9 +166,24 @@ __device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<T, NP>
   }
 }
 
+// Loads of the vector x of a product: through the read-only path when x is
+// not written during the launch (XL = 0); through L1 and L2 (ld.global.ca)
+// when another block of the same persistent launch wrote it (XL = 1).  The
+// latter is safe because in that launch every vector is written at most once,
+// before the grid barrier that precedes its product, and nothing loads it
+// into L1 before that write (those loads go through L2 only, __ldcg): no L1
+// line of it can be stale.
+template <int XL, typename T>
+__device__ __forceinline__ T xload(const T* p) {
+  if constexpr (XL == 0)
+    return __ldg(p);
+  else
+    return __ldca(p);
+}
+
 // K consecutive entries of a SELL row (stride 32), continuing the row's
 // multiply-add chain in column order (as CSR does).
-template <typename T, int K>
+template <typename T, int K, int XL = 0>
 __device__ __forceinline__ T sell_chunk(const int* __restrict__ col, const T* __restrict__ val,
                                         const T* __restrict__ x, int64_t base, T sum) {
   int c[K];
@@ -179,39 +194,41 @@ __device__ __forceinline__ T sell_chunk(const int* __restrict__ col, const T* __
     v[u] = ro(val + base + (int64_t)u * 32);
   }
 #pragma unroll
-  for (int u = 0; u < K; ++u) sum = fma_t(v[u], ro(x + c[u]), sum);
+  for (int u = 0; u < K; ++u) sum = fma_t(v[u], xload<XL>(x + c[u]), sum);
   return sum;
 }
 
 // One row of width w: chunks of 8, then an exact tail (no predicated slots).
-template <typename T>
+template <typename T, int XL = 0>
 __device__ __forceinline__ T sell_row(const int* __restrict__ col, const T* __restrict__ val,
                                       const T* __restrict__ x, int64_t base, int w) {
   T sum = T(0);
   int j = 0;
-  for (; j + 8 <= w; j += 8) sum = sell_chunk<T, 8>(col, val, x, base + (int64_t)j * 32, sum);
+  for (; j + 8 <= w; j += 8) sum = sell_chunk<T, 8, XL>(col, val, x, base + (int64_t)j * 32, sum);
   const int64_t b = base + (int64_t)j * 32;
   switch (w - j) {
-    case 1: return sell_chunk<T, 1>(col, val, x, b, sum);
-    case 2: return sell_chunk<T, 2>(col, val, x, b, sum);
-    case 3: return sell_chunk<T, 3>(col, val, x, b, sum);
-    case 4: return sell_chunk<T, 4>(col, val, x, b, sum);
-    case 5: return sell_chunk<T, 5>(col, val, x, b, sum);
-    case 6: return sell_chunk<T, 6>(col, val, x, b, sum);
-    case 7: return sell_chunk<T, 7>(col, val, x, b, sum);
+    case 1: return sell_chunk<T, 1, XL>(col, val, x, b, sum);
+    case 2: return sell_chunk<T, 2, XL>(col, val, x, b, sum);
+    case 3: return sell_chunk<T, 3, XL>(col, val, x, b, sum);
+    case 4: return sell_chunk<T, 4, XL>(col, val, x, b, sum);
+    case 5: return sell_chunk<T, 5, XL>(col, val, x, b, sum);
+    case 6: return sell_chunk<T, 6, XL>(col, val, x, b, sum);
+    case 7: return sell_chunk<T, 7, XL>(col, val, x, b, sum);
     default: return sum;
   }
 }
 
-// NP < 0: plain product; NP >= 0: also the reduction of up to NP dots with P,
-// y.y and b.b, and the epilogue.
-template <typename T, int NP>
-__global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
+// One pass of the SELL product y = A x (or b - A x) over the slices of this
+// thread's warp (warp w of the grid takes slices w, w + nwarps, ...), with the
+// row's contributions to the fused dots accumulated in acc (NP >= 0).  The
+// standalone product and the persistent level kernel both run it, with the
+// same grid, so that their sums are the same bit for bit.
+template <typename T, int NP, int XL>
+__device__ __forceinline__ void sell_pass(const SellMat<T>& A, const SpmvArgs<T>& a,
+                                          DotAcc<T, (NP < 0 ? 0 : NP)>& acc, int nblocks) {
   constexpr int NA = NP < 0 ? 0 : NP;
-  DotAcc<T, NA> acc;
-  acc.zero();
   const int lane = threadIdx.x & 31;
-  const int nwarps = gridDim.x * SNWARP;
+  const int nwarps = nblocks * SNWARP;
   int sl = (blockIdx.x * SNT + threadIdx.x) >> 5;
   // the next slice's width and start are loaded one iteration ahead
   int w_next = 0, base_next = 0;
@@ -236,7 +253,7 @@ __global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArg
     if constexpr (PRE) {
       if (pre) load_prow<T, NA>(a, row, pr);
     }
-    const T sum = sell_row<T>(A.col, A.val, a.x, base, w);
+    const T sum = sell_row<T, XL>(A.col, A.val, a.x, base, w);
     if (pos < A.n) {
       const T yv = a.b ? (T)(a.b[row] - sum) : sum;
       a.y[row] = yv;
@@ -250,6 +267,16 @@ __global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArg
       }
     }
   }
+}
+
+// NP < 0: plain product; NP >= 0: also the reduction of up to NP dots with P,
+// y.y and b.b, and the epilogue.
+template <typename T, int NP>
+__global__ void __launch_bounds__(SNT, 1) spmv_sell_kernel(SellMat<T> A, SpmvArgs<T> a) {
+  constexpr int NA = NP < 0 ? 0 : NP;
+  DotAcc<T, NA> acc;
+  acc.zero();
+  sell_pass<T, NP, 0>(A, a, acc, gridDim.x);
   if constexpr (NP >= 0) finish<T, NA>(a, acc);
 }
 
@@ -340,6 +367,217 @@ template cudaError_t spmv<double>(const Ctx&, const MatDesc&, const double*, dou
                                   const double*);
 template cudaError_t spmv<float>(const Ctx&, const MatDesc&, const float*, float*, const float*, const float*,
                                  int64_t, int, int, int, double*, Epi, const float*, int, const float*);
+
+// ---------------------------------------------------------------------------
+// Persistent level step: one cooperative launch runs, for level k of a cycle
+// of Algorithm 1,
+//   the gamma step on the top level      r^(k) -= V^(k) gamma_k,
+//   the product                          r^(k+1) = A r^(k) and P^T r^(k+1),
+//   for q = 0 .. s-1: the eta step       v_q^(k) = r^(k+1) - W^(k) eta_q,
+//                     the product        v_q^(k+1) = A v_q^(k) and P^T v_q^(k+1),
+// with every small solve (eta_q, then gamma_{k+1}) between them.  The updates
+// of the levels below k stay with lazy_update.  One 1024-thread block per SM;
+// the blocks meet at bounded grid barriers: after each vector update (the
+// product reads other blocks' rows) and after each product's per-block
+// partial sums, which every block then sums itself in the fixed order of the
+// standalone product's last block, and solves the next s x s system itself.
+// So no block waits on a single block's reduction and solve at the end of a
+// product, and no launch separates the steps.  The products use the grid and
+// slice-to-warp map of the standalone product (their first nb_prod blocks),
+// the vector updates the formulas of the standalone kernels: the results are
+// those of the per-kernel path bit for bit.  Vectors written during the
+// launch are read through L2, except x of a product (see xload).  Block 0
+// stores the projections and coefficients in the device state for the
+// kernels that follow.
+// ---------------------------------------------------------------------------
+template <typename T>
+struct LevelStepArgs {
+  SellMat<T> A;
+  T* R;              // r^(0..l), leading dimension ld
+  T* V;              // V^(-1..l): v_q^(i) at column (i + 1) s + q
+  int64_t ld;
+  int n, s, k;
+  int next_gamma;    // solve gamma_{k+1} at the end (k + 1 < l)
+  int nb_prod;       // blocks of the products (the standalone product's grid)
+  const T* P;
+  int64_t ldp;
+  const T* Pil;
+  int sp;
+  const T* Pb;
+  DevState* st;
+  double* partials;  // [nb_prod][MAXRED]
+  unsigned int* bar; // barrier counter, zero at launch
+  int* flag;
+  long long spin_limit;
+};
+
+// out[row] = base[row] - sum_j c[j] col_j[row] over the rows of this thread
+// (grid-stride over all blocks), j in column order: the formula of the
+// standalone gamma and eta kernels.
+template <typename T, int S, typename ColOf>
+__device__ __forceinline__ void level_combine(int n, int s, const T* base, T* out, const T* c, ColOf col_of) {
+  const int G = gridDim.x * SNT;
+  for (int row = blockIdx.x * SNT + threadIdx.x; row < n; row += G) {
+    T acc = __ldcg(base + row);
+    T v[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+      v[j] = __ldcg(col_of(j) + row);
+    }
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+      acc = acc - c[j] * v[j];
+    }
+    out[row] = acc;
+  }
+}
+
+// One product of the level step: y = A x with P^T y, this block's partial sums
+// published, a grid barrier, and the sums of all partials in red (every block).
+template <typename T, int NP>
+__device__ __forceinline__ bool level_product(const LevelStepArgs<T>& L, const T* x, T* y, unsigned int& gen,
+                                              double* smem_w, double* red, int* s_ok) {
+  constexpr int M = pow2_at_least(NP + 2);
+  const int s = L.s;
+  if (blockIdx.x < L.nb_prod) {
+    SpmvArgs<T> a{x, y, nullptr, L.P, L.ldp, s, 0, 0, nullptr, Epi{EPI_NONE, 0, 0, s, 0, nullptr},
+                  RedScratch{nullptr, nullptr, nullptr, 0}, L.Pil, L.sp, L.Pb};
+    DotAcc<T, NP> acc;
+    acc.zero();
+    sell_pass<T, NP, 1>(L.A, a, acc, L.nb_prod);
+    double fin[M];
+#pragma unroll
+    for (int i = 0; i < M; ++i) fin[i] = (i < NP && i < s) ? acc.get(i < NP ? i : 0) : 0.0;
+    if constexpr (M > 8) {
+      if (s <= 8)
+        block_reduce<8>(reinterpret_cast<double(&)[8]>(fin), s, smem_w, red);
+      else
+        block_reduce<M>(fin, s, smem_w, red);
+    } else {
+      block_reduce<M>(fin, s, smem_w, red);
+    }
+    if (threadIdx.x < s) L.partials[(size_t)blockIdx.x * MAXRED + threadIdx.x] = red[threadIdx.x];
+  }
+  if (!grid_sync(L.bar, ++gen, L.flag, L.spin_limit, s_ok)) return false;
+  sum_partials(L.partials, L.nb_prod, s, red);
+  return true;
+}
+
+// The s x s solve of the epilogues by warp 0: (P^T W) z = rhs with column j of
+// P^T W from hi (j < q) or lo (j >= q), [j][c] layout with stride SMAX.
+__device__ __forceinline__ bool level_solve(const double* lo, const double* hi, const double* rhs, int s, int q,
+                                            EpiScratch& w) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < s * s; i += 32) {
+    const int c = i / s, j = i % s;
+    w.a[i] = (j < q ? hi : lo)[j * SMAX + c];
+  }
+  if (lane < s) w.z[lane] = rhs[lane];
+  __syncwarp();
+  return warp_lu_solve(w.a, w.z, s, w.l);
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(SNT, 1) level_kernel(LevelStepArgs<T> L) {
+  __shared__ double smem_w[SNWARP * MAXRED];
+  __shared__ double red[MAXRED];
+  __shared__ double pv_lo[SMAX * SMAX];   // P^T V^(k):   [q][c]
+  __shared__ double pv_hi[SMAX * SMAX];   // P^T V^(k+1): [q][c], as the products complete
+  __shared__ double pr_hi[SMAX];          // P^T r^(k+1)
+  __shared__ T coef[SMAX];                // gamma_k, then eta_q
+  __shared__ EpiScratch ew;
+  __shared__ int s_ok;
+  const int s = L.s, k = L.k, n = L.n;
+  const int64_t ld = L.ld;
+  DevState* st = L.st;
+  unsigned int gen = 0;
+  for (int i = threadIdx.x; i < s * s; i += SNT)
+    pv_lo[(i / s) * SMAX + (i % s)] = __ldcg(&st->projV[(k * SMAX + i / s) * SMAX + (i % s)]);
+  if (threadIdx.x < s) coef[threadIdx.x] = (T)__ldcg(&st->gamma[k * SMAX + threadIdx.x]);
+  __syncthreads();
+  T* rk = L.R + (int64_t)k * ld;
+  T* rk1 = L.R + (int64_t)(k + 1) * ld;
+  T* Vk = L.V + (int64_t)(k + 1) * s * ld;    // V^(k)
+  T* Vk1 = L.V + (int64_t)(k + 2) * s * ld;   // V^(k+1)
+  // gamma step on the top level
+  level_combine<T, NP>(n, s, rk, rk, coef, [&](int j) { return Vk + (int64_t)j * ld; });
+  if (!grid_sync(L.bar, ++gen, L.flag, L.spin_limit, &s_ok)) return;
+  // r^(k+1) = A r^(k), P^T r^(k+1)
+  if (!level_product<T, NP>(L, rk, rk1, gen, smem_w, red, &s_ok)) return;
+  if (threadIdx.x < s) {
+    pr_hi[threadIdx.x] = red[threadIdx.x];
+    if (blockIdx.x == 0) st->projR[(k + 1) * SMAX + threadIdx.x] = red[threadIdx.x];
+  }
+  __syncthreads();
+  for (int q = 0; q < s; ++q) {
+    // eta_q: (P^T W^(k)) eta_q = P^T r^(k+1), W^(k) = [V^(k+1)_{0:q-1}, V^(k)_{q:s-1}]
+    if (threadIdx.x < 32) {
+      const bool ok = level_solve(pv_lo, pv_hi, pr_hi, s, q, ew);
+      if (threadIdx.x < s) {
+        coef[threadIdx.x] = (T)ew.z[threadIdx.x];
+        if (blockIdx.x == 0) st->eta[(k * SMAX + q) * SMAX + threadIdx.x] = ew.z[threadIdx.x];
+      }
+      if (threadIdx.x == 0 && blockIdx.x == 0 && !ok) atomicOr(&st->flag, FLAG_BREAKDOWN);
+    }
+    __syncthreads();
+    // v_q^(k) = r^(k+1) - W^(k) eta_q
+    level_combine<T, NP>(n, s, rk1, Vk + (int64_t)q * ld, coef,
+                         [&](int j) { return (j < q ? Vk1 : Vk) + (int64_t)j * ld; });
+    if (!grid_sync(L.bar, ++gen, L.flag, L.spin_limit, &s_ok)) return;
+    // v_q^(k+1) = A v_q^(k), P^T v_q^(k+1)
+    if (!level_product<T, NP>(L, Vk + (int64_t)q * ld, Vk1 + (int64_t)q * ld, gen, smem_w, red, &s_ok)) return;
+    if (threadIdx.x < s) {
+      pv_hi[q * SMAX + threadIdx.x] = red[threadIdx.x];
+      if (blockIdx.x == 0) st->projV[((k + 1) * SMAX + q) * SMAX + threadIdx.x] = red[threadIdx.x];
+    }
+    __syncthreads();
+  }
+  // gamma_{k+1}: (P^T V^(k+1)) gamma = P^T r^(k+1), for the next level step
+  if (L.next_gamma && blockIdx.x == 0 && threadIdx.x < 32) {
+    const bool ok = level_solve(pv_hi, pv_hi, pr_hi, s, 0, ew);
+    if (threadIdx.x < s) st->gamma[(k + 1) * SMAX + threadIdx.x] = ew.z[threadIdx.x];
+    if (threadIdx.x == 0 && !ok) atomicOr(&st->flag, FLAG_BREAKDOWN);
+  }
+}
+
+template <typename T, int NP>
+static cudaError_t launch_level(const Ctx& c, LevelStepArgs<T>& L) {
+  static int nb = -1;
+  if (nb < 0) {
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, level_kernel<T, NP>, SNT, 0) != cudaSuccess) nb = 0;
+  }
+  if (nb < 1) return cudaErrorCooperativeLaunchTooLarge;
+  void* args[] = {&L};
+  return cudaLaunchCooperativeKernel((const void*)level_kernel<T, NP>, dim3(c.sms), dim3(SNT), args, 0, c.stream);
+}
+
+template <typename T>
+cudaError_t level_step(const Ctx& c, const MatDesc& A, T* R, T* V, int64_t ld, int s, int k, int next_gamma,
+                       const T* P, int64_t ldp, const T* Pil, int sp, const T* Pb, DevState* st,
+                       unsigned int* bar, long long spin_limit) {
+  if (A.format != 0 || s < 1 || s > SMAX || c.sms > MAXBLK) return cudaErrorInvalidValue;
+  // the grid of the standalone product (launch_sell): min(slices' rows / SNT, SMs)
+  const int64_t need = ((int64_t)A.nslices * 32 + SNT - 1) / SNT;
+  const int nb_prod = (int)(need < c.sms ? need : c.sms);
+  const T* pb = (Pb && !A.perm) ? Pb : nullptr;
+  LevelStepArgs<T> L{SellMat<T>{A.n, A.nslices, A.slice_ptr, A.slice_w, A.perm, A.scol, pick_val<T>(A, true)},
+                 R, V, ld, A.n, s, k, next_gamma, nb_prod, P, ldp, Pil, sp, pb, st, c.rs.partials, bar,
+                 &st->flag, spin_limit};
+  cudaError_t e = cudaMemsetAsync(bar, 0, sizeof(unsigned int), c.stream);
+  if (e != cudaSuccess) return e;
+  if (s <= 4) return launch_level<T, 4>(c, L);
+  if (s <= 8) return launch_level<T, 8>(c, L);
+  return launch_level<T, 16>(c, L);
+}
+
+template cudaError_t level_step<double>(const Ctx&, const MatDesc&, double*, double*, int64_t, int, int, int,
+                                        const double*, int64_t, const double*, int, const double*, DevState*,
+                                        unsigned int*, long long);
+template cudaError_t level_step<float>(const Ctx&, const MatDesc&, float*, float*, int64_t, int, int, int,
+                                       const float*, int64_t, const float*, int, const float*, DevState*,
+                                       unsigned int*, long long);
 
 // y = z or b - z, row by row, with the fused reductions of the product.
 template <typename T, int NP>

@@ -23,7 +23,7 @@ PREC_FP64, PREC_FP32_INNER = 0, 1
 FETCH_ONCE, FETCH_EVERY, FETCH_NEVER, FETCH_SLOPE, FETCH_PROBE = 0, 1, 2, 3, 4
 FORMAT_SELL, FORMAT_CSR = 0, 1
 PRECOND_NONE, PRECOND_ILU0 = 0, 1
-KERNEL_FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond"]
+KERNEL_FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond", "level"]
 
 
 class Options(ctypes.Structure):
@@ -42,8 +42,9 @@ class Options(ctypes.Structure):
         ("inner_ell", ctypes.c_int32),
         ("replace_every", ctypes.c_int32),
         ("precond", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("persistent", ctypes.c_int32),
         ("stream", ctypes.c_void_p),
+        ("spin_limit", ctypes.c_int64),
     ]
 
 
@@ -64,8 +65,8 @@ class Stats(ctypes.Structure):
         ("fp64_finish", ctypes.c_int32),
         ("fetch_at", ctypes.c_int32),
         ("relres_orig", ctypes.c_double),
-        ("t_ms", ctypes.c_double * 9),
-        ("n_launch", ctypes.c_int64 * 9),
+        ("t_ms", ctypes.c_double * 10),
+        ("n_launch", ctypes.c_int64 * 10),
     ]
 
     def as_dict(self):
@@ -93,6 +94,7 @@ _SIGS = {
     "msstab_last_error": (ctypes.c_char_p, [_P]),
     "msstab_history": (_I32, [_P, _P, _P, _I32, ctypes.POINTER(_I32)]),
     "msstab_reset_recycle": (_I32, [_P]),
+    "msstab_set_spin_limit": (_I32, [_P, _I64]),
     "msstab_has_recycle": (_I32, [_P, ctypes.POINTER(_I32)]),
     "msstab_export_recycle": (_I32, [_P, _P, _P]),
     "msstab_import_recycle": (_I32, [_P, _P, _P]),
@@ -194,7 +196,7 @@ class Solver:
     random basis of P, shape (s, n).  Keyword arguments set msstab_options
     fields (precision, fetch_policy, fetch_threshold, fetch_cycle, orth_recycle,
     max_mvs, inner_tol, spmv_format, sell_sigma, kernel_timing, max_outer,
-    inner_ell, replace_every, precond).
+    inner_ell, replace_every, precond, persistent, spin_limit).
     """
 
     def __init__(self, A, s: int, ell: int, p_raw, device: str = "cuda", stream=None, **options):
@@ -274,6 +276,19 @@ class Solver:
         mv = np.zeros(cnt.value, dtype=np.int64)
         load().msstab_history(self._h, rel.ctypes.data, mv.ctypes.data, cnt.value, ctypes.byref(cnt))
         return rel, mv
+
+    def set_spin_limit(self, polls: int):
+        _check(load().msstab_set_spin_limit(self._h, int(polls)), self._h)
+
+    def solve_rc(self, b, x, tol: float = 1e-8):
+        """As solve, returning (status code, Stats) instead of raising."""
+        st = Stats()
+        rc = load().msstab_solve(self._h, _ptr(b), _ptr(x), float(tol), ctypes.byref(st))
+        return rc, st
+
+    def last_error(self) -> str:
+        m = load().msstab_last_error(self._h)
+        return m.decode() if m else ""
 
     def reset_recycle(self):
         _check(load().msstab_reset_recycle(self._h), self._h)

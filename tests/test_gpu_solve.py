@@ -315,18 +315,26 @@ def test_solve_host_matches_device(M):
     assert st1.mvs == st2.mvs
 
 
-def test_kernel_timing_and_launch_counts(M):
+@pytest.mark.parametrize("persistent", [0, 1])
+def test_kernel_timing_and_launch_counts(M, persistent):
     w = pb.WORKLOADS["convdiff3d_24"]
     A = w.matrix()
-    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, kernel_timing=1)
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, kernel_timing=1, persistent=persistent)
     x = _t(w.x0())
     st = S.solve(_t(w.x0() / w.tau + w.f()), x, w.tol)
     d = st.as_dict()
     assert d["launches"] == sum(d["n_launch"].values())
-    per_cycle = w.ell * (2 + 2 * w.s + 1) + 2
-    assert d["n_launch"]["spmv_dot"] == st.cycles * w.ell * (w.s + 1)
-    assert d["launches"] >= st.cycles * per_cycle
-    assert all(v >= 0 for v in d["t_ms"].values()) and d["t_ms"]["spmv_dot"] > 0
+    if persistent:
+        # one level-step launch and one lazy update per level step
+        assert d["n_launch"]["level"] == st.cycles * w.ell and d["n_launch"]["lazy"] == st.cycles * w.ell
+        assert d["n_launch"]["eta"] == 0 and d["n_launch"]["gamma"] == 0
+        assert d["t_ms"]["level"] > 0
+    else:
+        per_cycle = w.ell * (2 + 2 * w.s + 1) + 2
+        assert d["n_launch"]["spmv_dot"] == st.cycles * w.ell * (w.s + 1)
+        assert d["launches"] >= st.cycles * per_cycle
+        assert d["t_ms"]["spmv_dot"] > 0
+    assert all(v >= 0 for v in d["t_ms"].values())
 
 
 def test_zero_rhs(M):
@@ -478,3 +486,84 @@ def test_block_partitioned_cut_space_matches_oracle(M):
         assert _mvs_match(gs, os_, w.tol), (i, mvs, os_.mvs, hist, os_.history)
         assert np.linalg.norm(xg - os_.x) <= 1e-6 * np.linalg.norm(os_.x)
         xprev = xg
+
+
+def _sequence_with_history(M, w, A, steps, **opt):
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, **opt)
+    f = _t(w.f())
+    x = _t(w.x0())
+    b = torch.empty_like(x)
+    out = []
+    for _ in range(steps):
+        S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
+        st = S.solve(b, x, w.tol)
+        out.append((st.mvs, st.cycles, x.clone(), S.history()[0], st.launches))
+    S.close()
+    return out
+
+
+@pytest.mark.parametrize("wl,form", [("convdiff2d_32", "fp64"), ("convdiff3d_33", "fp64"),
+                                     ("convdiff3d_33", "fp64_replace"), ("convdiff3d_33", "fp32_inner")])
+def test_persistent_level_step_is_the_per_kernel_path_bit_for_bit(M, wl, form):
+    # the persistent level kernel runs the same products (grid, slice map,
+    # summation order), updates and small solves as the per-kernel launches
+    w = pb.WORKLOADS[wl]
+    A = w.matrix()
+    opt = {"fp64": {}, "fp64_replace": dict(replace_every=1),
+           "fp32_inner": dict(precision=M.PREC_FP32_INNER, inner_ell=1, fetch_policy=M.FETCH_NEVER)}[form]
+    a = _sequence_with_history(M, w, A, 3, persistent=1, **opt)
+    b = _sequence_with_history(M, w, A, 3, persistent=0, **opt)
+    for (ma, ca, xa, ha, la), (mb, cb, xb, hb, lb) in zip(a, b):
+        assert ma == mb and ca == cb
+        assert np.array_equal(ha, hb)
+        assert torch.equal(xa, xb)
+        assert la < lb                      # fewer launches per solve
+
+
+def test_persistent_level_step_128_first_systems_bit_for_bit(M):
+    w = pb.WORKLOADS["convdiff3d_128"]
+    A = w.matrix()
+    a = _sequence_with_history(M, w, A, 2, persistent=1, replace_every=1)
+    b = _sequence_with_history(M, w, A, 2, persistent=0, replace_every=1)
+    for (ma, ca, xa, ha, la), (mb, cb, xb, hb, lb) in zip(a, b):
+        assert ma == mb and np.array_equal(ha, hb) and torch.equal(xa, xb)
+
+
+def test_device_wait_runs_out_and_the_handle_recovers(M):
+    # failure detection without a fault: a wait limit of one poll makes the
+    # grid barriers of the persistent level step give up; every block leaves,
+    # the call returns MSSTAB_ERR_CUDA with x untouched, and the same handle
+    # solves normally once the limit is back to its default
+    w = pb.WORKLOADS["convdiff3d_33"]
+    A = w.matrix()
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, spin_limit=1)
+    x0 = w.x0()
+    b = _t(x0 / w.tau + w.f())
+    x = _t(x0)
+    rc, st = S.solve_rc(b, x, w.tol)
+    assert rc == M.ERR_CUDA and "timed out" in S.last_error()
+    assert np.array_equal(x.cpu().numpy(), x0)
+    S.set_spin_limit(0)
+    rc, st = S.solve_rc(b, x, w.tol)
+    assert rc == M.OK and st.relres_true <= w.tol
+    S.close()
+
+
+def test_ilu_sweep_wait_runs_out_and_the_handle_recovers(M):
+    # the chunked ILU(0) sweeps wait on values of the neighbouring chunks
+    w = pb.WORKLOADS["convdiff3d_33"]
+    A = w.matrix()
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, precond=M.PRECOND_ILU0, replace_every=1,
+                 fetch_policy=M.FETCH_NEVER)
+    assert S.op_ilu_levels()[4] > 1                 # several chunks: waits across blocks
+    x0 = w.x0()
+    b = _t(x0 / w.tau + w.f())
+    x = _t(x0)
+    S.set_spin_limit(1)
+    rc, st = S.solve_rc(b, x, w.tol)
+    assert rc == M.ERR_CUDA and "timed out" in S.last_error()
+    assert np.array_equal(x.cpu().numpy(), x0)
+    S.set_spin_limit(0)
+    rc, st = S.solve_rc(b, x, w.tol)
+    assert rc == M.OK and st.relres_true <= w.tol
+    S.close()
