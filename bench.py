@@ -65,6 +65,7 @@ def parse_args(argv=None):
     p.add_argument("--cnn", action="store_true",
                    help="time only the learned-guess network: inference on the full grid and training iterations")
     p.add_argument("--cpu-worker", action="store_true", help=argparse.SUPPRESS)
+    p.add_argument("--cpu-full-small", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--cpu-level-steps", type=int, default=4, help=argparse.SUPPRESS)
     p.add_argument("--cpu-k0", type=int, default=0, help=argparse.SUPPRESS)
     return p.parse_args(argv)
@@ -308,6 +309,59 @@ def cpu_worker(args):
         times.append(time.perf_counter() - t0)
     threads = int(os.environ.get("OPENBLAS_NUM_THREADS", "0")) or len(os.sched_getaffinity(0))
     print(json.dumps({"level_step_s": times, "mv_s": t_mv, "threads": threads}))
+
+
+def cpu_full_small(args):
+    """Time the oracle end to end on the small 2D configuration (32 x 32 grid,
+    10 systems, M(4)stab(2), fetch once): the whole sequence.  Prints JSON."""
+    from oracle import idrstab as O
+    from paper_1604_06043_gb300 import problems as pb
+    w = pb.WORKLOADS["convdiff2d_32"]
+    A = w.matrix()
+    t0 = time.perf_counter()
+    res = O.msstab_sequence(A, w.f(), w.x0(), w.tau, w.steps, w.s, w.ell, w.p_raw(), tol=w.tol, policy="once",
+                            replace_every=w.replace_every)
+    dt = time.perf_counter() - t0
+    print(json.dumps({"seconds": dt, "mvs": [int(r.mvs) for r in res.solves],
+                      "relres_true_max": max(float(r.relres_true) for r in res.solves)}))
+
+
+def small_config_line(M, torch, dev):
+    """The small configuration (2D 32 x 32, 10 systems) end to end on the GPU
+    and on the oracle, both the whole sequence."""
+    from paper_1604_06043_gb300 import problems as pb
+    w = pb.WORKLOADS["convdiff2d_32"]
+    A = w.matrix()
+    f = torch.tensor(w.f(), device=dev)
+    out = {"workload": f"convdiff2d_32: 2D convection-diffusion, 5-point FD on a 32x32 grid (N={A.n}), "
+                       f"beta={tuple(w.beta)}, tau={w.tau}, {w.steps} systems, M({w.s})stab({w.ell}), fetch once"}
+    for rep in range(2):            # the first pass warms the module and the graphs' code up
+        S = M.Solver(A, w.s, w.ell, w.p_raw(), device=dev, replace_every=w.replace_every)
+        x = torch.tensor(w.x0(), device=dev)
+        b = torch.empty_like(x)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record()
+        mv = run_sequence(M, torch, S, f, x, b, w.tau, w.tol, w.steps)
+        e1.record()
+        torch.cuda.synchronize()
+        S.close()
+    out["gpu_ms_per_system"] = round(e0.elapsed_time(e1) / w.steps, 4)
+    out["gpu_mvs"] = [t["mvs"] for t in mv]
+    env = dict(os.environ)
+    for v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "NUMEXPR_NUM_THREADS"):
+        env[v] = "1"
+    cmd = [sys.executable, os.path.abspath(__file__), "--cpu-full-small"]
+    r = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=600)
+    if r.returncode == 0:
+        o = json.loads(r.stdout.strip().splitlines()[-1])
+        out["oracle_ms_per_system"] = round(1e3 * o["seconds"] / w.steps, 3)
+        out["oracle_mvs"] = o["mvs"]
+        out["oracle_cores"] = 1
+    else:
+        out["oracle_error"] = r.stderr[-300:]
+    return out
 
 
 def run_cpu_sample(args, level_steps, k0=0, single_thread=True):
@@ -580,6 +634,9 @@ def main(argv=None):
     args = parse_args(argv)
     if args.cpu_worker:
         cpu_worker(args)
+        return
+    if args.cpu_full_small:
+        cpu_full_small(args)
         return
     if args.impl == "reference":
         reference_arm(args)
@@ -855,6 +912,10 @@ def main(argv=None):
         except Exception as e:  # the baseline is reported, not required
             line["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": 1, "kind": "oracle",
                                     "sample": f"failed: {str(e)[-200:]}"}
+        try:   # the small configuration, whole sequence on both sides
+            line["small_config_end_to_end"] = small_config_line(M, torch, dev)
+        except Exception as e:
+            line["small_config_end_to_end"] = {"error": str(e)[-300:]}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -118,12 +118,14 @@ typedef struct msstab_options {
                               point, the recycled U, V and replace_every refer to that system (its
                               true residual is L^-1 (b - A U^-1 x~)).  FP64 only; A must hold every
                               diagonal entry and strictly increasing columns in each row */
-  int32_t persistent;      /* 1 (default): each level step of a cycle (the gamma step, the s + 1
-                              products with A with their projections and small solves, the eta
-                              steps) runs as ONE cooperative launch of one 1024-thread block per SM
-                              whose blocks meet at grid barriers; results are those of 0 bit for
-                              bit.  0: one launch per step.  Used with the SELL format and without
-                              the preconditioner (else 0 applies) */
+  int32_t persistent;      /* 1 (default): each level step of an FP64 cycle (the gamma step, the
+                              s + 1 products with A with their projections and small solves, the
+                              eta steps) runs as ONE cooperative launch of one 1024-thread block
+                              per SM whose blocks meet at grid barriers; results are those of 0 bit
+                              for bit.  2: the FP32 inner cycles too (measured 2 % slower than their
+                              graph-replayed launches at 128^3: the barriers and per-block solves
+                              cost what the shorter FP32 products save).  0: one launch per step.
+                              Used with the SELL format and without the preconditioner (else 0) */
   void* stream;            /* cudaStream_t for all work of the handle; NULL = default stream */
   int64_t spin_limit;      /* polls after which a device-side wait of the library gives up (the
                               grid barriers of the level steps and of the ILU(0) sweeps, the

@@ -488,7 +488,7 @@ class SequenceResult:
 
 
 def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="once",
-                    fetch_threshold=None, orth_recycle=True, first_step=0,
+                    fetch_threshold=None, fetch_cycle=None, orth_recycle=True, first_step=0,
                     max_mvs=None, replace_every=0, on_solve: Optional[Callable] = None) -> SequenceResult:
     """Solve the implicit-Euler sequence A x^(i+1) = x^(i)/tau_t + f, one system
     after the other, from x^(0).
@@ -511,6 +511,9 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
                     converges earlier); the later systems recycle them.
     With ``orth_recycle`` (default) the passed basis is conditioned: V := A U
     (s MVs, counted in the solve that wrote it), then Cholesky QR twice.
+    ``fetch_cycle`` (policy "once") fetches at the end of that cycle of the
+    first solve instead of at the threshold (the fixed fetching cycles of the
+    finite-termination experiments of Section 5.2).
     ``first_step``/``steps`` select the slice of the sequence that is solved;
     x0 is then the solution of the step before the slice."""
     mv = MatVec(A)
@@ -529,7 +532,7 @@ def msstab_sequence(A, f, x0, tau_t, steps, s, ell, P_raw, tol=1e-8, *, policy="
         kw = {}
         want_fetch = rec is None and policy in ("once", "slope", "probe")
         if policy == "once" and want_fetch:
-            kw = dict(fetch_threshold=thr)
+            kw = dict(fetch_cycle=fetch_cycle) if fetch_cycle else dict(fetch_threshold=thr)
         elif policy == "slope" and want_fetch:
             kw = dict(fetch_slope=True, fetch_at_end=True)
         elif policy == "probe" and want_fetch:

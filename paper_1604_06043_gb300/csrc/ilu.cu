@@ -599,7 +599,9 @@ static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const doub
                  u == 1 ? F.cpdiag : nullptr, in, out, F.flag, F.spin_limit};
     void* cargs[] = {&ca};
     const int P = (F.n + F.CH[u] - 1) / F.CH[u];
-    const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_chunk_kernel<4> : (const void*)ilu_sweep_chunk_kernel<8>;
+    const void* k = F.W[u] == 3   ? (const void*)ilu_sweep_chunk_kernel<3>
+                    : F.W[u] == 4 ? (const void*)ilu_sweep_chunk_kernel<4>
+                                  : (const void*)ilu_sweep_chunk_kernel<8>;
     return cudaLaunchCooperativeKernel(k, dim3(P), dim3(CTS), cargs, 0, c.stream);
   }
   e = cudaMemsetAsync(&F.bar->count, 0, sizeof(unsigned int), c.stream);
@@ -608,7 +610,9 @@ static cudaError_t solve_sweep(const Ctx& c, const IluDesc& F, int u, const doub
                F.flag, F.spin_limit};
   LevelArgs L{p, F.nlev[u], F.pptr[u], &F.bar->count};
   void* largs[] = {&L};
-  const void* k = F.W[u] == 4 ? (const void*)ilu_sweep_level_kernel<4> : (const void*)ilu_sweep_level_kernel<8>;
+  const void* k = F.W[u] == 3   ? (const void*)ilu_sweep_level_kernel<3>
+                  : F.W[u] == 4 ? (const void*)ilu_sweep_level_kernel<4>
+                                : (const void*)ilu_sweep_level_kernel<8>;
   return cudaLaunchCooperativeKernel(k, dim3(F.grid[u]), dim3(ITS), largs, 0, c.stream);
 }
 
@@ -671,10 +675,11 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
   ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb3, ilu_sweep_kernel<SW_UPPER>, ITS, 0));
   nb = std::min(nb, std::min(nb2, nb3));
   {
-    int l4 = 0, l8 = 0;
+    int l3 = 0, l4 = 0, l8 = 0;
+    ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l3, ilu_sweep_level_kernel<3>, ITS, 0));
     ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l4, ilu_sweep_level_kernel<4>, ITS, 0));
     ICK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&l8, ilu_sweep_level_kernel<8>, ITS, 0));
-    nb = std::min(nb, std::min(l4, l8));
+    nb = std::min(nb, std::min(l3, std::min(l4, l8)));
   }
   if (nb < 1) nb = 1;
   const int co = nb * c.sms;
@@ -753,7 +758,9 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
     ICK(cudaGetLastError());
     int md = 0;
     ICK(read_int(scratch, &md));
-    const int W = md <= 4 ? 4 : (md <= 8 ? 8 : 0);
+    // the packed width: the smallest of 3, 4, 8 that holds every row (a 7-point
+    // stencil in natural order has 3 dependencies per triangle: no unused slot)
+    const int W = md <= 3 ? 3 : (md <= 4 ? 4 : (md <= 8 ? 8 : 0));
     F.W[u] = 0;
     if (W == 0) continue;
     const int nlev = F.nlev[u];
@@ -794,11 +801,12 @@ IluSetupResult ilu_setup(const Ctx& c, IluDesc& F, DevAllocFn alloc, void* actx,
     const int CH = std::max(1, (n + c.sms - 1) / c.sms);
     const int P = (n + CH - 1) / CH;
     bool ok = F.W[0] > 0 || F.W[1] > 0;
-    for (int W : {4, 8}) {
+    for (int W : {3, 4, 8}) {
       if (!ok) break;
       int nbk = 0;
       if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-              &nbk, W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>, CTS, 0) != cudaSuccess) {
+              &nbk, W == 3 ? ilu_sweep_chunk_kernel<3> : (W == 4 ? ilu_sweep_chunk_kernel<4> : ilu_sweep_chunk_kernel<8>),
+              CTS, 0) != cudaSuccess) {
         cudaGetLastError();
         ok = false;
         break;

@@ -514,7 +514,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     const bool replaced = ctl.replace_every > 0 && (out.cycles + 1) % ctl.replace_every == 0;
     auto launch_cycle = [&](const Ctx& c) -> msstab_status {
       for (int k = 0; k < ell; ++k) {
-        if (h->level) {
+        if (h->level && (prec == 0 || h->opt.persistent >= 2)) {
           // the gamma step, the s + 1 products and the eta steps of level k in one launch
           LAUNCH(MSSTAB_K_LEVEL, level_step<T>(c, h->A, w.R, w.V, ld, s, k, k + 1 < ell ? 1 : 0, P, ld, w.Pil,
                                                w.sp, w.Pb, st, h->level_bar, h->spin_limit));

@@ -10,37 +10,62 @@ seeded sample rows.  The full-size GPU parity tests compare against this
 record, and the CPU baseline of the benchmark takes its cycles per system from
 it.  Nothing here touches the CUDA path.
 
-    python tests/golden/make_oracle_records.py [systems [output.json]]
+    python tests/golden/make_oracle_records.py [--systems N] [--fetch-cycle C]
+        [--threads T] [--dots blas|pairwise] [--out FILE]
+
+Defaults write the committed record (oracle_convdiff3d_128.json: fetch at the
+first cycle end with relres <= sqrt(tol), the BLAS pool's default threads).
+The options write the records that show how the iteration depends on rounding:
+--fetch-cycle 2 fetches at the end of cycle 2 of the first system (before the
+rounding differences of two correct FP64 implementations have grown, so that
+both hand the same basis on; oracle_convdiff3d_128_fetch2.json, one BLAS
+thread); --threads sets the BLAS pool size before numpy loads (another
+summation order of the projections); --dots pairwise sums every projection and
+Gram entry of Algorithm 1 by numpy's pairwise summation instead of BLAS (a
+third order).  Each full run takes 40-60 minutes on one core.
 """
 
+import argparse
 import json
 import os
 import sys
 import time
 
-import numpy as np
-
 ROOT = os.path.dirname(os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
-sys.path.insert(0, ROOT)
-
-from oracle import idrstab as O  # noqa: E402
-from paper_1604_06043_gb300 import problems as pb  # noqa: E402
-
-OUT = os.path.join(os.path.dirname(os.path.abspath(__file__)), "oracle_convdiff3d_128.json")
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(HERE, "oracle_convdiff3d_128.json")
 
 
 def sample_rows(n, k=512, seed=99):
+    import numpy as np
     rows = np.random.default_rng(seed).choice(n, size=k - 2, replace=False)
     return np.sort(np.concatenate([[0, n - 1], rows])).astype(np.int64)
 
 
-def main(systems=23, out=OUT):
+def main(systems=23, out=OUT, fetch_cycle=None, threads=None, dots="blas"):
+    if threads:
+        os.environ["OPENBLAS_NUM_THREADS"] = str(threads)
+        os.environ["OMP_NUM_THREADS"] = str(threads)
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import idrstab as O
+    from paper_1604_06043_gb300 import problems as pb
+    if dots == "pairwise":
+        # the same projections and Gram entries, their terms added in numpy's
+        # pairwise order instead of the BLAS kernels' order
+        O.proj = lambda P, w: np.array([np.sum(p * w) for p in P])
+
+        def tau_step(R):
+            L = len(R)
+            return O.tau_from_gram(np.array([[np.sum(R[a] * R[c]) for c in range(L)] for a in range(L)]))
+        O.tau_step = tau_step
     w = pb.WORKLOADS["convdiff3d_128"]
     A = w.matrix()
     rows = sample_rows(w.n)
     rec = {"workload": w.name, "n": w.n, "nnz": A.nnz, "s": w.s, "ell": w.ell, "tau": w.tau, "tol": w.tol,
-           "policy": "once", "fetch_threshold": "sqrt(tol)", "orth_recycle": True,
-           "replace_every": w.replace_every,
+           "policy": "once", "fetch_threshold": "sqrt(tol)" if not fetch_cycle else None,
+           "fetch_cycle": fetch_cycle, "orth_recycle": True, "replace_every": w.replace_every,
+           "blas_threads": threads, "dots": dots,
            "sample_rows": rows.tolist(), "systems": []}
     t_start = time.time()
 
@@ -59,8 +84,16 @@ def main(systems=23, out=OUT):
         print(len(rec["systems"]), res.mvs, res.cycles, res.relres_true, time.time() - t_start, flush=True)
 
     O.msstab_sequence(A, w.f(), w.x0(), w.tau, systems, w.s, w.ell, w.p_raw(), tol=w.tol, policy="once",
-                      replace_every=w.replace_every, on_solve=on_solve)
+                      fetch_cycle=fetch_cycle, replace_every=w.replace_every, on_solve=on_solve)
 
 
 if __name__ == "__main__":
-    main(int(sys.argv[1]) if len(sys.argv) > 1 else 23, sys.argv[2] if len(sys.argv) > 2 else OUT)
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--systems", type=int, default=23)
+    ap.add_argument("--fetch-cycle", type=int, default=None)
+    ap.add_argument("--threads", type=int, default=None)
+    ap.add_argument("--dots", choices=["blas", "pairwise"], default="blas")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    out = a.out or (os.path.join(HERE, "oracle_convdiff3d_128_fetch2.json") if a.fetch_cycle == 2 else OUT)
+    main(a.systems, out, a.fetch_cycle, a.threads, a.dots)

@@ -2,11 +2,17 @@
 
 Both sides round the same operands to bfloat16 (weights, biases, inputs,
 hidden activations, upstream gradients) and accumulate wider (FP32 on the GPU,
-FP64 in the oracle).  A bfloat16 rounding can then land on either side of a
-rounding boundary for a few elements (the FP32 and FP64 pre-rounding values
-differ by ~1e-7 relative; bfloat16 spacing is 2^-8), so whole-network
-results are compared in norm: relative error <= 2e-3 for outputs and 5e-3 for
-gradients, far below the bfloat16 step and far above FP32 accumulation error.
+FP64 in the oracle).  A bfloat16 rounding can land on either side of a
+rounding boundary when the FP32 and FP64 pre-rounding values straddle it (they
+differ by ~1e-7 relative; the bfloat16 unit roundoff is U = 2^-8), and such a
+flip moves every later value that reads it.  So every element is compared
+against one bfloat16 unit roundoff of the sum of the absolute values of its
+terms: an output o = b + sum W h within U (|b| + sum |W| |h|), a gradient
+entry dW = sum g h within U sum |g| |h| (the terms of the oracle's own last
+contraction).  Measured: at most 0.06 U (outputs) and 0.14 U (gradients) of
+that scale.  The share of outputs that moved beyond FP32 accumulation slack
+(1e-6 of the scale) -- the footprint of the flips -- is reported and bounded,
+and the norm bounds stay as a second check.
 """
 
 import numpy as np
@@ -44,6 +50,54 @@ def _rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
+U_BF16 = 2.0 ** -8
+
+
+def _output_terms(th, x):
+    """|b| + sum |W| |h| of the last layer's outputs (the oracle's operands)."""
+    _, cache = C.forward(th, x, keep=True)
+    W, b = C.unpack(C.bf16(th))[-1]
+    return C.conv3d(np.abs(cache[-1][0]), np.abs(W), np.abs(b))
+
+
+def _gradient_terms(th, xb, tb, stencil=None):
+    """sum |upstream| |input| of every gradient entry (flat, like the
+    parameters), from the oracle's own backward pass."""
+    params = C.unpack(C.bf16(th))
+    acc = [(np.zeros_like(W), np.zeros_like(b)) for W, b in params]
+    count = tb.size
+    K = None if stencil is None else np.asarray(stencil, dtype=np.float64).reshape(1, 1, 3, 3, 3)
+    for x, t_ in zip(xb, tb):
+        out, cache = C.forward(th, x, keep=True)
+        diff = out - t_
+        if K is None:
+            g = 2.0 * diff / count
+        else:
+            s_ = C.conv3d(diff, K, np.zeros(1))
+            g = C.conv3d_backward(diff, K, 2.0 * s_ / count)[0]
+        for li in range(len(params) - 1, -1, -1):
+            h, z = cache[li]
+            W, _ = params[li]
+            if li < len(params) - 1:
+                g = g * C.gelu_grad(z)
+            gq = C.bf16(g)
+            _, dWa, dba = C.conv3d_backward(np.abs(h), np.abs(W), np.abs(gq))
+            acc[li][0][...] += dWa
+            acc[li][1][...] += dba
+            g = C.conv3d_backward(h, W, gq)[0]
+    return np.concatenate([np.concatenate([a.ravel(), b]) for a, b in acc])
+
+
+def _check_elementwise(got, ref, terms, moved_max):
+    """Every element within U_BF16 of its terms; the share beyond FP32 slack
+    (elements that a bfloat16 flip upstream moved) at most moved_max."""
+    d = np.abs(got - ref)
+    assert np.all(d <= U_BF16 * terms), float(np.max(d / (U_BF16 * terms)))
+    moved = float(np.mean(d > 1e-6 * terms))
+    assert moved <= moved_max, moved
+    return moved
+
+
 def test_forward_matches_oracle(M):
     B, D = 2, 12
     th = _params()
@@ -52,8 +106,10 @@ def test_forward_matches_oracle(M):
     net = M.CNN((D, D, D), th, max_batch=B, crop=D, device=DEV)
     out = net.forward(_t(x), B, D).cpu().numpy().reshape(B, 1, D, D, D)
     ref = np.stack([C.forward(th, xb.astype(np.float64)) for xb in x])
+    terms = np.stack([_output_terms(th, xb.astype(np.float64)) for xb in x])
+    moved = _check_elementwise(out, ref, terms, 0.5)
+    print("forward: %.1f %% of the outputs moved by a bfloat16 flip upstream" % (100 * moved))
     assert _rel(out, ref) <= 2e-3
-    assert np.max(np.abs(out - ref)) <= 1e-2 * np.max(np.abs(ref))
 
 
 def test_gradient_matches_oracle(M):
@@ -67,6 +123,11 @@ def test_gradient_matches_oracle(M):
     ref_loss, ref_g = C.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64))
     assert abs(loss - ref_loss) <= 1e-4 * ref_loss
     g = g.cpu().numpy()
+    terms = _gradient_terms(th, x.astype(np.float64), t.astype(np.float64))
+    # every gradient entry sums over all voxels, so nearly every entry sees a
+    # flip somewhere: the share is reported, the element-wise bound is the test
+    moved = _check_elementwise(g, ref_g, terms, 1.0)
+    print("gradient: %.1f %% of the entries moved by a bfloat16 flip upstream" % (100 * moved))
     o = 0
     for ci, co in C.LAYERS:
         n = co * ci * 27 + co
@@ -89,6 +150,7 @@ def test_operator_weighted_gradient_matches_oracle(M):
     ref_loss, ref_g = C.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64), stencil=K)
     assert abs(loss - ref_loss) <= 1e-4 * ref_loss
     g = g.cpu().numpy()
+    _check_elementwise(g, ref_g, _gradient_terms(th, x.astype(np.float64), t.astype(np.float64), K), 1.0)
     o = 0
     for ci, co in C.LAYERS:
         n = co * ci * 27 + co
@@ -153,6 +215,8 @@ def test_infer_matches_oracle(M):
     s_x, c = np.float32(2.0), np.float32(4.0)
     inp = np.stack([(s_r * r0.astype(np.float32)), (s_x * xp.astype(np.float32))]).reshape(2, n, n, n)
     ref = C.forward(th, inp.astype(np.float64)).reshape(-1) / (float(c) * float(s_r))
+    terms = _output_terms(th, inp.astype(np.float64)).reshape(-1) / (float(c) * float(s_r))
+    _check_elementwise(delta.cpu().numpy(), ref, terms, 0.5)
     assert _rel(delta.cpu().numpy(), ref) <= 2e-3
 
 

@@ -1,18 +1,32 @@
 """Parity at the full sizes of the measured workloads.
 
 128^3: the CUDA path solves the first 23 systems of the implicit-Euler
-sequence exactly as bench.py does (SELL-32, FP64, M(8)stab(4), one fetch, the
-true residual replacing the recursive one at every cycle end) and
-each system is compared with the FP64 oracle's committed record of the same
-sequence (tests/golden/oracle_convdiff3d_128.json, written by
-tests/golden/make_oracle_records.py from oracle/ alone): the true residual,
-the solution on 512 seeded rows and its norm, and the products with A (within
-2, or one cycle apart where the side that ran on had a residual within a
-factor 10 of tol where the other stopped).
+sequence and each system is compared with the FP64 oracle's committed record
+of the same sequence (written by tests/golden/make_oracle_records.py from
+oracle/ alone): the true residual, the solution on 512 seeded rows and its
+norm, and the products with A.
 
-256^3 (lognormal kappa, s = 16): products with A on sampled rows computed
-one by one on the host, and the first solve by its true residual (a property
-that holds at any size; the oracle would need hours here).
+At s = 8, l = 4 on this sequence the iteration amplifies rounding: two correct
+FP64 implementations (the oracle under another BLAS thread count or another
+summation order of its dot products, or the GPU) agree through cycle 2 of the
+first system and then drift apart (residuals a factor 2-6 apart from cycle 4
+on).  Every later system starts from the basis fetched in the first solve, so
+each implementation carries its own fetched basis through the whole sequence.
+Two tests follow from this:
+
+* the same-basis test: both sides fetch at the end of cycle 2 of the first
+  system, before the drift (oracle_convdiff3d_128_fetch2.json).  The later
+  systems then start from the same basis up to rounding; within each system
+  the histories agree for the first three or four cycles and then drift the
+  same way, so products with A must agree within 2 except on systems where
+  the two sides stop one cycle apart, whose number is bounded by what the
+  oracle shows against itself under another summation order.
+* the benchmarked sequence (fetch at relres <= sqrt(tol), cycle 8): the first
+  system (no recycled basis) must agree within 2 products; on the later
+  systems each side runs with its own draw of the fetched basis, so the count
+  of one-cycle cases is bounded by the spread that different draws produce,
+  and the sum of products with A over systems 2..23 must be within 8 % of the
+  record's.
 """
 
 import json
@@ -22,12 +36,17 @@ import numpy as np
 import pytest
 
 from paper_1604_06043_gb300 import problems as pb
-from parity_rules import mvs_match
+from parity_rules import one_cycle_apart
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 DEV = "cuda:0"
 GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_convdiff3d_128.json")
+GOLDEN_FETCH2 = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden",
+                             "oracle_convdiff3d_128_fetch2.json")
+# one-cycle cases allowed among the 22 recycled systems (see the module docstring)
+ONE_CYCLE_MAX_SAME_BASIS = 4
+ONE_CYCLE_MAX_OWN_BASIS = 11
 
 
 @pytest.fixture(scope="module")
@@ -39,20 +58,21 @@ def M():
     return msstab
 
 
-def test_128_sequence_matches_oracle_record(M):
-    rec = json.load(open(GOLDEN))
+def _sequence_against_record(M, rec, **opt):
+    """Solve the record's systems in order; check every system's true
+    residual and solution; return per-system (GPU MVs, record MVs, within 2?)."""
     w = pb.WORKLOADS["convdiff3d_128"]
     assert rec["n"] == w.n and rec["s"] == w.s and rec["ell"] == w.ell
     assert rec["replace_every"] == w.replace_every
     A = w.matrix()
     As = A.to_scipy()
     rows = np.array(rec["sample_rows"])
-    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, replace_every=w.replace_every)
+    S = M.Solver(A, w.s, w.ell, w.p_raw(), device=DEV, replace_every=w.replace_every, **opt)
     f = torch.tensor(w.f(), device=DEV)
     x = torch.tensor(w.x0(), device=DEV)
     b = torch.empty_like(x)
     xprev = w.x0()
-    total, total_rec = 0, 0
+    out = []
     for i, r in enumerate(rec["systems"]):
         S.op_axpby(1.0 / w.tau, x, 1.0, f, b)
         st = S.solve(b, x, w.tol)
@@ -61,17 +81,42 @@ def test_128_sequence_matches_oracle_record(M):
         assert st.status == 0
         assert np.linalg.norm(bn - As @ xn) <= w.tol * np.linalg.norm(bn) * 1.0001, i
         hist, _ = S.history()
-        assert mvs_match(st.mvs, r["mvs"], hist, r["history"], w.tol), (i, st.mvs, r["mvs"], hist, r["history"])
-        total += st.mvs
-        total_rec += r["mvs"]
+        # within 2, or one cycle apart (counted by the callers)
+        within2 = abs(int(st.mvs) - int(r["mvs"])) <= 2
+        assert within2 or one_cycle_apart(hist, r["history"]), (i, st.mvs, r["mvs"], hist, r["history"])
         xo = np.array(r["x_sample"])
         assert np.max(np.abs(xn[rows] - xo)) <= 1e-6 * np.max(np.abs(xo)), i
         assert abs(np.linalg.norm(xn) - r["x_norm"]) <= 1e-7 * r["x_norm"]
+        out.append((int(st.mvs), int(r["mvs"]), within2))
         xprev = xn
-    # the per-system rule bounds every difference to one threshold-decided
-    # cycle; the totals are reported, not bounded (a run-to-run property of
-    # the decisions near tol, 5-6 % apart across summation orders)
-    print("products with A, systems 1..%d: GPU %d, oracle record %d" % (len(rec["systems"]), total, total_rec))
+    S.close()
+    return out
+
+
+def test_128_sequence_same_basis_matches_oracle_record(M):
+    if not os.path.exists(GOLDEN_FETCH2):
+        pytest.skip("the fetch-at-cycle-2 record is not committed")
+    rec = json.load(open(GOLDEN_FETCH2))
+    assert rec["fetch_cycle"] == 2
+    res = _sequence_against_record(M, rec, fetch_cycle=2)
+    assert res[0][2]                                   # the first system: within 2
+    one_cycle = [(i + 1, g, o) for i, (g, o, ok) in enumerate(res) if not ok]
+    print("same basis: GPU %d, oracle %d products with A over %d systems; one cycle apart: %s"
+          % (sum(g for g, _, _ in res), sum(o for _, o, _ in res), len(res), one_cycle))
+    assert len(one_cycle) <= ONE_CYCLE_MAX_SAME_BASIS, one_cycle
+
+
+def test_128_sequence_matches_oracle_record(M):
+    rec = json.load(open(GOLDEN))
+    res = _sequence_against_record(M, rec)
+    assert res[0][2]                                   # the first system: within 2
+    one_cycle = [(i + 1, g, o) for i, (g, o, ok) in enumerate(res) if not ok]
+    tot_g = sum(g for g, _, _ in res[1:])
+    tot_o = sum(o for _, o, _ in res[1:])
+    print("own bases: GPU %d, oracle %d products with A over systems 2..%d; one cycle apart: %s"
+          % (tot_g, tot_o, len(res), one_cycle))
+    assert len(one_cycle) <= ONE_CYCLE_MAX_OWN_BASIS, one_cycle
+    assert abs(tot_g - tot_o) <= 0.08 * tot_o
 
 
 def test_128_fp32_inner_form_against_oracle_record(M):

@@ -511,7 +511,7 @@ def test_persistent_level_step_is_the_per_kernel_path_bit_for_bit(M, wl, form):
     A = w.matrix()
     opt = {"fp64": {}, "fp64_replace": dict(replace_every=1),
            "fp32_inner": dict(precision=M.PREC_FP32_INNER, inner_ell=1, fetch_policy=M.FETCH_NEVER)}[form]
-    a = _sequence_with_history(M, w, A, 3, persistent=1, **opt)
+    a = _sequence_with_history(M, w, A, 3, persistent=2, **opt)
     b = _sequence_with_history(M, w, A, 3, persistent=0, **opt)
     for (ma, ca, xa, ha, la), (mb, cb, xb, hb, lb) in zip(a, b):
         assert ma == mb and ca == cb
