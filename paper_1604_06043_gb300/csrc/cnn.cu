@@ -24,6 +24,9 @@
 #include <string>
 #include <vector>
 
+#include <cuda.h>          // CUtensorMap and its enums (types only: the encoder is fetched at run time)
+#include <cudaTypedefs.h>
+
 #include "launch.h"
 #include "msstab.h"
 
@@ -58,6 +61,19 @@ struct Dims {
   __host__ __device__ int64_t vol() const { return (int64_t)X * Y * Z; }
 };
 
+// Layout of the bfloat16 volumes the convolutions read and write ("half-
+// major"): channel c of voxel p of batch entry b of a C-channel batch sits at
+// element ((b * halves(C) + c / 8) * vol + p) * 8 + c % 8.  Each voxel's 8
+// channels of one half are one 16-byte row (zero channels when C < 8), so the
+// halo of a tile is one tiled tensor copy per half that lands in shared memory
+// already in the K-major operand layout of the MMAs.  FP32 volumes (pre-
+// activations, outputs, targets) stay channel-planar.
+__host__ __device__ constexpr int halves(int c) { return (c + 7) / 8; }
+
+__device__ __forceinline__ uint32_t bf16_bits(float v) {
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn(v));
+}
+
 // ---------------------------------------------------------------------------
 // The 3x3x3 convolutions on the tensor cores (tcgen05), as an implicit GEMM:
 // an output tile of 128 voxels (8 x-consecutive by 16 y-consecutive in one z
@@ -81,12 +97,13 @@ struct Dims {
 // ---------------------------------------------------------------------------
 constexpr int CTX = 8, CTY = 16;
 constexpr int CHX = CTX + 2, CHY = CTY + 2, CHZ = 3, CHV = CHX * CHY * CHZ;   // 540 halo voxels
-constexpr int TC_A_HALF = CHV * 16;                 // bytes of one channel half of the halo
-constexpr int TC_A_BYTES = 17 * 1024;               // 2 halves (17280 bytes), rounded up
+constexpr int TC_A_HALF = CHV * 16;                 // bytes of one channel half of the halo (8640)
+constexpr int TC_A_HSTRIDE = 8704;                  // the halves 128-byte aligned (tensor-copy destinations)
+constexpr int TC_A_BYTES = 2 * TC_A_HSTRIDE;
 constexpr int TC_B_BYTES = 27 * 512;                // weights of the 27 taps
-constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES;
+constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES + 128;   // + alignment slack
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
-static_assert(2 * TC_A_HALF <= TC_A_BYTES, "halo does not fit");
+static_assert(TC_A_HALF <= TC_A_HSTRIDE && TC_A_HSTRIDE % 128 == 0, "halo halves");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -97,16 +114,28 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
          ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | (1ull << 46);
 }
 
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
+  uint32_t done = 0;
+  for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it)
+    asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                 "selp.u32 %0, 1, 0, p;\n\t}\n"
+                 : "=r"(done) : "r"(bar), "r"(phase));
+  return done != 0;
+}
+
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __restrict__ in, Dims d, int B,
+__global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ CUtensorMap halo_map, Dims d, int B,
                                                       const __nv_bfloat16* __restrict__ w,
                                                       const float* __restrict__ bias, float* __restrict__ z,
                                                       __nv_bfloat16* __restrict__ act,
                                                       const float* __restrict__ zaux, int* flag) {
-  extern __shared__ __align__(1024) unsigned char tsm[];
+  extern __shared__ __align__(1024) unsigned char tsm_raw[];
+  // the tensor copies want 128-byte aligned destinations
+  unsigned char* tsm = tsm_raw + ((128u - (smem_u32(tsm_raw) & 127u)) & 127u);
   unsigned char* As = tsm;
   unsigned char* Bs = tsm + TC_A_BYTES;
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t tbar;   // completion of the halo's tensor copies
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tilesx = (d.X + CTX - 1) / CTX, tilesy = (d.Y + CTY - 1) / CTY;
@@ -119,10 +148,16 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
     const __nv_bfloat16 v = (co < CO && ci < CI) ? w[(co * CI + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
     *reinterpret_cast<__nv_bfloat16*>(Bs + tap * 512 + (ci >> 3) * 256 + co * 16 + (ci & 7) * 2) = v;
   }
+  // fewer than 9 input channels: the second half of the halo stays zero (the
+  // weights of those channels are zero too, and 0 * 0 keeps the sums finite)
+  if (halves(CI) < 2)
+    for (int i = tid; i < TC_A_HALF / 16; i += 128) reinterpret_cast<uint4*>(As + TC_A_HSTRIDE)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tbar)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
+  asm volatile("fence.proxy.async.shared::cta;");
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
                  "r"(32));
@@ -141,50 +176,44 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
     const int tz0 = tile / (tilesx * tilesy);
     const int ty0 = ((tile / tilesx) % tilesy) * CTY;
     const int tx0 = (tile % tilesx) * CTX;
-    const __nv_bfloat16* inb = in + (int64_t)b * CI * vol;
-    // halo: the 8 channels of one half of voxel v as one 16-byte store at
-    // half * A_HALF + v * 16; all of a thread's loads are issued before the
-    // first store (the loads are independent, their latency overlaps)
-    constexpr int HALO_ITEMS = 2 * CHV, HALO_PER_T = (HALO_ITEMS + 127) / 128;
-    uint32_t q[HALO_PER_T][4];
+    // halo: one tiled tensor copy per channel half, box (8 channels, 10 x,
+    // 18 y, 3 z) at (0, tx0 - 1, ty0 - 1, tz0 - 1, b * halves + half); the
+    // copy fills out-of-range voxels with zeros.  The previous tile's MMAs have
+    // completed (their mbarrier was waited on), so the buffer is free.
+    if (tid == 0) {
+      constexpr uint32_t bytes = (uint32_t)halves(CI) * TC_A_HALF;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&tbar)), "r"(bytes)
+                   : "memory");
 #pragma unroll
-    for (int k = 0; k < HALO_PER_T; ++k) {
-      const int i = tid + k * 128;
-      q[k][0] = q[k][1] = q[k][2] = q[k][3] = 0u;
-      if (i < HALO_ITEMS) {
-        const int half = i / CHV, v = i % CHV;
-        const int hx = v % CHX, hy = (v / CHX) % CHY, hz = v / (CHX * CHY);
-        const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-        if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z && half * 8 < CI) {
-          const unsigned short* src = reinterpret_cast<const unsigned short*>(inb) + (int64_t)(half * 8) * vol +
-                                      ((int64_t)gz * d.Y + gy) * d.X + gx;
-#pragma unroll
-          for (int c = 0; c < 8; c += 2) {
-            const uint32_t lo = half * 8 + c < CI ? (uint32_t)__ldg(src + (int64_t)c * vol) : 0u;
-            const uint32_t hi = half * 8 + c + 1 < CI ? (uint32_t)__ldg(src + (int64_t)(c + 1) * vol) : 0u;
-            q[k][c / 2] = lo | (hi << 16);
-          }
-        }
-      }
+      for (int hf = 0; hf < halves(CI); ++hf)
+        asm volatile(
+            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+            "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+            ::"r"(smem_u32(As + hf * TC_A_HSTRIDE)), "l"(reinterpret_cast<uint64_t>(&halo_map)), "r"(0),
+              "r"(tx0 - 1), "r"(ty0 - 1), "r"(tz0 - 1), "r"(b * halves(CI) + hf), "r"(smem_u32(&tbar))
+            : "memory");
     }
-#pragma unroll
-    for (int k = 0; k < HALO_PER_T; ++k) {
-      const int i = tid + k * 128;
-      if (i < HALO_ITEMS)
-        *reinterpret_cast<uint4*>(As + (i / CHV) * TC_A_HALF + (i % CHV) * 16) =
-            make_uint4(q[k][0], q[k][1], q[k][2], q[k][3]);
-    }
-    // the tile's smem writes reach the tensor cores; the previous tile's
-    // tensor-memory reads are done before the MMAs overwrite the accumulator
-    asm volatile("fence.proxy.async.shared::cta;");
+    const bool halo_ok = mbar_wait(smem_u32(&tbar), phase);
+    // the previous tile's tensor-memory reads are done before the MMAs
+    // overwrite the accumulator
     asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+    const int all_loaded = __syncthreads_and((int)halo_ok);
     asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!all_loaded) {
+      // give the copy in flight a second bounded wait before leaving
+      if (tid == 0) {
+        atomicOr(flag, 1);
+        mbar_wait(smem_u32(&tbar), phase);
+      }
+      __syncthreads();
+      ok = false;
+      break;
+    }
     if (tid == 0) {
       const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
       for (int tap = 0; tap < 27; ++tap) {
         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-        const uint64_t ad = umma_desc(a0 + ((dz * CHY + dy) * CHX + dx) * 16, TC_A_HALF, CHX * 16);
+        const uint64_t ad = umma_desc(a0 + ((dz * CHY + dy) * CHX + dx) * 16, TC_A_HSTRIDE, CHX * 16);
         const uint64_t bd = umma_desc(b0 + tap * 512, 256, 128);
         const uint32_t accum = tap > 0;
         asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -206,11 +235,7 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
 #pragma unroll
       for (int co = 0; co < CO; ++co) za[co] = inside ? __ldg(zaux + ob + (int64_t)co * vol + p) : 0.f;
     }
-    uint32_t done = 0;
-    for (long long it = 0; it < TC_WAIT_LIMIT && !done; ++it)
-      asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                   "selp.u32 %0, 1, 0, p;\n\t}\n"
-                   : "=r"(done) : "r"(smem_u32(&mbar)), "r"(phase));
+    const bool done = mbar_wait(smem_u32(&mbar), phase);
     // one decision for the whole block (tcgen05.ld below is warp-collective)
     const int all_done = __syncthreads_and((int)done);
     asm volatile("tcgen05.fence::after_thread_sync;");
@@ -228,20 +253,35 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
                  : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
     asm volatile("tcgen05.wait::ld.sync.aligned;");
     if (inside) {
+      // bf16 outputs of the 16 channels, as two 16-byte half-major rows
+      uint32_t packed[8];
 #pragma unroll
-      for (int co = 0; co < CO; ++co) {
-        const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
-        const int64_t o = ob + (int64_t)co * vol + p;
-        if (MODE == FWD_HIDDEN) {
-          z[o] = acc;
-          act[o] = __float2bfloat16_rn(gelu(acc));
-        } else if (MODE == FWD_LAST) {
-          z[o] = acc;
-        } else if (MODE == INFER_HIDDEN) {
-          act[o] = __float2bfloat16_rn(gelu(acc));
-        } else {
-          act[o] = __float2bfloat16_rn(acc * gelu_grad(za[MODE == BWD_DATA ? co : 0]));
+      for (int co = 0; co < 16; ++co) {
+        float out = 0.f;
+        if (co < CO) {
+          const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
+          const int64_t o = ob + (int64_t)co * vol + p;
+          if (MODE == FWD_HIDDEN) {
+            z[o] = acc;
+            out = gelu(acc);
+          } else if (MODE == FWD_LAST) {
+            z[o] = acc;
+          } else if (MODE == INFER_HIDDEN) {
+            out = gelu(acc);
+          } else {
+            out = acc * gelu_grad(za[MODE == BWD_DATA ? co : 0]);
+          }
         }
+        if (co % 2 == 0)
+          packed[co / 2] = bf16_bits(out);
+        else
+          packed[co / 2] |= bf16_bits(out) << 16;
+      }
+      if constexpr (MODE != FWD_LAST) {
+        static_assert(MODE == FWD_LAST || CO == 16, "bf16 outputs have 16 channels");
+        uint4* dst = reinterpret_cast<uint4*>(act);
+        dst[((int64_t)b * 2 + 0) * vol + p] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[((int64_t)b * 2 + 1) * vol + p] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
     }
   }
@@ -250,9 +290,39 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __nv_bfloat16* __res
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(32));
 }
 
+// The tensor map of a half-major input (B entries of nh halves): dimensions
+// (8 channels, x, y, z, entry * nh + half), innermost first; box (8, 10, 18,
+// 3, 1) = one halo half; out-of-range elements read as zero.  The encoder is
+// the driver's, fetched through the runtime (no link against the driver).
+static cudaError_t halo_map(CUtensorMap* m, const __nv_bfloat16* in, Dims d, int B, int nh) {
+  static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
+  if (!enc) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+  }
+  const cuuint64_t dims[5] = {8, (cuuint64_t)d.X, (cuuint64_t)d.Y, (cuuint64_t)d.Z, (cuuint64_t)B * nh};
+  const cuuint64_t strides[4] = {16, 16ull * d.X, 16ull * d.X * d.Y, 16ull * d.X * d.Y * d.Z};
+  const cuuint32_t box[5] = {8, CHX, CHY, CHZ, 1};
+  const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(in), dims, strides, box,
+                         estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
 template <int CI, int CO, int MODE>
 static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
                            const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
+  if (((uintptr_t)in & 15u) != 0) return cudaErrorMisalignedAddress;   // tensor-copy base: 16-byte aligned
+  CUtensorMap map;
+  {
+    const cudaError_t e = halo_map(&map, in, d, B, halves(CI));
+    if (e != cudaSuccess) return e;
+  }
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(conv_tc_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM);
@@ -277,7 +347,7 @@ static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int
   }
   const int64_t jobs = (int64_t)((d.X + CTX - 1) / CTX) * ((d.Y + CTY - 1) / CTY) * d.Z * B;
   const int grid = (int)(jobs < cap ? jobs : cap);   // persistent blocks, tiles in a grid-stride loop
-  conv_tc_kernel<CI, CO, MODE><<<grid, 128, TC_SMEM, st>>>(in, d, B, w, bias, z, act, zaux, flag);
+  conv_tc_kernel<CI, CO, MODE><<<grid, 128, TC_SMEM, st>>>(map, d, B, w, bias, z, act, zaux, flag);
   return cudaGetLastError();
 }
 
@@ -323,7 +393,8 @@ __global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restri
     const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
     float v = 0.f;
     if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z)
-      v = __bfloat162float(a[(int64_t)b * CI * vol + (int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
+      v = __bfloat162float(a[(((int64_t)b * halves(CI) + (c >> 3)) * vol + ((int64_t)gz * d.Y + gy) * d.X + gx) * 8 +
+                             (c & 7)]);
     a_s[c * HVP + h] = v;
   }
   for (int i = threadIdx.x; i < CO * TV; i += TV) {
@@ -332,7 +403,8 @@ __global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restri
     const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
     float v = 0.f;
     if (gx < d.X && gy < d.Y && gz < d.Z)
-      v = __bfloat162float(g[(int64_t)b * CO * vol + (int64_t)c * vol + ((int64_t)gz * d.Y + gy) * d.X + gx]);
+      v = __bfloat162float(g[(((int64_t)b * halves(CO) + (c >> 3)) * vol + ((int64_t)gz * d.Y + gy) * d.X + gx) * 8 +
+                             (c & 7)]);
     g_s[i] = v;
   }
   __syncthreads();
@@ -427,7 +499,7 @@ __global__ void loss_kernel(const float* out, const float* t, int64_t n, double 
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const float dlt = out[i] - t[i];
     s += (double)dlt * dlt;
-    g[i] = __float2bfloat16_rn((float)(2.0 * (double)dlt * inv_count));
+    reinterpret_cast<uint4*>(g)[i] = make_uint4(bf16_bits((float)(2.0 * (double)dlt * inv_count)), 0u, 0u, 0u);
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
@@ -494,7 +566,7 @@ __global__ void stencil_bwd_kernel(const float* s, int B, int D, const float* k2
           if (kk == 0.f || zz < 0 || zz >= D || yy < 0 || yy >= D || xx < 0 || xx >= D) continue;
           v = fmaf(kk, s[base + ((int64_t)zz * D + yy) * D + xx], v);
         }
-    g[i] = __float2bfloat16_rn((float)(2.0 * (double)v * inv_count));
+    reinterpret_cast<uint4*>(g)[i] = make_uint4(bf16_bits((float)(2.0 * (double)v * inv_count)), 0u, 0u, 0u);
   }
 }
 
@@ -538,8 +610,9 @@ __global__ void gather_kernel(const float* pin, const float* pt, int64_t N, Dims
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < v3; i += (int64_t)gridDim.x * blockDim.x) {
     const int x = (int)(i % D), y = (int)((i / D) % D), z = (int)(i / ((int64_t)D * D));
     const int64_t g = ((int64_t)(oz + z) * full.Y + (oy + y)) * full.X + (ox + x);
-    in[((int64_t)b * 2 + 0) * v3 + i] = __float2bfloat16_rn(s0 * pin[((int64_t)k * 2 + 0) * N + g]);
-    in[((int64_t)b * 2 + 1) * v3 + i] = __float2bfloat16_rn(s1 * pin[((int64_t)k * 2 + 1) * N + g]);
+    const uint32_t c01 = bf16_bits(s0 * pin[((int64_t)k * 2 + 0) * N + g]) |
+                         (bf16_bits(s1 * pin[((int64_t)k * 2 + 1) * N + g]) << 16);
+    reinterpret_cast<uint4*>(in)[(int64_t)b * v3 + i] = make_uint4(c01, 0u, 0u, 0u);   // half-major, C = 2
     t[(int64_t)b * v3 + i] = st * pt[(int64_t)k * N + g];
   }
 }
@@ -558,8 +631,18 @@ __global__ void pair_kernel(const double* r0, const double* xp, const double* xn
 __global__ void infer_in_kernel(const double* r0, const double* xp, int64_t N, float s0, float s1,
                                 __nv_bfloat16* in) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
-    in[i] = __float2bfloat16_rn(s0 * (float)r0[i]);
-    in[N + i] = __float2bfloat16_rn(s1 * (float)xp[i]);
+    const uint32_t c01 = bf16_bits(s0 * (float)r0[i]) | (bf16_bits(s1 * (float)xp[i]) << 16);
+    reinterpret_cast<uint4*>(in)[i] = make_uint4(c01, 0u, 0u, 0u);   // half-major, C = 2
+  }
+}
+
+// a batch of FP32 two-channel volumes [B][2][v3] as the half-major bf16 input
+__global__ void pack_input_kernel(const float* x, int B, int64_t v3, __nv_bfloat16* in) {
+  const int64_t n = (int64_t)B * v3;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t b = i / v3, p = i % v3;
+    const uint32_t c01 = bf16_bits(x[(b * 2 + 0) * v3 + p]) | (bf16_bits(x[(b * 2 + 1) * v3 + p]) << 16);
+    reinterpret_cast<uint4*>(in)[i] = make_uint4(c01, 0u, 0u, 0u);
   }
 }
 
@@ -823,9 +906,9 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
     CKC(calloc_(h, &h->wq[l], CO_[l] * CI_[l] * 27));
     CKC(calloc_(h, &h->wt[l], CO_[l] * CI_[l] * 27));
     CKC(calloc_(h, &h->bq[l], CO_[l]));
-    CKC(calloc_(h, &h->act[l], (size_t)CI_[l] * bv));
+    CKC(calloc_(h, &h->act[l], (size_t)8 * halves(CI_[l]) * bv));   // half-major bf16
     CKC(calloc_(h, &h->z[l], (size_t)CO_[l] * bv));
-    CKC(calloc_(h, &h->dz[l], (size_t)CO_[l] * bv));
+    CKC(calloc_(h, &h->dz[l], (size_t)8 * halves(CO_[l]) * bv));
   }
   CKC(calloc_(h, &h->tgt, bv));
   CKC(calloc_(h, &h->sbuf, bv));
@@ -841,7 +924,7 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
     CKC(calloc_(h, &h->pt, (size_t)max_pairs * h->N));
     CKC(calloc_(h, &h->d_pair_sr, (size_t)max_pairs));
   }
-  CKC(calloc_(h, &h->iin, 2 * (size_t)h->N));
+  CKC(calloc_(h, &h->iin, 8 * (size_t)h->N));
   CKC(calloc_(h, &h->ia, 16 * (size_t)h->N));
   CKC(calloc_(h, &h->ib, 16 * (size_t)h->N));
   CKC(calloc_(h, &h->iout, (size_t)h->N));
@@ -918,8 +1001,8 @@ msstab_status msstab_cnn_get_scales(msstab_cnn_t h, float* scales2) {
 msstab_status msstab_cnn_forward(msstab_cnn_t h, const float* d_in, int32_t B, int32_t D, float* d_out) {
   if (!h || !d_in || !d_out) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
   CKA(check_batch(h, B, D));
-  const int64_t n = (int64_t)B * 2 * D * D * D;
-  bf16_from_float_kernel<<<grid1(n), 256, 0, h->stream>>>(d_in, n, h->act[0]);
+  const int64_t v3 = (int64_t)D * D * D;
+  pack_input_kernel<<<grid1((int64_t)B * v3), 256, 0, h->stream>>>(d_in, B, v3, h->act[0]);
   CCK(cudaGetLastError());
   CKA(forward_batch(h, B, D));
   CCK(cudaMemcpyAsync(d_out, h->z[3], sizeof(float) * B * D * D * D, cudaMemcpyDeviceToDevice, h->stream));
@@ -931,8 +1014,8 @@ msstab_status msstab_cnn_grad(msstab_cnn_t h, const float* d_in, const float* d_
                               float* d_grad, double* loss) {
   if (!h || !d_in || !d_target || !d_grad) return cfail(h, MSSTAB_ERR_INVALID_ARG, "NULL argument");
   CKA(check_batch(h, B, D));
-  const int64_t n = (int64_t)B * 2 * D * D * D;
-  bf16_from_float_kernel<<<grid1(n), 256, 0, h->stream>>>(d_in, n, h->act[0]);
+  const int64_t v3 = (int64_t)D * D * D;
+  pack_input_kernel<<<grid1((int64_t)B * v3), 256, 0, h->stream>>>(d_in, B, v3, h->act[0]);
   CCK(cudaGetLastError());
   CCK(cudaMemcpyAsync(h->tgt, d_target, sizeof(float) * B * D * D * D, cudaMemcpyDeviceToDevice, h->stream));
   CKA(forward_batch(h, B, D));
