@@ -38,6 +38,9 @@ WORKLOAD = "convdiff3d_128"
 GOLDEN = os.path.join(ROOT, "tests", "golden", "oracle_convdiff3d_128.json")
 FAMILIES = ["spmv", "spmv_dot", "gamma", "eta", "lazy", "tau", "other", "cnn", "precond", "level"]
 FP64_NOMINAL_TFLOPS = 1.25   # GB300 FP64 (vector and tensor), nominal
+# GB300 FP32 on the CUDA cores, from the unit counts and the clock: 152 SMs x
+# 128 FP32 lanes x 2 flops (multiply-add) x 2.07 GHz
+FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel of each form,
 # from one ncu capture of the current kernel at 128^3
 # (profiles/ncu_level_fp64_convdiff3d_128.md, ncu_spmv_dot_*_convdiff3d_128.md).
@@ -750,10 +753,22 @@ def main(argv=None):
                         "avg_us": round(avg_s * 1e6, 2), "alg_bytes_per_launch": int(mod["bytes"]),
                         "GBps": round(gbs, 1), "hbm_frac": round(gbs / hbm_peak, 3),
                         "fp64_tflops": round(tf, 3), "fp64_frac_nominal": round(tf / FP64_NOMINAL_TFLOPS, 3)}
+    fp32_form = args.form.startswith("fp32_inner")
+    if fp32_form:
+        # the FP32 inner kernels' arithmetic is FP32: their ALU bound is the FP32 rate
+        for k_ in kernels:
+            kernels[k_]["fp32_tflops"] = kernels[k_].pop("fp64_tflops")
+            kernels[k_]["fp32_frac_nominal"] = round(kernels[k_]["fp32_tflops"] / FP32_NOMINAL_TFLOPS, 3)
+            kernels[k_].pop("fp64_frac_nominal")
     dom = max(kernels, key=lambda k_: kernels[k_]["total_ms"])
     kd = kernels[dom]
     share = round(fam_ms[dom] / max(1e-9, sum(fam_ms.values())), 3)
-    if kd["fp64_frac_nominal"] > kd["hbm_frac"]:
+    if fp32_form:
+        roofline = {"kernel": dom, "bound": "hbm", "achieved": kd["GBps"], "peak": hbm_peak, "unit": "GB/s",
+                    "frac": kd["hbm_frac"], "traffic": NCU_TRAFFIC.get((args.workload, args.form, dom)),
+                    "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                    "fp32_frac_of_nominal": kd["fp32_frac_nominal"], "share_of_step": share}
+    elif kd["fp64_frac_nominal"] > kd["hbm_frac"]:
         # FP64 FMA throughput, not HBM, binds this kernel on GB300
         roofline = {"kernel": dom, "bound": "alu", "achieved": kd["fp64_tflops"], "peak": FP64_NOMINAL_TFLOPS,
                     "unit": "TFLOP/s (FP64)", "frac": kd["fp64_frac_nominal"],
