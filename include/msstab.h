@@ -317,6 +317,16 @@ msstab_status msstab_op_lazy_update(msstab_t h, int32_t prec, void* d_R, void* d
 msstab_status msstab_op_tau_update(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x, int64_t ld,
                                    const double* d_tau);
 
+/* The degree-l step as a solve runs it at a cycle end (Algorithm 1, after the
+ * level loop): the updates of msstab_op_tau_update when do_update != 0, then,
+ * in the same pass, the projections of the new r and V^(0) that the next
+ * cycle's first gamma solve uses.  d_out (FP64, s*s + s + 1 values):
+ * d_out[q*s + c] = p_c . v_q^(0), d_out[s*s + c] = p_c . r^(0),
+ * d_out[s*s + s] = r^(0) . r^(0), with P the handle's cut space in the
+ * precision prec.  Layout of d_R, d_V, d_x as msstab_op_tau_update. */
+msstab_status msstab_op_tau_step(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x, int64_t ld,
+                                 const double* d_tau, int32_t do_update, double* d_out);
+
 /* Solve the n x n system d_M z = d_rhs (d_M row-major, n <= 16) on the device by
  * Gaussian elimination with partial pivoting; *d_flag = 1 if the pivot of a
  * column fell below 1e-14 times the largest magnitude in that column of M

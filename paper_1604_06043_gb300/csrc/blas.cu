@@ -22,6 +22,14 @@ static int max_grid(K kernel, const Ctx& c, int cap_blocks = MAXBLK) {
   return g > cap_blocks ? cap_blocks : g;
 }
 
+template <typename K>
+static int max_grid_nt(K kernel, const Ctx& c, int nt) {
+  int nb = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, kernel, nt, 0) != cudaSuccess || nb < 1) nb = 1;
+  const int g = nb * c.sms;
+  return g > MAXBLK ? MAXBLK : g;
+}
+
 static inline int clamp_grid(int64_t need, int cap) { return (int)(need < 1 ? 1 : (need < cap ? need : cap)); }
 
 // Per-thread dot-product accumulators: FP64 for FP64 vectors, compensated FP32
@@ -264,9 +272,184 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 1) lazy_kernel(int n,
   }
 }
 
+// The same updates four rows at a time for FP32 (16-byte loads and stores;
+// row by row, this kernel is bound by its instruction count, not by HBM).
+// Each row sees exactly the operations of lazy_kernel, in its order; the
+// n % 4 rows of a ragged tail are done by block 0 one per thread.
+__device__ __forceinline__ float4 ld4(const float* p, int64_t g) { return reinterpret_cast<const float4*>(p)[g]; }
+__device__ __forceinline__ void st4(float* p, int64_t g, float4 v) { reinterpret_cast<float4*>(p)[g] = v; }
+__device__ __forceinline__ void fnma4(float4& a, float c, const float4& b) {
+  a.x -= c * b.x;
+  a.y -= c * b.y;
+  a.z -= c * b.z;
+  a.w -= c * b.w;
+}
+__device__ __forceinline__ void fma4(float4& a, float c, const float4& b) {
+  a.x += c * b.x;
+  a.y += c * b.y;
+  a.z += c * b.z;
+  a.w += c * b.w;
+}
+
+template <int S>
+__global__ void __launch_bounds__(NT, 2) lazy_f32x4_kernel(int n, int s, float* R, float* V, float* x, int64_t ld,
+                                                          int k, const double* __restrict__ gamma,
+                                                          const double* __restrict__ eta, int eta_ld) {
+  __shared__ float g[SMAX];
+  __shared__ float e[SMAX * SMAX];
+  if (threadIdx.x < s) g[threadIdx.x] = (float)gamma[threadIdx.x];
+  for (int i = threadIdx.x; i < s * s; i += NT) e[(i / s) * SMAX + (i % s)] = (float)eta[(i / s) * eta_ld + (i % s)];
+  __syncthreads();
+  const int64_t groups = n / 4;
+  const int64_t stride = (int64_t)gridDim.x * NT;
+  for (int64_t gi = blockIdx.x * (int64_t)NT + threadIdx.x; gi < groups; gi += stride) {
+    float4 above[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+      above[j] = ld4(V + ((int64_t)(k + 1) * s + j) * ld, gi);
+    }
+    float4 rup = ld4(R + (int64_t)k * ld, gi);
+    for (int i = k - 1; i >= -1; --i) {
+      float4 old[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (j >= s) break;
+        old[j] = ld4(V + ((int64_t)(i + 1) * s + j) * ld, gi);
+      }
+      if (i >= 0) {
+        float4 ri = ld4(R + (int64_t)i * ld, gi);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          if (j >= s) break;
+          fnma4(ri, g[j], old[j]);
+        }
+        st4(R + (int64_t)i * ld, gi, ri);
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q >= s) break;
+          float4 v = rup;
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            if (j >= s) break;
+            fnma4(v, e[q * SMAX + j], j < q ? above[j] : old[j]);
+          }
+          st4(V + ((int64_t)(i + 1) * s + q) * ld, gi, v);
+          old[q] = v;
+        }
+        rup = ri;
+      } else {
+        float4 xv = ld4(x, gi);
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          if (j >= s) break;
+          fma4(xv, g[j], old[j]);
+        }
+        st4(x, gi, xv);
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q >= s) break;
+          float4 v = rup;
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            if (j >= s) break;
+            fnma4(v, e[q * SMAX + j], j < q ? above[j] : old[j]);
+          }
+          st4(V + (int64_t)q * ld, gi, v);
+          old[q] = v;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (j >= s) break;
+        above[j] = old[j];
+      }
+    }
+  }
+  // ragged tail
+  const int64_t row = groups * 4 + threadIdx.x;
+  if (blockIdx.x == 0 && row < n) {
+    float above[S];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      if (j >= s) break;
+      above[j] = V[((int64_t)(k + 1) * s + j) * ld + row];
+    }
+    float rup = R[(int64_t)k * ld + row];
+    for (int i = k - 1; i >= -1; --i) {
+      float old[S];
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (j >= s) break;
+        old[j] = V[((int64_t)(i + 1) * s + j) * ld + row];
+      }
+      if (i >= 0) {
+        float ri = R[(int64_t)i * ld + row];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          if (j >= s) break;
+          ri -= g[j] * old[j];
+        }
+        R[(int64_t)i * ld + row] = ri;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q >= s) break;
+          float v = rup;
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            if (j >= s) break;
+            v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
+          }
+          V[((int64_t)(i + 1) * s + q) * ld + row] = v;
+          old[q] = v;
+        }
+        rup = ri;
+      } else {
+        float xv = x[row];
+#pragma unroll
+        for (int j = 0; j < S; ++j) {
+          if (j >= s) break;
+          xv += g[j] * old[j];
+        }
+        x[row] = xv;
+#pragma unroll
+        for (int q = 0; q < S; ++q) {
+          if (q >= s) break;
+          float v = rup;
+#pragma unroll
+          for (int j = 0; j < S; ++j) {
+            if (j >= s) break;
+            v -= e[q * SMAX + j] * (j < q ? above[j] : old[j]);
+          }
+          V[(int64_t)q * ld + row] = v;
+          old[q] = v;
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        if (j >= s) break;
+        above[j] = old[j];
+      }
+    }
+  }
+}
+
 template <typename T>
 cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld, int k, const double* gamma,
                         const double* eta, int eta_ld) {
+  if constexpr (sizeof(T) == 4) {
+    if (s <= 8 && ld % 4 == 0 && aligned16(R) && aligned16(V) && aligned16(x)) {
+      const int64_t need = (n / 4 + NT - 1) / NT;
+      if (s <= 4) {
+        static int cap = max_grid(lazy_f32x4_kernel<4>, c);
+        lazy_f32x4_kernel<4><<<clamp_grid(need, cap), NT, 0, c.stream>>>(n, s, R, V, x, ld, k, gamma, eta, eta_ld);
+      } else {
+        static int cap = max_grid(lazy_f32x4_kernel<8>, c);
+        lazy_f32x4_kernel<8><<<clamp_grid(need, cap), NT, 0, c.stream>>>(n, s, R, V, x, ld, k, gamma, eta, eta_ld);
+      }
+      return cudaGetLastError();
+    }
+  }
   const int64_t need = (n + NT - 1) / NT;
   if (s <= 4) {
     static int cap = max_grid(lazy_kernel<T, 4>, c);
@@ -300,6 +483,8 @@ struct TauArgs {
   Epi epi;
   RedScratch rs;
   const T* Pb;   // block-partitioned P (see pblock_col), or NULL
+  const T* Pil;  // P interleaved by row (row stride sp), or NULL
+  int sp;
 };
 
 // L: compile-time bound on the degree l (1, 2, 4 or 8): level arrays of L + 2
@@ -445,6 +630,198 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs
   if (threadIdx.x < 32) run_epilogue(a.epi, ew);
 }
 
+// ---------------------------------------------------------------------------
+// Degree-1 step of the FP32 inner form (l = 1, s <= S <= 8), four rows per
+// thread (16-byte loads and stores, as the other FP32 block kernels).  The
+// s + 1 vector groups of a row (group 0: r and x; group 1 + q: v_q and u_q)
+// are split into T1_G chunks of consecutive groups; warp w of a block takes
+// chunk w % T1_G of the 128 rows of its slab w / T1_G, so that a thread keeps
+// only its chunk's dots (P^T of its groups' new vectors, and r.r in chunk 0)
+// in FP32 registers and issues every load of its groups and of the rows' P
+// entries before its first store (the chunks' repeated P loads hit L1).  Each
+// dot takes the four rows in order.  Warp sums are FP32 (reduce-scatter over
+// rounds of 32 values); the sums over a block's slabs and over the blocks are
+// FP64.  One block per SM, so that the last block adds few partials per value
+// (FP64 additions are slow on this GPU).  The n % 4 rows of a ragged tail go
+// to block 0, one row per lane of each chunk's first-slab warp.  Outputs and
+// epilogue as tau_kernel's.
+// ---------------------------------------------------------------------------
+constexpr int T1_G = 3;
+constexpr int T1_SLABS = 4;
+constexpr int T1_NW = T1_G * T1_SLABS;
+constexpr int T1_NT = 32 * T1_NW;
+constexpr int T1_ROWS = 4 * 32 * T1_SLABS;   // rows of a block per iteration
+
+template <int S>
+__global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
+  constexpr int GPC = (S + 1 + T1_G - 1) / T1_G;   // groups per chunk
+  constexpr int NL = GPC * S + 1;                 // a thread's values: P^T of its groups, then r.r
+  constexpr int NLP = (NL + 31) / 32 * 32;
+  constexpr int NV = S * S + S + 1;               // block values: P^T v_q [q][c], P^T r [c], r.r
+  static_assert((int64_t)MAXBLK * NV <= (int64_t)MAXGRP * MAXBLK * MAXRED, "partials exceed the reduction scratch");
+  __shared__ double wsum[T1_NW][NL];
+  __shared__ double bsum[NV];
+  __shared__ EpiScratch ew;
+  __shared__ int s_last;
+  const int s = a.s;
+  const int64_t ld = a.ld;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int chunk = w % T1_G, slab = w / T1_G;
+  const float tau1 = a.do_update ? (float)a.tau[0] : 0.f;
+  float acc[NLP];
+#pragma unroll
+  for (int i = 0; i < NLP; ++i) acc[i] = 0.f;
+  auto col = [&](int g, int which) -> float* {
+    // which: 0 = r^(0) / v_q^(0), 1 = x / v_q^(-1), 2 = r^(1) / v_q^(1)
+    if (g == 0) return which == 0 ? a.R : (which == 1 ? a.x : a.R + ld);
+    const int q = g - 1;
+    return a.V + ((which == 0 ? (int64_t)s : (which == 1 ? 0 : (int64_t)2 * s)) + q) * ld;
+  };
+  // one row quad (4-row group index gi) or, in the tail, one row (float path)
+  auto do_rows = [&](auto vec_tag, int64_t gi) {
+    using V = decltype(vec_tag);
+    constexpr int NR = sizeof(V) / sizeof(float);
+    auto ld_v = [&](const float* p) -> V { return reinterpret_cast<const V*>(p)[gi]; };
+    auto st_v = [&](float* p, const V& v) { reinterpret_cast<V*>(p)[gi] = v; };
+    auto cmp = [](const V& v, int u) -> float { return reinterpret_cast<const float*>(&v)[u]; };
+    auto cmpr = [](V& v, int u) -> float& { return reinterpret_cast<float*>(&v)[u]; };
+    V pc[S];
+    if (a.proj) {
+#pragma unroll
+      for (int c = 0; c < S; ++c)
+        if (c < s) pc[c] = __ldg(reinterpret_cast<const V*>(a.P + (int64_t)c * a.ldp) + gi);
+    }
+    V v0[GPC], vm[GPC], v1[GPC];
+#pragma unroll
+    for (int i = 0; i < GPC; ++i) {
+      const int g = chunk * GPC + i;
+      if (g > s) break;
+      v0[i] = ld_v(col(g, 0));
+      if (a.do_update) {
+        vm[i] = ld_v(col(g, 1));
+        v1[i] = ld_v(col(g, 2));
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < GPC; ++i) {
+      const int g = chunk * GPC + i;
+      if (g > s) break;
+      V out = v0[i];
+      if (a.do_update) {
+        V nv = v0[i], nm = vm[i];
+#pragma unroll
+        for (int u = 0; u < NR; ++u) {
+          if (g == 0) {
+            cmpr(nv, u) -= tau1 * cmp(v1[i], u);      // r = r^(0) - tau r^(1)
+            cmpr(nm, u) += tau1 * cmp(v0[i], u);      // x = x + tau r^(0)
+          } else {
+            cmpr(nv, u) -= tau1 * cmp(v1[i], u);      // v_q = v_q^(0) - tau v_q^(1)
+            cmpr(nm, u) -= tau1 * cmp(v0[i], u);      // u_q = v_q^(-1) - tau v_q^(0)
+          }
+        }
+        st_v(col(g, 0), nv);
+        st_v(col(g, 1), nm);
+        if (g == 0 && a.xbak) st_v(a.xbak, nm);
+        out = nv;
+      }
+      if (a.proj) {
+#pragma unroll
+        for (int c = 0; c < S; ++c) {
+          if (c >= s) break;
+#pragma unroll
+          for (int u = 0; u < NR; ++u) acc[i * S + c] = fmaf(cmp(out, u), cmp(pc[c], u), acc[i * S + c]);
+        }
+        if (g == 0) {
+#pragma unroll
+          for (int u = 0; u < NR; ++u) acc[NL - 1] = fmaf(cmp(out, u), cmp(out, u), acc[NL - 1]);
+        }
+      }
+    }
+  };
+  const int64_t quads = a.n / 4;
+  const int64_t stride = (int64_t)gridDim.x * (32 * T1_SLABS);
+  for (int64_t gi = (int64_t)blockIdx.x * (32 * T1_SLABS) + slab * 32 + lane; gi < quads; gi += stride)
+    do_rows(float4{}, gi);
+  if (blockIdx.x == 0 && slab == 0 && lane < a.n - quads * 4) do_rows(float{}, quads * 4 + lane);
+  if (!a.proj) return;
+#pragma unroll
+  for (int r0 = 0; r0 < NLP; r0 += 32) {
+    float v[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = acc[r0 + i];
+    RedScatterT<float, 32, 16, 32>::run(v, lane);
+    const int idx = r0 + rs_index<32>(lane);
+    if (idx < NL) wsum[w][idx] = widen_f32(v[0]);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < NV; i += T1_NT) {
+    int g, loc;
+    if (i < S * S) {
+      g = 1 + i / S;
+      loc = ((g % GPC) * S) + (i % S);
+    } else if (i < S * S + S) {
+      g = 0;
+      loc = i - S * S;
+    } else {
+      g = 0;
+      loc = NL - 1;
+    }
+    double sum = 0.0;
+#pragma unroll
+    for (int sl = 0; sl < T1_SLABS; ++sl) sum += wsum[sl * T1_G + g / GPC][loc];
+    bsum[i] = sum;
+  }
+  __syncthreads();
+  // every block's NV sums, then the last block to arrive adds them up: thread
+  // (value v, part j) sums blocks j, j + NJ, ... in four chains, then the NJ
+  // parts of each value are added in order (a fixed order: the result does
+  // not depend on which block is last)
+  constexpr int NJ = T1_NT / NV;
+  static_assert(NJ >= 1, "block too small for the value count");
+  __shared__ double part[NJ][NV];
+  double* partials = a.rs.partials;
+  const int nblk = gridDim.x;
+  for (int i = threadIdx.x; i < NV; i += T1_NT) partials[(size_t)blockIdx.x * NV + i] = bsum[i];
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.rs.tickets[0], 1u) == (unsigned)(nblk - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x < NJ * NV) {
+    const int v = threadIdx.x % NV, j = threadIdx.x / NV;
+    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
+    int b = j;
+    for (; b + 3 * NJ < nblk; b += 4 * NJ) {
+      c0 += __ldcg(partials + (size_t)b * NV + v);
+      c1 += __ldcg(partials + (size_t)(b + NJ) * NV + v);
+      c2 += __ldcg(partials + (size_t)(b + 2 * NJ) * NV + v);
+      c3 += __ldcg(partials + (size_t)(b + 3 * NJ) * NV + v);
+    }
+    for (; b < nblk; b += NJ) c0 += __ldcg(partials + (size_t)b * NV + v);
+    part[j][v] = (c0 + c1) + (c2 + c3);
+  }
+  __syncthreads();
+  DevState* st = a.st;
+  for (int i = threadIdx.x; i < NV; i += T1_NT) {
+    double v = part[0][i];
+#pragma unroll
+    for (int j = 1; j < NJ; ++j) v += part[j][i];
+    if (i < S * S) {
+      const int q = i / S, c = i % S;
+      if (q < s && c < s) st->projV[q * SMAX + c] = v;
+    } else if (i < S * S + S) {
+      if (i - S * S < s) st->projR[i - S * S] = v;
+    } else {
+      st->rr = v;
+    }
+  }
+  if (threadIdx.x == 0) a.rs.tickets[0] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x < 32) run_epilogue(a.epi, ew);
+}
+
 template <typename T, int L>
 static void launch_tau(const Ctx& c, const TauArgs<T>& a) {
   static int cap = max_grid(tau_kernel<T, L>, c, MAXBLK);
@@ -460,8 +837,24 @@ static void launch_tau(const Ctx& c, const TauArgs<T>& a) {
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi, const T* Pb) {
-  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs, Pb};
+                       Epi epi, const T* Pb, const T* Pil, int sp) {
+  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs, Pb,
+               Pil, sp};
+  if constexpr (sizeof(T) == 4) {
+    const bool vec = ld % 4 == 0 && ldp % 4 == 0 && aligned16(R) && aligned16(V) && aligned16(x) && aligned16(P) &&
+                     (xbak == nullptr || aligned16(xbak));
+    if (ell == 1 && Pb == nullptr && s <= 8 && vec) {
+      const int64_t need = ((int64_t)n + T1_ROWS - 1) / T1_ROWS;
+      if (s <= 4) {
+        static int cap = max_grid_nt(tau1_f32_kernel<4>, c, T1_NT);
+        tau1_f32_kernel<4><<<clamp_grid(need, cap), T1_NT, 0, c.stream>>>(a);
+      } else {
+        static int cap = max_grid_nt(tau1_f32_kernel<8>, c, T1_NT);
+        tau1_f32_kernel<8><<<clamp_grid(need, cap), T1_NT, 0, c.stream>>>(a);
+      }
+      return cudaGetLastError();
+    }
+  }
   if (ell <= 1)
     launch_tau<T, 1>(c, a);
   else if (ell <= 2)
@@ -485,7 +878,12 @@ struct MdArgs {
   RedScratch rs;
 };
 
-template <typename T>
+// C: compile-time bound on ny; U rows per iteration, all their loads issued
+// before the first multiply-add (a thread has few rows in flight otherwise:
+// the loop is latency-bound).  Each accumulator still takes its rows in
+// order and, within a row, the columns in order, so the sums are those of
+// one row at a time.
+template <typename T, int C, int U>
 __global__ void __launch_bounds__(NT, 2) multidot_kernel(MdArgs<T> a) {
   __shared__ EpiScratch ew;
   __shared__ double smem_w[NWARP * MAXRED];
@@ -494,30 +892,52 @@ __global__ void __launch_bounds__(NT, 2) multidot_kernel(MdArgs<T> a) {
   const int t = blockIdx.x % a.nt;
   const int chunk = blockIdx.x / a.nt;
   const int nchunks = gridDim.x / a.nt;
-  Acc<T, MD_MAXC + 1> acc;  // X_t . Y_c in slots 0..ny-1, X_t . X_t in slot MD_MAXC
+  Acc<T, C + 1> acc;  // X_t . Y_c in slots 0..ny-1, X_t . X_t in slot C
   acc.zero();
   const T* xt = a.cols.x[t];
   const int stride = nchunks * NT;
-  for (int row = chunk * NT + threadIdx.x; row < a.n; row += stride) {
-    const T xv = __ldg(xt + row);
-    T yv[MD_MAXC];
+  int row = chunk * NT + threadIdx.x;
+  for (; row + (U - 1) * stride < a.n; row += U * stride) {
+    T xv[U], yv[U][C];
 #pragma unroll
-    for (int c = 0; c < MD_MAXC; ++c) {
+    for (int u = 0; u < U; ++u) {
+      xv[u] = __ldg(xt + row + u * stride);
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (c >= a.ny) break;
+        yv[u][c] = __ldg(a.cols.y[c] + row + u * stride);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+#pragma unroll
+      for (int c = 0; c < C; ++c) {
+        if (c >= a.ny) break;
+        acc.add(c, xv[u], yv[u][c]);
+      }
+      if (a.self) acc.add(C, xv[u], xv[u]);
+    }
+  }
+  for (; row < a.n; row += stride) {
+    const T xv = __ldg(xt + row);
+    T yv[C];
+#pragma unroll
+    for (int c = 0; c < C; ++c) {
       if (c >= a.ny) break;
       yv[c] = __ldg(a.cols.y[c] + row);
     }
 #pragma unroll
-    for (int c = 0; c < MD_MAXC; ++c) {
+    for (int c = 0; c < C; ++c) {
       if (c >= a.ny) break;
       acc.add(c, xv, yv[c]);
     }
-    if (a.self) acc.add(MD_MAXC, xv, xv);
+    if (a.self) acc.add(C, xv, xv);
   }
   const int m = a.ny + a.self;
   double fin[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i)
-    fin[i] = i < MD_MAXC && i < a.ny ? acc.get(i < MD_MAXC ? i : 0) : (i == a.ny ? acc.get(MD_MAXC) : 0.0);
+    fin[i] = i < C && i < a.ny ? acc.get(i < C ? i : 0) : (i == a.ny ? acc.get(C) : 0.0);
   block_reduce<32>(fin, m, smem_w, red);
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
   if (!groups_done(a.rs, t, a.nt, m, red, &s_last)) return;
@@ -530,18 +950,32 @@ __global__ void __launch_bounds__(NT, 2) multidot_kernel(MdArgs<T> a) {
   if (threadIdx.x < 32) run_epilogue(a.epi, ew);
 }
 
+// Two blocks per SM whatever the variant's occupancy: the row-to-thread map,
+// and with it every partial sum, is then the same for all variants.
+template <typename T, int C, int U>
+static void launch_multidot(const Ctx& c, const MdArgs<T>& a) {
+  const int cap = 2 * c.sms < MAXBLK ? 2 * c.sms : MAXBLK;
+  int64_t chunks = (a.n + NT - 1) / NT;
+  int64_t capc = cap / a.nt;
+  if (capc < 1) capc = 1;
+  if (chunks > capc) chunks = capc;
+  if (chunks < 1) chunks = 1;
+  multidot_kernel<T, C, U><<<(int)(chunks * a.nt), NT, 0, c.stream>>>(a);
+}
+
 template <typename T>
 cudaError_t multidot(const Ctx& c, int n, const MdCols<T>& cols, int nt, int ny, int self, double* out,
                      int ostride, Epi epi) {
   if (nt < 1 || nt > MD_MAXT || ny < 0 || ny + self > MAXRED || ny > MD_MAXC) return cudaErrorInvalidValue;
-  static int cap = max_grid(multidot_kernel<T>, c, MAXBLK);
-  int64_t chunks = (n + NT - 1) / NT;
-  int64_t capc = cap / nt;
-  if (capc < 1) capc = 1;
-  if (chunks > capc) chunks = capc;
-  if (chunks < 1) chunks = 1;
   MdArgs<T> a{cols, n, nt, ny, self, ostride, out, epi, c.rs};
-  multidot_kernel<T><<<(int)(chunks * nt), NT, 0, c.stream>>>(a);
+  if (ny <= 2)
+    launch_multidot<T, 2, 8>(c, a);
+  else if (ny <= 4)
+    launch_multidot<T, 4, 4>(c, a);
+  else if (ny <= 8)
+    launch_multidot<T, 8, 2>(c, a);
+  else
+    launch_multidot<T, MD_MAXC, 1>(c, a);
   return cudaGetLastError();
 }
 
@@ -720,7 +1154,8 @@ cudaError_t f64_to_f32_n(const Ctx& c, int64_t n, const double* x, float* y, dou
   template cudaError_t lazy_update<T>(const Ctx&, int, int, T*, T*, T*, int64_t, int, const double*,      \
                                       const double*, int);                                                \
   template cudaError_t tau_update<T>(const Ctx&, int, int, int, T*, T*, T*, T*, int64_t, const double*,   \
-                                     const T*, int64_t, int, int, DevState*, Epi, const T*);             \
+                                     const T*, int64_t, int, int, DevState*, Epi, const T*, const T*,    \
+                                     int);                                                               \
   template cudaError_t cols_axpy<T>(const Ctx&, int, T*, const T*, int64_t, int, const double*);          \
   template cudaError_t scale_rsqrt<T>(const Ctx&, int, const T*, T*, const double*);                      \
   template cudaError_t tri_apply<T>(const Ctx&, int, int, T*, T*, int64_t, const double*);

@@ -155,25 +155,27 @@ __device__ __forceinline__ double warp_sum(double v) {
 // partner's copy of that half, so a lane spends CNT/2 + CNT/4 + ... additions
 // instead of 5 per value.  Afterwards v[0] of lane L holds the warp sum of
 // value index rs_index<CNT>(L).
-template <int CNT, int O, int M>
-struct RedScatter {
-  static __device__ __forceinline__ void run(double (&v)[M], int lane) {
+template <typename V, int CNT, int O, int M>
+struct RedScatterT {
+  static __device__ __forceinline__ void run(V (&v)[M], int lane) {
     if constexpr (CNT > 1) {
       constexpr int H = CNT / 2;
       const bool up = (lane & O) != 0;
 #pragma unroll
       for (int i = 0; i < H; ++i) {
-        const double send = up ? v[i] : v[i + H];
-        const double keep = up ? v[i + H] : v[i];
+        const V send = up ? v[i] : v[i + H];
+        const V keep = up ? v[i + H] : v[i];
         v[i] = keep + __shfl_xor_sync(0xffffffffu, send, O);
       }
-      if constexpr (O > 1) RedScatter<H, O / 2, M>::run(v, lane);
+      if constexpr (O > 1) RedScatterT<V, H, O / 2, M>::run(v, lane);
     } else {
       v[0] += __shfl_xor_sync(0xffffffffu, v[0], O);
-      if constexpr (O > 1) RedScatter<1, O / 2, M>::run(v, lane);
+      if constexpr (O > 1) RedScatterT<V, 1, O / 2, M>::run(v, lane);
     }
   }
 };
+template <int CNT, int O, int M>
+using RedScatter = RedScatterT<double, CNT, O, M>;
 
 template <int M>
 __device__ __forceinline__ int rs_index(int lane) {

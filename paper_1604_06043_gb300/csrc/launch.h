@@ -101,7 +101,7 @@ cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi, const T* Pb = nullptr);
+                       Epi epi, const T* Pb = nullptr, const T* Pil = nullptr, int sp = 0);
 
 // w -= sum_{c<nc} h[c] U_c (h: FP64 device), columns U_c at U + c*ld.
 template <typename T>

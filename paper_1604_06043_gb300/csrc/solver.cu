@@ -506,7 +506,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     }
     if (need_proj) {
       LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, nullptr, ld, nullptr, P, ld, 0, 1, st,
-                                         epi_of(EPI_GAMMA, 0, 0), w.Pb));
+                                         epi_of(EPI_GAMMA, 0, 0), w.Pb, w.Pil, w.sp));
       need_proj = false;
     }
     // ---- one cycle: level steps k = 0..l-1, the degree-l step, and the
@@ -543,7 +543,7 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
                                          epi_of(EPI_TAU, 0, 0)));
       }
       LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
-                                         epi_of(EPI_GAMMA, 0, 0), w.Pb));
+                                         epi_of(EPI_GAMMA, 0, 0), w.Pb, w.Pil, w.sp));
       // residual replacement at the cycle end: r = b - A x with P^T r and ||r||^2 in the same pass
       // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
       // level step from P^T V (left by tau_update) in the epilogue
@@ -1721,6 +1721,35 @@ msstab_status msstab_op_tau_update(msstab_t h, int32_t prec, void* d_R, void* d_
   else
     LAUNCH(MSSTAB_K_TAU, tau_update<float>(c, h->n, h->s, h->ell, (float*)d_R, (float*)d_V, (float*)d_x, nullptr,
                                            ld, d_tau, h->w32.P, h->w32.ld, 1, 0, h->st, epi_none(h)));
+  CK(cudaStreamSynchronize(h->stream));
+  return MSSTAB_OK;
+}
+
+msstab_status msstab_op_tau_step(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x, int64_t ld,
+                                 const double* d_tau, int32_t do_update, double* d_out) {
+  CKS(check_handle(h));
+  CKS(check_prec(h, prec));
+  if (ld < h->n) return fail(h, MSSTAB_ERR_INVALID_ARG, "ld < n");
+  CKS(check_ptr(h, d_R, "R", prec == 0 ? 8 : 4));
+  CKS(check_ptr(h, d_V, "V", prec == 0 ? 8 : 4));
+  CKS(check_ptr(h, d_x, "x", prec == 0 ? 8 : 4));
+  if (!d_tau || !d_out) return fail(h, MSSTAB_ERR_INVALID_ARG, "NULL pointer");
+  const Ctx c = h->ctx();
+  const int s = h->s;
+  if (prec == 0)
+    LAUNCH(MSSTAB_K_TAU, tau_update<double>(c, h->n, s, h->ell, (double*)d_R, (double*)d_V, (double*)d_x, nullptr,
+                                            ld, d_tau, h->w64.P, h->w64.ld, do_update ? 1 : 0, 1, h->st,
+                                            epi_none(h), h->w64.Pb, h->w64.Pil, h->w64.sp));
+  else
+    LAUNCH(MSSTAB_K_TAU, tau_update<float>(c, h->n, s, h->ell, (float*)d_R, (float*)d_V, (float*)d_x, nullptr,
+                                           ld, d_tau, h->w32.P, h->w32.ld, do_update ? 1 : 0, 1, h->st,
+                                           epi_none(h), h->w32.Pb, h->w32.Pil, h->w32.sp));
+  for (int q = 0; q < s; ++q)
+    CK(cudaMemcpyAsync(d_out + (size_t)q * s, &h->st->projV[q * SMAX], sizeof(double) * s, cudaMemcpyDeviceToDevice,
+                       h->stream));
+  CK(cudaMemcpyAsync(d_out + (size_t)s * s, &h->st->projR[0], sizeof(double) * s, cudaMemcpyDeviceToDevice,
+                     h->stream));
+  CK(cudaMemcpyAsync(d_out + (size_t)s * s + s, &h->st->rr, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   CK(cudaStreamSynchronize(h->stream));
   return MSSTAB_OK;
 }

@@ -338,6 +338,54 @@ def test_tau_update(msstab, case, s, ell):
         assert np.all(np.abs(Vc[0][q] - U[q]) <= TOL64 * sc(Vl[0][q], [(tau[i - 1], Vl[i][q]) for i in range(1, ell + 1)]))
 
 
+@pytest.mark.parametrize("prec,s,ell,upd", [(0, 8, 4, True), (0, 4, 1, True), (1, 8, 1, True), (1, 5, 1, True),
+                                              (1, 4, 1, True), (1, 8, 1, False), (1, 16, 1, True), (1, 8, 2, True)])
+def test_tau_step_projections(msstab, case, prec, s, ell, upd):
+    """The degree-l step with the fused projections of the next cycle's first
+    gamma solve (P^T V^(0), P^T r, r.r), in FP64 and in the FP32 inner form
+    (l = 1, s <= 8: warps over chunks of vector groups; otherwise the
+    per-group kernel), against the oracle's update and plain FP64 dots of the
+    oracle's vectors."""
+    w, A = case
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 90 + s + ell)
+    x0 = np.random.default_rng(13).standard_normal(A.n)
+    tau = np.random.default_rng(14).standard_normal(ell)
+    P = O.orthonormalize_mgs2(pb.randn_cols(A.n, s, pb.SEED_P))
+    if prec == 1:
+        # the FP32 form works on FP32 copies; the oracle takes the same values
+        R = [r_.astype(np.float32).astype(np.float64) for r_ in R]
+        Vl = [v_.astype(np.float32).astype(np.float64) for v_ in Vl]
+        x0 = x0.astype(np.float32).astype(np.float64)
+        P = P.astype(np.float32).astype(np.float64)
+    dt, tol = (torch.float64, TOL64) if prec == 0 else (torch.float32, TOL32)
+    t_ = tau if upd else np.zeros(ell)
+    r, x, U, V = O.tau_update(R, Vl, x0, t_)
+    Rg, Vg = _pack(R, Vl)
+    Rt, Vt, xt = _t(Rg, dt), _t(Vg, dt), _t(x0, dt)
+    out = torch.zeros(s * s + s + 1, dtype=torch.float64, device=DEV)
+    S.op_tau_step(Rt, Vt, xt, _t(tau), out, do_update=upd, prec=prec)
+    Rc, Vc = _unpack(Rt.cpu().numpy().astype(np.float64), Vt.cpu().numpy().astype(np.float64), s, ell)
+    sc = lambda a, terms: np.abs(a) + sum(abs(c_) * np.abs(v_) for c_, v_ in terms)
+    sr = sc(R[0], [(t_[i - 1], R[i]) for i in range(1, ell + 1)])
+    assert np.all(np.abs(Rc[0] - r) <= tol * sr)
+    assert np.all(np.abs(xt.cpu().numpy().astype(np.float64) - x)
+                  <= tol * sc(x0, [(t_[i - 1], R[i - 1]) for i in range(1, ell + 1)]))
+    sv = []
+    for q in range(s):
+        sv.append(sc(Vl[1][q], [(t_[i - 1], Vl[i + 1][q]) for i in range(1, ell + 1)]))
+        assert np.all(np.abs(Vc[1][q] - V[q]) <= tol * sv[q])
+        assert np.all(np.abs(Vc[0][q] - U[q]) <= tol * sc(Vl[0][q], [(t_[i - 1], Vl[i][q]) for i in range(1, ell + 1)]))
+    o = out.cpu().numpy()
+    pv = o[:s * s].reshape(s, s)
+    for q in range(s):
+        # rounding of the update (scale sv) and of the sums (scale |P||v|)
+        bound = tol * (np.abs(P) @ sv[q]) * 4
+        assert np.all(np.abs(pv[q] - P @ V[q]) <= bound), (q, np.max(np.abs(pv[q] - P @ V[q]) / bound))
+    assert np.all(np.abs(o[s * s:s * s + s] - P @ r) <= tol * (np.abs(P) @ sr) * 4)
+    assert abs(o[s * s + s] - r @ r) <= tol * (sr @ sr) * 4
+
+
 @pytest.mark.parametrize("n", [1, 2, 4, 8, 16])
 def test_small_solve(msstab, case, n):
     w, A = case
