@@ -30,6 +30,8 @@ static int max_grid_nt(K kernel, const Ctx& c, int nt) {
   return g > MAXBLK ? MAXBLK : g;
 }
 
+__host__ __device__ constexpr int pow2_ge(int v) { return v <= 1 ? 1 : (v <= 2 ? 2 : (v <= 4 ? 4 : (v <= 8 ? 8 : (v <= 16 ? 16 : 32)))); }
+
 static inline int clamp_grid(int64_t need, int cap) { return (int)(need < 1 ? 1 : (need < cap ? need : cap)); }
 
 // Per-thread dot-product accumulators: FP64 for FP64 vectors, compensated FP32
@@ -658,7 +660,8 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
   constexpr int NL = GPC * S + 1;                 // a thread's values: P^T of its groups, then r.r
   constexpr int NLP = (NL + 31) / 32 * 32;
   constexpr int NV = S * S + S + 1;               // block values: P^T v_q [q][c], P^T r [c], r.r
-  static_assert((int64_t)MAXBLK * NV <= (int64_t)MAXGRP * MAXBLK * MAXRED, "partials exceed the reduction scratch");
+  static_assert((int64_t)(MAXBLK + MAXGRP) * NV <= (int64_t)MAXGRP * MAXBLK * MAXRED,
+                "partials exceed the reduction scratch");
   __shared__ double wsum[T1_NW][NL];
   __shared__ double bsum[NV];
   __shared__ EpiScratch ew;
@@ -772,36 +775,56 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
     bsum[i] = sum;
   }
   __syncthreads();
-  // every block's NV sums, then the last block to arrive adds them up: thread
-  // (value v, part j) sums blocks j, j + NJ, ... in four chains, then the NJ
-  // parts of each value are added in order (a fixed order: the result does
-  // not depend on which block is last)
+  // every block's NV sums, added in two stages so that no block adds many:
+  // the last block to arrive of each group of GB consecutive blocks adds the
+  // group's sums (blocks in order), the last group to finish adds the groups'
+  // sums, each value by NJ threads over parts of the groups, then the parts in
+  // order.  A fixed order: the result does not depend on which blocks are last.
   constexpr int NJ = T1_NT / NV;
   static_assert(NJ >= 1, "block too small for the value count");
   __shared__ double part[NJ][NV];
-  double* partials = a.rs.partials;
+  double* bpart = a.rs.partials;                              // [block][NV]
+  double* gpart = a.rs.partials + (size_t)MAXBLK * NV;        // [group][NV]
   const int nblk = gridDim.x;
-  for (int i = threadIdx.x; i < NV; i += T1_NT) partials[(size_t)blockIdx.x * NV + i] = bsum[i];
+  const int GB = (nblk + MAXGRP - 1) / MAXGRP > 8 ? (nblk + MAXGRP - 1) / MAXGRP : 8;
+  const int ngrp = (nblk + GB - 1) / GB, grp = blockIdx.x / GB;
+  const int gsize = (grp + 1) * GB <= nblk ? GB : nblk - grp * GB;
+  for (int i = threadIdx.x; i < NV; i += T1_NT) bpart[(size_t)blockIdx.x * NV + i] = bsum[i];
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&a.rs.tickets[0], 1u) == (unsigned)(nblk - 1);
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.rs.tickets[grp], 1u) == (unsigned)(gsize - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  for (int i = threadIdx.x; i < NV; i += T1_NT) {
+    double v = 0.0;
+    int b = grp * GB;
+    const int bend = b + gsize;
+    for (; b + 8 <= bend; b += 8) {   // eight loads in flight, added in block order
+      double r[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) r[u] = __ldcg(bpart + (size_t)(b + u) * NV + i);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v += r[u];
+    }
+    for (; b < bend; ++b) v += __ldcg(bpart + (size_t)b * NV + i);
+    gpart[(size_t)grp * NV + i] = v;
+  }
+  if (threadIdx.x == 0) a.rs.tickets[grp] = 0u;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&a.rs.tickets[MAXGRP], 1u) == (unsigned)(ngrp - 1);
   __syncthreads();
   if (!s_last) return;
   __threadfence();
   if (threadIdx.x < NJ * NV) {
     const int v = threadIdx.x % NV, j = threadIdx.x / NV;
-    double c0 = 0.0, c1 = 0.0, c2 = 0.0, c3 = 0.0;
-    int b = j;
-    for (; b + 3 * NJ < nblk; b += 4 * NJ) {
-      c0 += __ldcg(partials + (size_t)b * NV + v);
-      c1 += __ldcg(partials + (size_t)(b + NJ) * NV + v);
-      c2 += __ldcg(partials + (size_t)(b + 2 * NJ) * NV + v);
-      c3 += __ldcg(partials + (size_t)(b + 3 * NJ) * NV + v);
-    }
-    for (; b < nblk; b += NJ) c0 += __ldcg(partials + (size_t)b * NV + v);
-    part[j][v] = (c0 + c1) + (c2 + c3);
+    double c = 0.0;
+    for (int g = j; g < ngrp; g += NJ) c += __ldcg(gpart + (size_t)g * NV + v);
+    part[j][v] = c;
   }
   __syncthreads();
+  if (threadIdx.x == 0) a.rs.tickets[MAXGRP] = 0u;
   DevState* st = a.st;
   for (int i = threadIdx.x; i < NV; i += T1_NT) {
     double v = part[0][i];
@@ -816,7 +839,6 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
       st->rr = v;
     }
   }
-  if (threadIdx.x == 0) a.rs.tickets[0] = 0u;
   __threadfence();
   __syncthreads();
   if (threadIdx.x < 32) run_epilogue(a.epi, ew);
@@ -934,11 +956,20 @@ __global__ void __launch_bounds__(NT, 2) multidot_kernel(MdArgs<T> a) {
     if (a.self) acc.add(C, xv, xv);
   }
   const int m = a.ny + a.self;
-  double fin[32];
+  if constexpr (sizeof(T) == 4) {
+    // FP32 partials: FP32 warp stage over the C + 1 slots only
+    constexpr int M = pow2_ge(C + 1);
+    float fin[M];
 #pragma unroll
-  for (int i = 0; i < 32; ++i)
-    fin[i] = i < C && i < a.ny ? acc.get(i < C ? i : 0) : (i == a.ny ? acc.get(C) : 0.0);
-  block_reduce<32>(fin, m, smem_w, red);
+    for (int i = 0; i < M; ++i) fin[i] = i < C && i < a.ny ? acc.v[i < C ? i : 0] : (i == a.ny ? acc.v[C] : 0.f);
+    block_reduce_f32<M>(fin, m, smem_w, red);
+  } else {
+    double fin[32];
+#pragma unroll
+    for (int i = 0; i < 32; ++i)
+      fin[i] = i < C && i < a.ny ? acc.get(i < C ? i : 0) : (i == a.ny ? acc.get(C) : 0.0);
+    block_reduce<32>(fin, m, smem_w, red);
+  }
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
   if (!groups_done(a.rs, t, a.nt, m, red, &s_last)) return;
   for (int i = threadIdx.x; i < a.nt * m; i += NT) {

@@ -221,6 +221,36 @@ __device__ __forceinline__ void block_reduce(double (&v)[M], int m, double* smem
   __syncthreads();
 }
 
+// block_reduce for FP32 partials (the FP32 inner form's dots): the warp stage
+// in FP32 (reduce-scatter), the warps' sums widened exactly and added in FP64
+// in block_reduce's order.  FP64 additions cost 64 times FP32 ones on this GPU;
+// the warp stage would otherwise dominate a short reduction kernel.
+template <int M>
+__device__ __forceinline__ void block_reduce_f32(float (&v)[M], int m, double* smem_w, double* red) {
+  static_assert(M >= 1 && M <= 32 && (M & (M - 1)) == 0, "M must be a power of two <= 32");
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  RedScatterT<float, M, 16, M>::run(v, lane);
+  constexpr int SPLIT_BITS = M >= 32 ? 5 : (M >= 16 ? 4 : (M >= 8 ? 3 : (M >= 4 ? 2 : (M >= 2 ? 1 : 0))));
+  constexpr int LOW_MASK = (1 << (5 - SPLIT_BITS)) - 1;
+  const int idx = rs_index<M>(lane);
+  if ((lane & LOW_MASK) == 0 && idx < m) smem_w[w * MAXRED + idx] = widen_f32(v[0]);
+  __syncthreads();
+  if (threadIdx.x < m) {
+    const int nw = (int)(blockDim.x >> 5);
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int j = 0;
+    for (; j + 3 < nw; j += 4) {
+      s0 += smem_w[j * MAXRED + threadIdx.x];
+      s1 += smem_w[(j + 1) * MAXRED + threadIdx.x];
+      s2 += smem_w[(j + 2) * MAXRED + threadIdx.x];
+      s3 += smem_w[(j + 3) * MAXRED + threadIdx.x];
+    }
+    for (; j < nw; ++j) s0 += smem_w[j * MAXRED + threadIdx.x];
+    red[threadIdx.x] = (s0 + s1) + (s2 + s3);
+  }
+  __syncthreads();
+}
+
 // Sum the m values of the nblk per-block partials at base (partial b, value i
 // at base[b * MAXRED + i]) into red[0..m) in a fixed order: warp w takes
 // values w, w + nwarps, ...; its lanes stride over the blocks with four

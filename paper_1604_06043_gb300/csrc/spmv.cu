@@ -131,33 +131,49 @@ __device__ __forceinline__ void acc_row(const SpmvArgs<T>& a, int row, T yv, Dot
   }
 }
 
+// The block's sums of the fused dots into red[0..m): (P^T y [np], y.y?,
+// b.b?) compacted into the first m slots; FP64 partials through block_reduce,
+// FP32 ones through block_reduce_f32 (FP32 warp stage).  The s dots of a
+// cycle's products fill 8 of the 16 slots: only those are reduced.
+template <typename T, int NP>
+__device__ __forceinline__ void block_reduce_acc(const SpmvArgs<T>& a, const DotAcc<T, NP>& acc, int m,
+                                                 double* smem_w, double* red) {
+  constexpr int M = pow2_at_least(NP + 2);
+  using V = std::conditional_t<sizeof(T) == 4, float, double>;
+  V fin[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    V v = V(0);
+    if (i < NP && i < a.np) v = acc.v[i < NP ? i : 0];
+    if (a.self && i == a.np) v = acc.v[NP];
+    if (a.bdot && i == a.np + a.self) v = acc.v[NP + 1];
+    fin[i] = v;
+  }
+  auto reduce = [&](auto& f, auto mtag) {
+    constexpr int MM = decltype(mtag)::value;
+    if constexpr (sizeof(T) == 4)
+      block_reduce_f32<MM>(f, m, smem_w, red);
+    else
+      block_reduce<MM>(f, m, smem_w, red);
+  };
+  if constexpr (M > 8) {
+    if (m <= 8)
+      reduce(reinterpret_cast<V(&)[8]>(fin), std::integral_constant<int, 8>{});
+    else
+      reduce(fin, std::integral_constant<int, M>{});
+  } else {
+    reduce(fin, std::integral_constant<int, M>{});
+  }
+}
+
 template <typename T, int NP>
 __device__ __forceinline__ void finish(const SpmvArgs<T>& a, const DotAcc<T, NP>& acc) {
-  constexpr int M = pow2_at_least(NP + 2);
   __shared__ double smem_w[SNWARP * MAXRED];
   __shared__ double red[MAXRED];
   __shared__ int s_last;
   __shared__ EpiScratch ew;
   const int m = a.np + a.self + a.bdot;
-  // compact (P^T y [np], y.y?, b.b?) into the first m slots
-  double fin[M];
-#pragma unroll
-  for (int i = 0; i < M; ++i) {
-    double v = 0.0;
-    if (i < NP && i < a.np) v = acc.get(i < NP ? i : 0);
-    if (a.self && i == a.np) v = acc.get(NP);
-    if (a.bdot && i == a.np + a.self) v = acc.get(NP + 1);
-    fin[i] = v;
-  }
-  // the s dots of a cycle's products fill 8 of the 16 slots: reduce only those
-  if constexpr (M > 8) {
-    if (m <= 8)
-      block_reduce<8>(reinterpret_cast<double(&)[8]>(fin), m, smem_w, red);
-    else
-      block_reduce<M>(fin, m, smem_w, red);
-  } else {
-    block_reduce<M>(fin, m, smem_w, red);
-  }
+  block_reduce_acc<T, NP>(a, acc, m, smem_w, red);
   if (grid_reduce(a.rs, 0, blockIdx.x, gridDim.x, m, red, &s_last)) {
     if (threadIdx.x < m) a.out[threadIdx.x] = red[threadIdx.x];
     __threadfence();
@@ -439,7 +455,6 @@ __device__ __forceinline__ void level_combine(int n, int s, const T* base, T* ou
 template <typename T, int NP>
 __device__ __forceinline__ bool level_product(const LevelStepArgs<T>& L, const T* x, T* y, unsigned int& gen,
                                               double* smem_w, double* red, int* s_ok) {
-  constexpr int M = pow2_at_least(NP + 2);
   const int s = L.s;
   if (blockIdx.x < L.nb_prod) {
     SpmvArgs<T> a{x, y, nullptr, L.P, L.ldp, s, 0, 0, nullptr, Epi{EPI_NONE, 0, 0, s, 0, nullptr},
@@ -447,17 +462,7 @@ __device__ __forceinline__ bool level_product(const LevelStepArgs<T>& L, const T
     DotAcc<T, NP> acc;
     acc.zero();
     sell_pass<T, NP, 1>(L.A, a, acc, L.nb_prod);
-    double fin[M];
-#pragma unroll
-    for (int i = 0; i < M; ++i) fin[i] = (i < NP && i < s) ? acc.get(i < NP ? i : 0) : 0.0;
-    if constexpr (M > 8) {
-      if (s <= 8)
-        block_reduce<8>(reinterpret_cast<double(&)[8]>(fin), s, smem_w, red);
-      else
-        block_reduce<M>(fin, s, smem_w, red);
-    } else {
-      block_reduce<M>(fin, s, smem_w, red);
-    }
+    block_reduce_acc<T, NP>(a, acc, s, smem_w, red);
     if (threadIdx.x < s) L.partials[(size_t)blockIdx.x * MAXRED + threadIdx.x] = red[threadIdx.x];
   }
   if (!grid_sync(L.bar, ++gen, L.flag, L.spin_limit, s_ok)) return false;
