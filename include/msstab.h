@@ -122,7 +122,7 @@ typedef struct msstab_options {
                               s + 1 products with A with their projections and small solves, the
                               eta steps) runs as ONE cooperative launch of one 1024-thread block
                               per SM whose blocks meet at grid barriers; results are those of 0 bit
-                              for bit.  2: the FP32 inner cycles too (measured 2 % slower than their
+                              for bit.  2: the FP32 inner cycles too (measured 6 % slower than their
                               graph-replayed launches at 128^3: the barriers and per-block solves
                               cost what the shorter FP32 products save).  0: one launch per step.
                               Used with the SELL format and without the preconditioner (else 0) */
