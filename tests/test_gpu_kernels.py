@@ -298,6 +298,63 @@ def test_level_step_equals_algorithm1(msstab, case, s, ell, k):
     assert np.all(np.abs(gram.cpu().numpy().reshape(ell + 1, ell + 1) - G) <= TOL64 * Gs)
 
 
+@pytest.mark.parametrize("k", [0, 1, 3])
+def test_level_updates_fp32_four_rows(msstab, case, k):
+    """The FP32 inner form's gamma, eta and lower-level updates of level step k
+    (products with A left out: they only touch levels above k) with the
+    solver's vector layout, so that every kernel takes four rows per thread,
+    against Algorithm 1's order on the same FP32 values; and bit for bit
+    against the row-by-row kernels, which run when the columns are not
+    16-byte aligned (leading dimension n = 35937)."""
+    w, A = case
+    s, ell = 8, 4
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 70 + k)
+    R = [r_.astype(np.float32).astype(np.float64) for r_ in R]
+    Vl = [v_.astype(np.float32).astype(np.float64) for v_ in Vl]
+    x0 = np.random.default_rng(15).standard_normal(A.n).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(16)
+    gamma = rng.standard_normal(s)
+    etas = rng.standard_normal((s, s)) * 0.5
+    Ro, Vo, xo = [r.copy() for r in R], [v.copy() for v in Vl], x0.copy()
+    O.gamma_update(Ro, Vo, xo, gamma, k)
+    for q in range(s):
+        O.eta_update(Ro, Vo, k, q, etas[q])
+    Rg, Vg = _pack(R, Vl)
+    n = A.n
+    runs = []
+    for pad in (True, False):
+        if pad:
+            Rt, Vt, xt = _padded(Rg, torch.float32), _padded(Vg, torch.float32), _padded(x0[None, :], torch.float32)[0]
+        else:
+            Rt, Vt, xt = _t(Rg, torch.float32), _t(Vg, torch.float32), _t(x0, torch.float32)
+        S.op_gamma_update(Rt, Vt, k, _t(gamma), prec=1)
+        for q in range(s):
+            S.op_eta_update(Rt, Vt, k, q, _t(etas[q]), prec=1)
+        S.op_lazy_update(Rt, Vt, xt, k, _t(gamma), _t(etas), prec=1)
+        runs.append((Rt[:, :n].clone(), Vt[:, :n].clone(), xt[:n].clone()))
+    (Ra, Va, xa), (Rb, Vb, xb) = runs
+    assert torch.equal(Ra, Rb) and torch.equal(Va, Vb) and torch.equal(xa, xb)
+    Rc, Vc = _unpack(Ra.cpu().numpy().astype(np.float64), Va.cpu().numpy().astype(np.float64), s, ell)
+    # the propagated scales of the same operations on absolute values
+    Sr = [np.abs(r) for r in R]
+    Sv = [np.abs(v) for v in Vl]
+    g = np.abs(gamma)
+    for i in range(k + 1):
+        Sr[i] = Sr[i] + g @ Sv[i + 1]
+    sx = np.abs(x0) + g @ Sv[0]
+    for q in range(s):
+        e = np.abs(etas[q])
+        new = [Sr[i + 1] + e @ np.concatenate([Sv[i + 2][:q], Sv[i + 1][q:]], axis=0) for i in range(-1, k + 1)]
+        for i, v in zip(range(-1, k + 1), new):
+            Sv[i + 1][q] = v
+    for i in range(k + 1):
+        assert np.all(np.abs(Rc[i] - Ro[i]) <= TOL32 * Sr[i]), ("r", i)
+    for i in range(k + 2):
+        assert np.all(np.abs(Vc[i] - Vo[i]) <= TOL32 * Sv[i]), ("V", i - 1)
+    assert np.all(np.abs(xa.cpu().numpy().astype(np.float64) - xo) <= TOL32 * sx)
+
+
 def _level_step_scales(A, R, Vl, x0, gamma, etas, k):
     """The propagated magnitudes of one level step of Algorithm 1 (the same
     sequence of operations as the oracle, on absolute values)."""
@@ -338,14 +395,29 @@ def test_tau_update(msstab, case, s, ell):
         assert np.all(np.abs(Vc[0][q] - U[q]) <= TOL64 * sc(Vl[0][q], [(tau[i - 1], Vl[i][q]) for i in range(1, ell + 1)]))
 
 
-@pytest.mark.parametrize("prec,s,ell,upd", [(0, 8, 4, True), (0, 4, 1, True), (1, 8, 1, True), (1, 5, 1, True),
-                                              (1, 4, 1, True), (1, 8, 1, False), (1, 16, 1, True), (1, 8, 2, True)])
-def test_tau_step_projections(msstab, case, prec, s, ell, upd):
+def _padded(a, dtype):
+    """a (rows x n) in a device array whose leading dimension is n rounded up
+    to 64 elements, as the solver's workspace lays its vectors out."""
+    rows, n = a.shape
+    ld = (n + 63) // 64 * 64
+    out = torch.zeros((rows, ld), dtype=dtype, device=DEV)
+    out[:, :n] = _t(a, dtype)
+    return out
+
+
+@pytest.mark.parametrize("prec,s,ell,upd,pad", [(0, 8, 4, True, False), (0, 4, 1, True, False),
+                                                  (1, 8, 1, True, True), (1, 5, 1, True, True),
+                                                  (1, 4, 1, True, True), (1, 8, 1, False, True),
+                                                  (1, 8, 1, True, False), (1, 16, 1, True, True),
+                                                  (1, 8, 2, True, True)])
+def test_tau_step_projections(msstab, case, prec, s, ell, upd, pad):
     """The degree-l step with the fused projections of the next cycle's first
     gamma solve (P^T V^(0), P^T r, r.r), in FP64 and in the FP32 inner form
-    (l = 1, s <= 8: warps over chunks of vector groups; otherwise the
-    per-group kernel), against the oracle's update and plain FP64 dots of the
-    oracle's vectors."""
+    (l = 1, s <= 8 and 16-byte aligned columns: four rows per thread, warps
+    over chunks of vector groups; otherwise the per-group kernel), against the
+    oracle's update and plain FP64 dots of the oracle's vectors.  The padded
+    cases lay the vectors out as the solver does (leading dimension a multiple
+    of 64), the others with leading dimension n (35937: not 16-byte aligned)."""
     w, A = case
     S = _solver(msstab, A, s, ell)
     R, Vl = _levels(A.n, s, ell, 90 + s + ell)
@@ -362,10 +434,15 @@ def test_tau_step_projections(msstab, case, prec, s, ell, upd):
     t_ = tau if upd else np.zeros(ell)
     r, x, U, V = O.tau_update(R, Vl, x0, t_)
     Rg, Vg = _pack(R, Vl)
-    Rt, Vt, xt = _t(Rg, dt), _t(Vg, dt), _t(x0, dt)
+    if pad:
+        Rt, Vt, xt = _padded(Rg, dt), _padded(Vg, dt), _padded(x0[None, :], dt)[0]
+    else:
+        Rt, Vt, xt = _t(Rg, dt), _t(Vg, dt), _t(x0, dt)
     out = torch.zeros(s * s + s + 1, dtype=torch.float64, device=DEV)
     S.op_tau_step(Rt, Vt, xt, _t(tau), out, do_update=upd, prec=prec)
-    Rc, Vc = _unpack(Rt.cpu().numpy().astype(np.float64), Vt.cpu().numpy().astype(np.float64), s, ell)
+    n = A.n
+    Rc, Vc = _unpack(Rt[:, :n].cpu().numpy().astype(np.float64), Vt[:, :n].cpu().numpy().astype(np.float64), s, ell)
+    xt = xt[:n]
     sc = lambda a, terms: np.abs(a) + sum(abs(c_) * np.abs(v_) for c_, v_ in terms)
     sr = sc(R[0], [(t_[i - 1], R[i]) for i in range(1, ell + 1)])
     assert np.all(np.abs(Rc[0] - r) <= tol * sr)
