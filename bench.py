@@ -789,6 +789,10 @@ def main(argv=None):
             "config": workload_config(w, A.n, A.nnz, W, K, args.form, world),
             "mvs_per_system": round(statistics.mean(mvs), 2),
             "cycles_per_system": round(sum(t["cycles"] for t in timed) / K, 3),
+            # time per cycle: the FP32 inner form's products count is a draw of
+            # its rounding (it changes with the FP32 summation order), the time
+            # per cycle is not
+            "ms_per_cycle": round(T / max(1, sum(t["cycles"] for t in timed)), 4),
             "kernel_timing_pass": {"ms_per_system": round(kt0.elapsed_time(kt1) / K, 4),
                                    "note": "same systems, launches one by one with CUDA events around each "
                                            "(the timed run replays each cycle as a CUDA graph)"},
