@@ -176,7 +176,7 @@ def test_spmv_dot_fp32(msstab, case):
     assert np.all(np.abs(dd[:s] - ref) <= TOL32 * (np.abs(P) @ np.abs(yv)))
 
 
-@pytest.mark.parametrize("nx,ny", [(1, 1), (5, 5), (16, 16), (3, 9)])
+@pytest.mark.parametrize("nx,ny", [(1, 1), (2, 4), (5, 5), (16, 16), (3, 9)])
 def test_multidot(msstab, case, nx, ny):
     w, A = case
     S = _solver(msstab, A, 4, 2)
@@ -188,6 +188,24 @@ def test_multidot(msstab, case, nx, ny):
     ref = X @ Y.T
     scale = np.abs(X) @ np.abs(Y).T
     assert np.all(np.abs(out.cpu().numpy().reshape(nx, ny) - ref) <= TOL64 * scale)
+
+
+@pytest.mark.parametrize("nx,ny", [(2, 2), (1, 4), (4, 8), (3, 16)])
+def test_multidot_fp32(msstab, case, nx, ny):
+    """FP32 multi-dot (the Gram of the FP32 inner form's degree-1 step and the
+    Arnoldi and Cholesky QR projections): FP32 partials per thread and warp,
+    FP64 across warps and blocks, against FP64 dots of the same FP32 values."""
+    w, A = case
+    S = _solver(msstab, A, 4, 2)
+    rng = np.random.default_rng(nx * 1000 + ny)
+    X = rng.standard_normal((nx, A.n)).astype(np.float32)
+    Y = rng.standard_normal((ny, A.n)).astype(np.float32)
+    out = torch.zeros(nx * ny, dtype=torch.float64, device=DEV)
+    S.op_multidot(_t(X, torch.float32), _t(Y, torch.float32), out, prec=1)
+    Xd, Yd = X.astype(np.float64), Y.astype(np.float64)
+    ref = Xd @ Yd.T
+    scale = np.abs(Xd) @ np.abs(Yd).T
+    assert np.all(np.abs(out.cpu().numpy().reshape(nx, ny) - ref) <= TOL32 * scale)
 
 
 # ---------------------------------------------------------------------------
