@@ -323,9 +323,14 @@ msstab_status msstab_op_tau_update(msstab_t h, int32_t prec, void* d_R, void* d_
  * cycle's first gamma solve uses.  d_out (FP64, s*s + s + 1 values):
  * d_out[q*s + c] = p_c . v_q^(0), d_out[s*s + c] = p_c . r^(0),
  * d_out[s*s + s] = r^(0) . r^(0), with P the handle's cut space in the
- * precision prec.  Layout of d_R, d_V, d_x as msstab_op_tau_update. */
+ * precision prec.  Layout of d_R, d_V, d_x as msstab_op_tau_update.
+ * d_lazy_gamma, d_lazy_eta (both NULL, or gamma_0 and the s x s eta of level
+ * step 0, row q = eta_q): first the updates of msstab_op_lazy_update with
+ * k = 0, in the same pass -- the FP32 inner form with l = 1 does this when
+ * the columns are 16-byte aligned and n % 4 == 0 (else MSSTAB_ERR_INVALID_ARG). */
 msstab_status msstab_op_tau_step(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x, int64_t ld,
-                                 const double* d_tau, int32_t do_update, double* d_out);
+                                 const double* d_tau, int32_t do_update, const double* d_lazy_gamma,
+                                 const double* d_lazy_eta, double* d_out);
 
 /* Solve the n x n system d_M z = d_rhs (d_M row-major, n <= 16) on the device by
  * Gaussian elimination with partial pivoting; *d_flag = 1 if the pivot of a

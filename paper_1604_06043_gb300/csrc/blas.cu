@@ -487,6 +487,9 @@ struct TauArgs {
   const T* Pb;   // block-partitioned P (see pblock_col), or NULL
   const T* Pil;  // P interleaved by row (row stride sp), or NULL
   int sp;
+  const double* lgamma;   // non-NULL: first the level -1 updates of level step 0 (see lazy_update)
+  const double* leta;     //   with gamma_0 and eta rows q at leta + q * leta_ld
+  int leta_ld;
 };
 
 // L: compile-time bound on the degree l (1, 2, 4 or 8): level arrays of L + 2
@@ -654,7 +657,7 @@ constexpr int T1_NW = T1_G * T1_SLABS;
 constexpr int T1_NT = 32 * T1_NW;
 constexpr int T1_ROWS = 4 * 32 * T1_SLABS;   // rows of a block per iteration
 
-template <int S>
+template <int S, bool LZ>
 __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
   constexpr int GPC = (S + 1 + T1_G - 1) / T1_G;   // groups per chunk
   constexpr int NL = GPC * S + 1;                 // a thread's values: P^T of its groups, then r.r
@@ -743,9 +746,116 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
   };
   const int64_t quads = a.n / 4;
   const int64_t stride = (int64_t)gridDim.x * (32 * T1_SLABS);
-  for (int64_t gi = (int64_t)blockIdx.x * (32 * T1_SLABS) + slab * 32 + lane; gi < quads; gi += stride)
-    do_rows(float4{}, gi);
-  if (blockIdx.x == 0 && slab == 0 && lane < a.n - quads * 4) do_rows(float{}, quads * 4 + lane);
+  if constexpr (!LZ) {
+    for (int64_t gi = (int64_t)blockIdx.x * (32 * T1_SLABS) + slab * 32 + lane; gi < quads; gi += stride)
+      do_rows(float4{}, gi);
+    if (blockIdx.x == 0 && slab == 0 && lane < a.n - quads * 4) do_rows(float{}, quads * 4 + lane);
+  } else {
+    // First the level -1 updates of level step 0 (lazy_update with k = 0):
+    // x += V^(-1) gamma_0 and v_q^(-1) = r^(0) - [V^(0)_{0:q-1}, V^(-1)_{q:s-1}] eta_q, each
+    // row with lazy_update's operations in its order; every chunk needs all of a row's V^(-1)
+    // and V^(0) entries, so the slab's rows go through shared memory, between two barriers
+    // of the slab's warps per iteration (n % 4 == 0, no tail).  The updated
+    // x and V^(-1) then enter the degree-1 step in registers.
+    __shared__ float4 stg[T1_SLABS][2 * S + 1][32];
+    __shared__ float gs[SMAX];
+    __shared__ float es[SMAX * SMAX];
+    if (threadIdx.x < s) gs[threadIdx.x] = (float)a.lgamma[threadIdx.x];
+    for (int i = threadIdx.x; i < s * s; i += T1_NT) es[(i / s) * SMAX + (i % s)] = (float)a.leta[(i / s) * a.leta_ld + (i % s)];
+    __syncthreads();
+    // the T1_G warps of a slab meet at their own barrier (ids 1.., T1_G * 32 threads), so
+    // that the slabs stream independently
+    auto slab_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + slab), "r"(T1_G * 32) : "memory"); };
+    for (int64_t base = (int64_t)blockIdx.x * (32 * T1_SLABS); base < quads; base += stride) {
+      const int64_t gi = base + slab * 32 + lane;
+      const bool act = gi < quads;
+      auto ld_v = [&](const float* p) -> float4 { return reinterpret_cast<const float4*>(p)[gi]; };
+      auto st_v = [&](float* p, const float4& v) { reinterpret_cast<float4*>(p)[gi] = v; };
+      float4 pc[S], v0[GPC], vm[GPC], v1[GPC];
+      if (act) {
+        if (a.proj) {
+#pragma unroll
+          for (int c = 0; c < S; ++c)
+            if (c < s) pc[c] = __ldg(reinterpret_cast<const float4*>(a.P + (int64_t)c * a.ldp) + gi);
+        }
+#pragma unroll
+        for (int i = 0; i < GPC; ++i) {
+          const int g = chunk * GPC + i;
+          if (g > s) break;
+          v0[i] = ld_v(col(g, 0));
+          vm[i] = ld_v(col(g, 1));
+          v1[i] = ld_v(col(g, 2));
+          if (g == 0)
+            stg[slab][2 * S][lane] = v0[i];          // r^(0)
+          else {
+            stg[slab][g - 1][lane] = vm[i];          // v_{g-1}^(-1), before the update
+            stg[slab][S + g - 1][lane] = v0[i];      // v_{g-1}^(0)
+          }
+        }
+      }
+      slab_sync();
+      if (act) {
+#pragma unroll
+        for (int i = 0; i < GPC; ++i) {
+          const int g = chunk * GPC + i;
+          if (g > s) break;
+          if (g == 0) {
+            float4 xv = vm[i];
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+              if (j >= s) break;
+              fma4(xv, gs[j], stg[slab][j][lane]);
+            }
+            vm[i] = xv;
+          } else {
+            const int q = g - 1;
+            float4 v = stg[slab][2 * S][lane];
+#pragma unroll
+            for (int j = 0; j < S; ++j) {
+              if (j >= s) break;
+              fnma4(v, es[q * SMAX + j], j < q ? stg[slab][S + j][lane] : stg[slab][j][lane]);
+            }
+            vm[i] = v;
+          }
+        }
+      }
+      slab_sync();
+      if (act) {
+#pragma unroll
+        for (int i = 0; i < GPC; ++i) {
+          const int g = chunk * GPC + i;
+          if (g > s) break;
+          float4 nv = v0[i], nm = vm[i];
+          if (g == 0) {
+            nv.x -= tau1 * v1[i].x; nv.y -= tau1 * v1[i].y; nv.z -= tau1 * v1[i].z; nv.w -= tau1 * v1[i].w;
+            nm.x += tau1 * v0[i].x; nm.y += tau1 * v0[i].y; nm.z += tau1 * v0[i].z; nm.w += tau1 * v0[i].w;
+          } else {
+            nv.x -= tau1 * v1[i].x; nv.y -= tau1 * v1[i].y; nv.z -= tau1 * v1[i].z; nv.w -= tau1 * v1[i].w;
+            nm.x -= tau1 * v0[i].x; nm.y -= tau1 * v0[i].y; nm.z -= tau1 * v0[i].z; nm.w -= tau1 * v0[i].w;
+          }
+          st_v(col(g, 0), nv);
+          st_v(col(g, 1), nm);
+          if (g == 0 && a.xbak) st_v(a.xbak, nm);
+          if (a.proj) {
+#pragma unroll
+            for (int c = 0; c < S; ++c) {
+              if (c >= s) break;
+              acc[i * S + c] = fmaf(nv.x, pc[c].x, acc[i * S + c]);
+              acc[i * S + c] = fmaf(nv.y, pc[c].y, acc[i * S + c]);
+              acc[i * S + c] = fmaf(nv.z, pc[c].z, acc[i * S + c]);
+              acc[i * S + c] = fmaf(nv.w, pc[c].w, acc[i * S + c]);
+            }
+            if (g == 0) {
+              acc[NL - 1] = fmaf(nv.x, nv.x, acc[NL - 1]);
+              acc[NL - 1] = fmaf(nv.y, nv.y, acc[NL - 1]);
+              acc[NL - 1] = fmaf(nv.z, nv.z, acc[NL - 1]);
+              acc[NL - 1] = fmaf(nv.w, nv.w, acc[NL - 1]);
+            }
+          }
+        }
+      }
+    }
+  }
   if (!a.proj) return;
 #pragma unroll
   for (int r0 = 0; r0 < NLP; r0 += 32) {
@@ -856,23 +966,42 @@ static void launch_tau(const Ctx& c, const TauArgs<T>& a) {
   tau_kernel<T, L><<<(int)(chunks * nt), NT, 0, c.stream>>>(a);
 }
 
+template <int S, bool LZ>
+static void launch_tau1(const Ctx& c, const TauArgs<float>& a, int64_t need) {
+  static int cap = max_grid_nt(tau1_f32_kernel<S, LZ>, c, T1_NT);
+  tau1_f32_kernel<S, LZ><<<clamp_grid(need, cap), T1_NT, 0, c.stream>>>(a);
+}
+
+template <typename T>
+static bool tau1_applies(int n, int s, int ell, const T* R, const T* V, const T* x, const T* xbak, int64_t ld,
+                         const T* P, int64_t ldp, const T* Pb) {
+  (void)n;
+  return sizeof(T) == 4 && ell == 1 && Pb == nullptr && s <= 8 && ld % 4 == 0 && ldp % 4 == 0 && aligned16(R) &&
+         aligned16(V) && aligned16(x) && aligned16(P) && (xbak == nullptr || aligned16(xbak));
+}
+
+template <typename T>
+bool tau_fuses_lazy(int n, int s, int ell, const T* R, const T* V, const T* x, const T* xbak, int64_t ld,
+                    const T* P, int64_t ldp, const T* Pb) {
+  return tau1_applies(n, s, ell, R, V, x, xbak, ld, P, ldp, Pb) && n % 4 == 0;
+}
+
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi, const T* Pb, const T* Pil, int sp) {
+                       Epi epi, const T* Pb, const T* Pil, int sp, const double* lgamma, const double* leta,
+                       int leta_ld) {
   TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs, Pb,
-               Pil, sp};
+               Pil, sp, lgamma, leta, leta_ld};
+  if (lgamma && !(do_update && tau_fuses_lazy(n, s, ell, R, V, x, xbak, ld, P, ldp, Pb)))
+    return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
-    const bool vec = ld % 4 == 0 && ldp % 4 == 0 && aligned16(R) && aligned16(V) && aligned16(x) && aligned16(P) &&
-                     (xbak == nullptr || aligned16(xbak));
-    if (ell == 1 && Pb == nullptr && s <= 8 && vec) {
+    if (tau1_applies(n, s, ell, R, V, x, xbak, ld, P, ldp, Pb)) {
       const int64_t need = ((int64_t)n + T1_ROWS - 1) / T1_ROWS;
       if (s <= 4) {
-        static int cap = max_grid_nt(tau1_f32_kernel<4>, c, T1_NT);
-        tau1_f32_kernel<4><<<clamp_grid(need, cap), T1_NT, 0, c.stream>>>(a);
+        if (lgamma) launch_tau1<4, true>(c, a, need); else launch_tau1<4, false>(c, a, need);
       } else {
-        static int cap = max_grid_nt(tau1_f32_kernel<8>, c, T1_NT);
-        tau1_f32_kernel<8><<<clamp_grid(need, cap), T1_NT, 0, c.stream>>>(a);
+        if (lgamma) launch_tau1<8, true>(c, a, need); else launch_tau1<8, false>(c, a, need);
       }
       return cudaGetLastError();
     }
@@ -1186,7 +1315,9 @@ cudaError_t f64_to_f32_n(const Ctx& c, int64_t n, const double* x, float* y, dou
                                       const double*, int);                                                \
   template cudaError_t tau_update<T>(const Ctx&, int, int, int, T*, T*, T*, T*, int64_t, const double*,   \
                                      const T*, int64_t, int, int, DevState*, Epi, const T*, const T*,    \
-                                     int);                                                               \
+                                     int, const double*, const double*, int);                            \
+  template bool tau_fuses_lazy<T>(int, int, int, const T*, const T*, const T*, const T*, int64_t, const T*,  \
+                                  int64_t, const T*);                                                    \
   template cudaError_t cols_axpy<T>(const Ctx&, int, T*, const T*, int64_t, int, const double*);          \
   template cudaError_t scale_rsqrt<T>(const Ctx&, int, const T*, T*, const double*);                      \
   template cudaError_t tri_apply<T>(const Ctx&, int, int, T*, T*, int64_t, const double*);

@@ -101,7 +101,16 @@ cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
-                       Epi epi, const T* Pb = nullptr, const T* Pil = nullptr, int sp = 0);
+                       Epi epi, const T* Pb = nullptr, const T* Pil = nullptr, int sp = 0,
+                       const double* lgamma = nullptr, const double* leta = nullptr, int leta_ld = 0);
+
+// Whether tau_update can run the level -1 updates of level step 0 (lazy_update
+// with k = 0, gamma and eta passed as lgamma, leta) in the same pass (the FP32
+// degree-1 step with 16-byte aligned columns, n % 4 == 0); results are those of
+// lazy_update followed by tau_update bit for bit.
+template <typename T>
+bool tau_fuses_lazy(int n, int s, int ell, const T* R, const T* V, const T* x, const T* xbak, int64_t ld,
+                    const T* P, int64_t ldp, const T* Pb);
 
 // w -= sum_{c<nc} h[c] U_c (h: FP64 device), columns U_c at U + c*ld.
 template <typename T>

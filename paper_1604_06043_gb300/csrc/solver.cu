@@ -512,14 +512,18 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
     // ---- one cycle: level steps k = 0..l-1, the degree-l step, and the
     // residual replacement; the same launch sequence every cycle ----
     const bool replaced = ctl.replace_every > 0 && (out.cycles + 1) % ctl.replace_every == 0;
+    // the FP32 degree-1 step takes the level -1 updates of level step 0 in its own pass
+    // (same results bit for bit, one pass over V^(-1), V^(0), r^(0) and x instead of two)
+    const bool fuse_lazy = ell == 1 && tau_fuses_lazy<T>(n, s, ell, w.R, w.V, w.X, w.XB2, ld, P, ld, w.Pb);
     auto launch_cycle = [&](const Ctx& c) -> msstab_status {
       for (int k = 0; k < ell; ++k) {
         if (h->level && (prec == 0 || h->opt.persistent >= 2)) {
           // the gamma step, the s + 1 products and the eta steps of level k in one launch
           LAUNCH(MSSTAB_K_LEVEL, level_step<T>(c, h->A, w.R, w.V, ld, s, k, k + 1 < ell ? 1 : 0, P, ld, w.Pil,
                                                w.sp, w.Pb, st, h->level_bar, h->spin_limit));
-          LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
-                                                 &st->eta[k * SMAX * SMAX], SMAX));
+          if (!fuse_lazy)
+            LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
+                                                   &st->eta[k * SMAX * SMAX], SMAX));
           continue;
         }
         LAUNCH(MSSTAB_K_GAMMA, gamma_eager<T>(c, n, s, w.R, w.V, ld, k, &st->gamma[k * SMAX]));
@@ -532,8 +536,9 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
           CKS(amv<T>(h, c, MSSTAB_K_SPMV_DOT, Vq(k, q), Vq(k + 1, q), nullptr, P, ld, s, 0, 0,
                                             &st->projV[((k + 1) * SMAX + q) * SMAX], next, w.Pil, w.sp, w.Pb));
         }
-        LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
-                                               &st->eta[k * SMAX * SMAX], SMAX));
+        if (!fuse_lazy)
+          LAUNCH(MSSTAB_K_LAZY, lazy_update<T>(c, n, s, w.R, w.V, w.X, ld, k, &st->gamma[k * SMAX],
+                                                 &st->eta[k * SMAX * SMAX], SMAX));
       }
       // degree-l minimisation
       {
@@ -543,7 +548,9 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
                                          epi_of(EPI_TAU, 0, 0)));
       }
       LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
-                                         epi_of(EPI_GAMMA, 0, 0), w.Pb, w.Pil, w.sp));
+                                         epi_of(EPI_GAMMA, 0, 0), w.Pb, w.Pil, w.sp,
+                                         fuse_lazy ? &st->gamma[0] : nullptr, fuse_lazy ? &st->eta[0] : nullptr,
+                                         SMAX));
       // residual replacement at the cycle end: r = b - A x with P^T r and ||r||^2 in the same pass
       // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
       // level step from P^T V (left by tau_update) in the epilogue
@@ -1726,7 +1733,8 @@ msstab_status msstab_op_tau_update(msstab_t h, int32_t prec, void* d_R, void* d_
 }
 
 msstab_status msstab_op_tau_step(msstab_t h, int32_t prec, void* d_R, void* d_V, void* d_x, int64_t ld,
-                                 const double* d_tau, int32_t do_update, double* d_out) {
+                                 const double* d_tau, int32_t do_update, const double* d_lazy_gamma,
+                                 const double* d_lazy_eta, double* d_out) {
   CKS(check_handle(h));
   CKS(check_prec(h, prec));
   if (ld < h->n) return fail(h, MSSTAB_ERR_INVALID_ARG, "ld < n");
@@ -1736,6 +1744,13 @@ msstab_status msstab_op_tau_step(msstab_t h, int32_t prec, void* d_R, void* d_V,
   if (!d_tau || !d_out) return fail(h, MSSTAB_ERR_INVALID_ARG, "NULL pointer");
   const Ctx c = h->ctx();
   const int s = h->s;
+  if ((d_lazy_gamma == nullptr) != (d_lazy_eta == nullptr))
+    return fail(h, MSSTAB_ERR_INVALID_ARG, "lazy gamma and eta: both or neither");
+  if (d_lazy_gamma && !(prec == 1 && do_update &&
+                        tau_fuses_lazy<float>(h->n, s, h->ell, (const float*)d_R, (const float*)d_V,
+                                              (const float*)d_x, nullptr, ld, h->w32.P, h->w32.ld, h->w32.Pb)))
+    return fail(h, MSSTAB_ERR_INVALID_ARG, "the fused lower-level updates need the FP32 degree-1 step, "
+                                           "16-byte aligned columns and n % 4 == 0");
   if (prec == 0)
     LAUNCH(MSSTAB_K_TAU, tau_update<double>(c, h->n, s, h->ell, (double*)d_R, (double*)d_V, (double*)d_x, nullptr,
                                             ld, d_tau, h->w64.P, h->w64.ld, do_update ? 1 : 0, 1, h->st,
@@ -1743,7 +1758,8 @@ msstab_status msstab_op_tau_step(msstab_t h, int32_t prec, void* d_R, void* d_V,
   else
     LAUNCH(MSSTAB_K_TAU, tau_update<float>(c, h->n, s, h->ell, (float*)d_R, (float*)d_V, (float*)d_x, nullptr,
                                            ld, d_tau, h->w32.P, h->w32.ld, do_update ? 1 : 0, 1, h->st,
-                                           epi_none(h), h->w32.Pb, h->w32.Pil, h->w32.sp));
+                                           epi_none(h), h->w32.Pb, h->w32.Pil, h->w32.sp, d_lazy_gamma,
+                                           d_lazy_eta, s));
   for (int q = 0; q < s; ++q)
     CK(cudaMemcpyAsync(d_out + (size_t)q * s, &h->st->projV[q * SMAX], sizeof(double) * s, cudaMemcpyDeviceToDevice,
                        h->stream));

@@ -113,7 +113,7 @@ _SIGS = {
     "msstab_op_eta_update": (_I32, [_P, _I32, _P, _P, _I64, _I32, _I32, _P]),
     "msstab_op_lazy_update": (_I32, [_P, _I32, _P, _P, _P, _I64, _I32, _P, _P, _P]),
     "msstab_op_tau_update": (_I32, [_P, _I32, _P, _P, _P, _I64, _P]),
-    "msstab_op_tau_step": (_I32, [_P, _I32, _P, _P, _P, _I64, _P, _I32, _P]),
+    "msstab_op_tau_step": (_I32, [_P, _I32, _P, _P, _P, _I64, _P, _I32, _P, _P, _P]),
     "msstab_op_small_solve": (_I32, [_P, _I32, _P, _P, _P, _P]),
     "msstab_op_tau_solve": (_I32, [_P, _I32, _P, _P]),
     "msstab_op_ilu_factor": (_I32, [_P, _P]),
@@ -365,9 +365,11 @@ class Solver:
         _check(load().msstab_op_tau_update(self._h, prec, _ptr(R), _ptr(V), _ptr(x), R.shape[1], _ptr(tau)),
                self._h)
 
-    def op_tau_step(self, R, V, x, tau, out, do_update: bool = True, prec: int = 0):
+    def op_tau_step(self, R, V, x, tau, out, do_update: bool = True, prec: int = 0, lazy_gamma=None,
+                    lazy_eta=None):
         _check(load().msstab_op_tau_step(self._h, prec, _ptr(R), _ptr(V), _ptr(x), R.shape[1], _ptr(tau),
-                                         1 if do_update else 0, _ptr(out)), self._h)
+                                         1 if do_update else 0, _ptr(lazy_gamma), _ptr(lazy_eta), _ptr(out)),
+               self._h)
 
     def op_small_solve(self, M, rhs, z, flag):
         _check(load().msstab_op_small_solve(self._h, rhs.numel(), _ptr(M), _ptr(rhs), _ptr(z), _ptr(flag)),

@@ -316,6 +316,56 @@ def test_level_step_equals_algorithm1(msstab, case, s, ell, k):
     assert np.all(np.abs(gram.cpu().numpy().reshape(ell + 1, ell + 1) - G) <= TOL64 * Gs)
 
 
+@pytest.mark.parametrize("s", [8, 5, 4])
+def test_tau_step_with_fused_lower_level_updates(msstab, s):
+    """The FP32 degree-1 step that first applies the level -1 updates of level
+    step 0 (x += V^(-1) gamma_0, v_q^(-1) = r^(0) - [V^(0)_{0:q-1}, V^(-1)_{q:s-1}]
+    eta_q) in the same pass equals the lower-level update followed by the
+    degree-1 step bit for bit (vectors and projections), and both equal the
+    oracle's Algorithm-1 order within the FP32 bound."""
+    w = pb.WORKLOADS["convdiff3d_24"]      # n = 13824: a multiple of 4
+    A = w.matrix()
+    ell = 1
+    S = _solver(msstab, A, s, ell)
+    R, Vl = _levels(A.n, s, ell, 120 + s)
+    R = [r_.astype(np.float32).astype(np.float64) for r_ in R]
+    Vl = [v_.astype(np.float32).astype(np.float64) for v_ in Vl]
+    x0 = np.random.default_rng(17).standard_normal(A.n).astype(np.float32).astype(np.float64)
+    rng = np.random.default_rng(18)
+    gamma = rng.standard_normal(s)
+    etas = rng.standard_normal((s, s)) * 0.5
+    tau = rng.standard_normal(ell)
+    Rg, Vg = _pack(R, Vl)
+    n = A.n
+    res = []
+    for fused in (False, True):
+        Rt, Vt, xt = _padded(Rg, torch.float32), _padded(Vg, torch.float32), _padded(x0[None, :], torch.float32)[0]
+        out = torch.zeros(s * s + s + 1, dtype=torch.float64, device=DEV)
+        if fused:
+            S.op_tau_step(Rt, Vt, xt, _t(tau), out, prec=1, lazy_gamma=_t(gamma), lazy_eta=_t(etas))
+        else:
+            S.op_lazy_update(Rt, Vt, xt, 0, _t(gamma), _t(etas), prec=1)
+            S.op_tau_step(Rt, Vt, xt, _t(tau), out, prec=1)
+        res.append((Rt[:, :n].clone(), Vt[:, :n].clone(), xt[:n].clone(), out.clone()))
+    (Ra, Va, xa, oa), (Rb, Vb, xb, ob) = res
+    assert torch.equal(Ra, Rb) and torch.equal(Va, Vb) and torch.equal(xa, xb) and torch.equal(oa, ob)
+    # the oracle: the level -1 part of the gamma and eta updates of level step 0, then the degree-1 step
+    Ro, Vo, xo = [r.copy() for r in R], [v.copy() for v in Vl], x0.copy()
+    xo = xo + gamma @ Vo[0]
+    newV = [Ro[0] - etas[q] @ np.concatenate([Vo[1][:q], Vo[0][q:]], axis=0) for q in range(s)]
+    Vo[0] = np.array(newV)
+    r, x, U, V = O.tau_update(Ro, Vo, xo, tau)
+    Rc, Vc = _unpack(Ra.cpu().numpy().astype(np.float64), Va.cpu().numpy().astype(np.float64), s, ell)
+    sc_u = [np.abs(R[0]) + np.abs(etas[q]) @ np.abs(np.concatenate([Vl[1][:q], Vl[0][q:]], axis=0))
+            for q in range(s)]
+    for q in range(s):
+        assert np.all(np.abs(Vc[0][q] - U[q]) <= TOL32 * (sc_u[q] + abs(tau[0]) * np.abs(Vl[1][q]))), q
+        assert np.all(np.abs(Vc[1][q] - V[q]) <= TOL32 * (np.abs(Vl[1][q]) + abs(tau[0]) * np.abs(Vl[2][q]))), q
+    sx = np.abs(x0) + np.abs(gamma) @ np.abs(Vl[0]) + abs(tau[0]) * np.abs(R[0])
+    assert np.all(np.abs(xa.cpu().numpy().astype(np.float64) - x) <= TOL32 * sx)
+    assert np.all(np.abs(Rc[0] - r) <= TOL32 * (np.abs(R[0]) + abs(tau[0]) * np.abs(R[1])))
+
+
 @pytest.mark.parametrize("k", [0, 1, 3])
 def test_level_updates_fp32_four_rows(msstab, case, k):
     """The FP32 inner form's gamma, eta and lower-level updates of level step k
