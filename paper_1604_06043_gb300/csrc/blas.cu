@@ -757,7 +757,12 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
     // and V^(0) entries, so the slab's rows go through shared memory, between two barriers
     // of the slab's warps per iteration (n % 4 == 0, no tail).  The updated
     // x and V^(-1) then enter the degree-1 step in registers.
-    __shared__ float4 stg[T1_SLABS][2 * S + 1][32];
+    // two staging buffers (dynamic shared memory), [buffer][slab][column][lane]: the
+    // iteration after next writes a buffer only after every warp of the slab has passed
+    // the next iteration's barrier, i.e. finished reading it, so one barrier per iteration
+    extern __shared__ __align__(16) unsigned char t1_dyn[];
+    float4* stgb = reinterpret_cast<float4*>(t1_dyn);
+    auto stg = [&](int buf, int c) -> float4& { return stgb[((buf * T1_SLABS + slab) * (2 * S + 1) + c) * 32 + lane]; };
     __shared__ float gs[SMAX];
     __shared__ float es[SMAX * SMAX];
     if (threadIdx.x < s) gs[threadIdx.x] = (float)a.lgamma[threadIdx.x];
@@ -766,7 +771,9 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
     // the T1_G warps of a slab meet at their own barrier (ids 1.., T1_G * 32 threads), so
     // that the slabs stream independently
     auto slab_sync = [&]() { asm volatile("bar.sync %0, %1;" ::"r"(1 + slab), "r"(T1_G * 32) : "memory"); };
-    for (int64_t base = (int64_t)blockIdx.x * (32 * T1_SLABS); base < quads; base += stride) {
+    int it = 0;
+    for (int64_t base = (int64_t)blockIdx.x * (32 * T1_SLABS); base < quads; base += stride, ++it) {
+      const int buf = it & 1;
       const int64_t gi = base + slab * 32 + lane;
       const bool act = gi < quads;
       auto ld_v = [&](const float* p) -> float4 { return reinterpret_cast<const float4*>(p)[gi]; };
@@ -786,10 +793,10 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
           vm[i] = ld_v(col(g, 1));
           v1[i] = ld_v(col(g, 2));
           if (g == 0)
-            stg[slab][2 * S][lane] = v0[i];          // r^(0)
+            stg(buf, 2 * S) = v0[i];          // r^(0)
           else {
-            stg[slab][g - 1][lane] = vm[i];          // v_{g-1}^(-1), before the update
-            stg[slab][S + g - 1][lane] = v0[i];      // v_{g-1}^(0)
+            stg(buf, g - 1) = vm[i];          // v_{g-1}^(-1), before the update
+            stg(buf, S + g - 1) = v0[i];      // v_{g-1}^(0)
           }
         }
       }
@@ -804,22 +811,21 @@ __global__ void __launch_bounds__(T1_NT, 1) tau1_f32_kernel(TauArgs<float> a) {
 #pragma unroll
             for (int j = 0; j < S; ++j) {
               if (j >= s) break;
-              fma4(xv, gs[j], stg[slab][j][lane]);
+              fma4(xv, gs[j], stg(buf, j));
             }
             vm[i] = xv;
           } else {
             const int q = g - 1;
-            float4 v = stg[slab][2 * S][lane];
+            float4 v = stg(buf, 2 * S);
 #pragma unroll
             for (int j = 0; j < S; ++j) {
               if (j >= s) break;
-              fnma4(v, es[q * SMAX + j], j < q ? stg[slab][S + j][lane] : stg[slab][j][lane]);
+              fnma4(v, es[q * SMAX + j], j < q ? stg(buf, S + j) : stg(buf, j));
             }
             vm[i] = v;
           }
         }
       }
-      slab_sync();
       if (act) {
 #pragma unroll
         for (int i = 0; i < GPC; ++i) {
@@ -968,8 +974,17 @@ static void launch_tau(const Ctx& c, const TauArgs<T>& a) {
 
 template <int S, bool LZ>
 static void launch_tau1(const Ctx& c, const TauArgs<float>& a, int64_t need) {
-  static int cap = max_grid_nt(tau1_f32_kernel<S, LZ>, c, T1_NT);
-  tau1_f32_kernel<S, LZ><<<clamp_grid(need, cap), T1_NT, 0, c.stream>>>(a);
+  constexpr size_t dyn = LZ ? sizeof(float4) * 2 * T1_SLABS * (2 * S + 1) * 32 : 0;
+  static bool attr = !LZ || cudaFuncSetAttribute(tau1_f32_kernel<S, LZ>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)dyn) == cudaSuccess;
+  (void)attr;
+  static int cap = [&] {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tau1_f32_kernel<S, LZ>, T1_NT, dyn) != cudaSuccess || nb < 1)
+      nb = 1;
+    return nb * c.sms > MAXBLK ? MAXBLK : nb * c.sms;
+  }();
+  tau1_f32_kernel<S, LZ><<<clamp_grid(need, cap), T1_NT, dyn, c.stream>>>(a);
 }
 
 template <typename T>
