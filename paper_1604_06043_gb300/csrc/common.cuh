@@ -261,6 +261,27 @@ __device__ __forceinline__ void sum_partials(const double* base, int nblk, int m
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
   for (int i = w; i < m; i += nw) {
     double v0 = 0.0, v1 = 0.0, v2 = 0.0, v3 = 0.0;
+    if (nblk <= 160) {
+      // up to five partials per lane, all loaded before the first addition; the
+      // additions are those of the loops below, in their order
+      double r[5];
+#pragma unroll
+      for (int u = 0; u < 5; ++u) r[u] = lane + 32 * u < nblk ? __ldcg(base + (size_t)(lane + 32 * u) * MAXRED + i) : 0.0;
+      if (lane + 96 < nblk) {
+        v0 += r[0];
+        v1 += r[1];
+        v2 += r[2];
+        v3 += r[3];
+        if (lane + 128 < nblk) v0 += r[4];
+      } else {
+        if (lane < nblk) v0 += r[0];
+        if (lane + 32 < nblk) v0 += r[1];
+        if (lane + 64 < nblk) v0 += r[2];
+      }
+      double v = warp_sum((v0 + v1) + (v2 + v3));
+      if (lane == 0) red[i] = v;
+      continue;
+    }
     int b = lane;
     for (; b + 96 < nblk; b += 128) {
       v0 += __ldcg(base + (size_t)b * MAXRED + i);
