@@ -44,9 +44,9 @@ FP32_NOMINAL_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one launch of the dominant kernel of each form,
 # from one ncu capture of the current kernel at 128^3
 # (profiles/ncu_level_fp64_convdiff3d_128.md, ncu_spmv_dot_*_convdiff3d_128.md).
-NCU_TRAFFIC = {("convdiff3d_128", "fp64", "level"): 4_600_564_224,
+NCU_TRAFFIC = {("convdiff3d_128", "fp64", "level"): 4_600_663_808,
                ("convdiff3d_128", "fp64", "spmv_dot"): 342_305_280,
-               ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_367_872,
+               ("convdiff3d_128", "fp32_inner", "spmv_dot"): 200_357_376,
                ("convdiff3d_128", "ilu0", "precond"): 161_049_344}
 
 
