@@ -481,6 +481,7 @@ struct TauArgs {
   const T* P;
   int64_t ldp;
   int do_update, proj;
+  int xonly;     // r^(0) is replaced after this step: group 0 updates x (and xbak) only
   DevState* st;
   Epi epi;
   RedScratch rs;
@@ -560,10 +561,11 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs
           r -= tau[i - 1] * lv[i];
           xv += tau[i - 1] * lv[i - 1];
         }
-        a.R[row] = r;
+        if (!a.xonly) a.R[row] = r;
         a.x[row] = xv;
         if (a.xbak) a.xbak[row] = xv;
       }
+      if (a.xonly) return;
       out = r;
     } else {
       const int q = t - 1;
@@ -611,17 +613,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs
     load_row(row, lv0, pv0, x0);
     update_row(row, lv0, pv0, x0);
   }
-  if (!a.proj) return;
+  if (!a.proj || (a.xonly && t == 0)) return;
   const int m = a.s + (t == 0 ? 1 : 0);
   double fin[32];
 #pragma unroll
   for (int i = 0; i < 32; ++i) fin[i] = i < SMAX && i < a.s ? acc.get(i < SMAX ? i : 0) : (i == a.s ? acc.get(SMAX) : 0.0);
   block_reduce<32>(fin, m, smem_w, red);
   if (!grid_reduce(a.rs, t, chunk, nchunks, m, red, &s_last)) return;
-  if (!groups_done(a.rs, t, nt, m, red, &s_last)) return;
+  if (!groups_done(a.rs, t, a.xonly ? nt - 1 : nt, m, red, &s_last)) return;
   // very last block: scatter all groups' sums into the device state
   DevState* st = a.st;
-  for (int i = threadIdx.x; i < nt * a.s; i += NT) {
+  for (int i = a.xonly ? a.s + threadIdx.x : threadIdx.x; i < nt * a.s; i += NT) {
     const int tt = i / a.s, cc = i % a.s;
     const double v = __ldcg(a.rs.group_out + tt * MAXRED + cc);
     if (tt == 0)
@@ -629,7 +631,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 3 : 2) tau_kernel(TauArgs
     else
       st->projV[(tt - 1) * SMAX + cc] = v;
   }
-  if (threadIdx.x == 0) st->rr = __ldcg(a.rs.group_out + a.s);
+  if (threadIdx.x == 0 && !a.xonly) st->rr = __ldcg(a.rs.group_out + a.s);
   __threadfence();
   __syncthreads();
   if (threadIdx.x < 32) run_epilogue(a.epi, ew);
@@ -1005,9 +1007,10 @@ template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
                        Epi epi, const T* Pb, const T* Pil, int sp, const double* lgamma, const double* leta,
-                       int leta_ld) {
-  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, st, epi, c.rs, Pb,
-               Pil, sp, lgamma, leta, leta_ld};
+                       int leta_ld, int xonly) {
+  TauArgs<T> a{n, s, ell, R, V, x, xbak, ld, tau ? tau : st->tau, P, ldp, do_update, proj, xonly, st, epi, c.rs,
+               Pb, Pil, sp, lgamma, leta, leta_ld};
+  if (xonly && (!do_update || tau1_applies(n, s, ell, R, V, x, xbak, ld, P, ldp, Pb))) return cudaErrorInvalidValue;
   if (lgamma && !(do_update && tau_fuses_lazy(n, s, ell, R, V, x, xbak, ld, P, ldp, Pb)))
     return cudaErrorInvalidValue;
   if constexpr (sizeof(T) == 4) {
@@ -1330,7 +1333,7 @@ cudaError_t f64_to_f32_n(const Ctx& c, int64_t n, const double* x, float* y, dou
                                       const double*, int);                                                \
   template cudaError_t tau_update<T>(const Ctx&, int, int, int, T*, T*, T*, T*, int64_t, const double*,   \
                                      const T*, int64_t, int, int, DevState*, Epi, const T*, const T*,    \
-                                     int, const double*, const double*, int);                            \
+                                     int, const double*, const double*, int, int);                       \
   template bool tau_fuses_lazy<T>(int, int, int, const T*, const T*, const T*, const T*, int64_t, const T*,  \
                                   int64_t, const T*);                                                    \
   template cudaError_t cols_axpy<T>(const Ctx&, int, T*, const T*, int64_t, int, const double*);          \

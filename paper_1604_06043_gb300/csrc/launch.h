@@ -97,12 +97,15 @@ cudaError_t lazy_update(const Ctx& c, int n, int s, T* R, T* V, T* x, int64_t ld
 // Degree-l step (tau from st->tau if tau == NULL, else from tau), followed
 // (proj != 0) by P^T r, P^T V^(0) and r.r into st->projR[0], st->projV[0],
 // st->rr and the epilogue.  With do_update == 0 only the projections are
-// computed.  xbak (nullable) receives a copy of the new x.
+// computed.  xbak (nullable) receives a copy of the new x.  xonly != 0 (the
+// per-group kernel only, do_update != 0): r^(0) is replaced right after this
+// step, so it updates x but neither r^(0) nor P^T r, r.r.
 template <typename T>
 cudaError_t tau_update(const Ctx& c, int n, int s, int ell, T* R, T* V, T* x, T* xbak, int64_t ld,
                        const double* tau, const T* P, int64_t ldp, int do_update, int proj, DevState* st,
                        Epi epi, const T* Pb = nullptr, const T* Pil = nullptr, int sp = 0,
-                       const double* lgamma = nullptr, const double* leta = nullptr, int leta_ld = 0);
+                       const double* lgamma = nullptr, const double* leta = nullptr, int leta_ld = 0,
+                       int xonly = 0);
 
 // Whether tau_update can run the level -1 updates of level step 0 (lazy_update
 // with k = 0, gamma and eta passed as lgamma, leta) in the same pass (the FP32

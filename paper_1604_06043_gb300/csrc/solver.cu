@@ -547,10 +547,13 @@ msstab_status idrstab(msstab_t h, Work<T>& w, int prec, const SolveCtl& ctl, Sol
         LAUNCH(MSSTAB_K_TAU, multidot<T>(c, n, cols, ell + 1, ell + 1, 0, st->gram, ell + 1,
                                          epi_of(EPI_TAU, 0, 0)));
       }
+      // with the replacement that follows, r^(0), P^T r, r.r and gamma_0 of this step
+      // would be overwritten: the FP64 step updates x and V only
+      const bool xonly = replaced && sizeof(T) == 8;
       LAUNCH(MSSTAB_K_TAU, tau_update<T>(c, n, s, ell, w.R, w.V, w.X, w.XB2, ld, nullptr, P, ld, 1, 1, st,
-                                         epi_of(EPI_GAMMA, 0, 0), w.Pb, w.Pil, w.sp,
+                                         xonly ? epi_none(h) : epi_of(EPI_GAMMA, 0, 0), w.Pb, w.Pil, w.sp,
                                          fuse_lazy ? &st->gamma[0] : nullptr, fuse_lazy ? &st->eta[0] : nullptr,
-                                         SMAX));
+                                         SMAX, xonly ? 1 : 0));
       // residual replacement at the cycle end: r = b - A x with P^T r and ||r||^2 in the same pass
       // (out[c] = P_c . r at projR level 0, out[s] = r . r), then gamma of the next cycle's first
       // level step from P^T V (left by tau_update) in the epilogue
