@@ -35,9 +35,7 @@ namespace mcnn {
 constexpr int NL = 4;
 constexpr int CI_[NL] = {2, 16, 16, 16};
 constexpr int CO_[NL] = {16, 16, 16, 1};
-constexpr int TX = 8, TY = 8, TZ = 4, TV = TX * TY * TZ;   // output tile, one voxel per thread
-constexpr int HX = TX + 2, HY = TY + 2, HZ = TZ + 2, HV = HX * HY * HZ;
-constexpr int HVP = HV + 1;   // 601: channel planes in shared memory start in distinct banks
+constexpr int WG_MAX_BLOCKS = 1024;   // rows of the weight-gradient partials (two blocks per SM are launched)
 
 __host__ __device__ constexpr int n_params() {
   return 2 * 16 * 27 + 16 + 16 * 16 * 27 + 16 + 16 * 16 * 27 + 16 + 16 * 1 * 27 + 1;
@@ -290,11 +288,13 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ CU
   if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(32));
 }
 
-// The tensor map of a half-major input (B entries of nh halves): dimensions
-// (8 channels, x, y, z, entry * nh + half), innermost first; box (8, 10, 18,
-// 3, 1) = one halo half; out-of-range elements read as zero.  The encoder is
+// The tensor map of a half-major volume (B entries of nh halves): dimensions
+// (8 channels, x, y, z, entry * nh + half), innermost first; box (8, bx, by,
+// bz, 1): (8, 10, 18, 3, 1) is one halo half of a convolution tile, (8, 8, 16,
+// 1, 1) one half of the tile itself; out-of-range elements read as zero.  The encoder is
 // the driver's, fetched through the runtime (no link against the driver).
-static cudaError_t halo_map(CUtensorMap* m, const __nv_bfloat16* in, Dims d, int B, int nh) {
+static cudaError_t half_major_map(CUtensorMap* m, const __nv_bfloat16* in, Dims d, int B, int nh, int bx, int by,
+                                  int bz) {
   static PFN_cuTensorMapEncodeTiled_v12000 enc = nullptr;
   if (!enc) {
     void* fn = nullptr;
@@ -306,12 +306,16 @@ static cudaError_t halo_map(CUtensorMap* m, const __nv_bfloat16* in, Dims d, int
   }
   const cuuint64_t dims[5] = {8, (cuuint64_t)d.X, (cuuint64_t)d.Y, (cuuint64_t)d.Z, (cuuint64_t)B * nh};
   const cuuint64_t strides[4] = {16, 16ull * d.X, 16ull * d.X * d.Y, 16ull * d.X * d.Y * d.Z};
-  const cuuint32_t box[5] = {8, CHX, CHY, CHZ, 1};
+  const cuuint32_t box[5] = {8, (cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz, 1};
   const cuuint32_t estr[5] = {1, 1, 1, 1, 1};
   const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<__nv_bfloat16*>(in), dims, strides, box,
                          estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+static cudaError_t halo_map(CUtensorMap* m, const __nv_bfloat16* in, Dims d, int B, int nh) {
+  return half_major_map(m, in, d, B, nh, CHX, CHY, CHZ);
 }
 
 template <int CI, int CO, int MODE>
@@ -367,101 +371,257 @@ static cudaError_t conv(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B,
 }
 
 // ---------------------------------------------------------------------------
-// weight and bias gradients: per-block partials of dW[co][ci][tap] =
-// sum_p g[co, p] a[ci, p + tap - 1] and db[co] = sum_p g[co, p]
+// Weight and bias gradients on the tensor cores.  For each tap the weight
+// gradient is a product with the voxels as the contraction:
+//   dW_tap[co][ci] = sum_p a[ci][p + tap - 1] g[co][p],
+// transposed: D = A_s . G with A_s (shifted input channels x voxels) and G
+// (voxels x output channels).  Both operands are read MN-major, straight from
+// the half-major tiles that the tensor copies land (8 consecutive voxels of
+// one channel half are one 128-byte core matrix: 8 K-rows of 8 channels):
+//   A_s:  the halo of the forward convolution; its 16 M-direction core
+//         matrices 16 bytes (one voxel) apart, so that core n is the window
+//         shifted by n voxels: n = dx + 10 dy' (a halo row is 10 voxels) puts
+//         the taps dx = 0..2 of two consecutive dy in one MMA (cores 0..2 and
+//         10..12, rows 8n .. 8n + 7 = the 8 channels of the half); the other
+//         cores are products never read.  K: one halo row (160 bytes) per 8
+//         voxels;
+//   G:    the output-gradient tile [half][y 16][x 8][8]: 128 bytes per 8
+//         voxels (K), 2048 bytes per channel half (N = 16).
+// An MMA (kind::f16, M = 128, N = 16, K = 16) covers two tile rows; per K step
+// 13 MMAs: 3 dz x 2 channel halves x (dy 0-1, dy 2), and the bias gradient
+// (a 128 x 16 block of ones times G).  The issue of an MMA costs about the
+// same whatever its shape (measured: M = 64..128, N = 16..128), so the taps
+// share MMAs rather than padding the 16 output channels to M = 128.  The 13
+// accumulators (16 columns each) stay in tensor memory over all tiles of the
+// block; one thread issues the tensor copies of the next tile (two stages)
+// and the MMAs of the current one.  Then each warp reads its lanes and writes
+// the entries they hold of the block's partial sums: dW as [co][ci][tap], then
+// the CO bias sums db[co] = sum_p g[co][p].  Waits are bounded: one that runs
+// out raises *flag, the copies and MMAs in flight get a second bounded wait,
+// and tensor memory is freed on every path.
 // ---------------------------------------------------------------------------
-template <int CI, int CO>
-__global__ void __launch_bounds__(TV) wgrad_kernel(const __nv_bfloat16* __restrict__ a, const __nv_bfloat16* __restrict__ g,
-                                                   Dims d, float* __restrict__ partials) {
-  constexpr int PAIRS = CO * CI;
-  constexpr int GROUPS = TV / PAIRS >= 1 ? TV / PAIRS : 1;
-  constexpr int NV = PAIRS * 27 + CO;
-  extern __shared__ float smem[];
-  float* a_s = smem;                  // [CI][HVP]: planes one word longer than HV, so that the
-                                      // lanes' 16 channels fall in distinct banks
-  float* g_s = smem + CI * HVP;       // [CO][TV]
-  float* r_s = g_s + CO * TV;         // [GROUPS][PAIRS][28]
-  const int tilesx = (d.X + TX - 1) / TX, tilesy = (d.Y + TY - 1) / TY;
-  const int tz0 = (blockIdx.x / (tilesx * tilesy)) * TZ;
-  const int ty0 = ((blockIdx.x / tilesx) % tilesy) * TY;
-  const int tx0 = (blockIdx.x % tilesx) * TX;
-  const int b = blockIdx.y;
-  const int64_t vol = d.vol();
-  for (int i = threadIdx.x; i < CI * HV; i += TV) {
-    const int c = i / HV, h = i % HV;
-    const int hx = h % HX, hy = (h / HX) % HY, hz = h / (HX * HY);
-    const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-    float v = 0.f;
-    if (gx >= 0 && gx < d.X && gy >= 0 && gy < d.Y && gz >= 0 && gz < d.Z)
-      v = __bfloat162float(a[(((int64_t)b * halves(CI) + (c >> 3)) * vol + ((int64_t)gz * d.Y + gy) * d.X + gx) * 8 +
-                             (c & 7)]);
-    a_s[c * HVP + h] = v;
-  }
-  for (int i = threadIdx.x; i < CO * TV; i += TV) {
-    const int c = i / TV, t = i % TV;
-    const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-    const int gx = tx0 + lx, gy = ty0 + ly, gz = tz0 + lz;
-    float v = 0.f;
-    if (gx < d.X && gy < d.Y && gz < d.Z)
-      v = __bfloat162float(g[(((int64_t)b * halves(CO) + (c >> 3)) * vol + ((int64_t)gz * d.Y + gy) * d.X + gx) * 8 +
-                             (c & 7)]);
-    g_s[i] = v;
-  }
-  __syncthreads();
-  const int pair = threadIdx.x % PAIRS, grp = threadIdx.x / PAIRS;
-  const int co = pair / CI, ci = pair % CI;
-  float acc[27];
-#pragma unroll
-  for (int k = 0; k < 27; ++k) acc[k] = 0.f;
-  float db = 0.f;
-  if (grp < GROUPS) {
-    for (int t = grp; t < TV; t += GROUPS) {
-      const float gv = g_s[co * TV + t];
-      const int lx = t % TX, ly = (t / TX) % TY, lz = t / (TX * TY);
-      const float* src = a_s + ci * HVP;
-#pragma unroll
-      for (int dz = 0; dz < 3; ++dz)
-#pragma unroll
-        for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-          for (int dx = 0; dx < 3; ++dx)
-            acc[(dz * 3 + dy) * 3 + dx] = fmaf(gv, src[((lz + dz) * HY + (ly + dy)) * HX + (lx + dx)],
-                                               acc[(dz * 3 + dy) * 3 + dx]);
-      db += gv;
-    }
-    float* r = r_s + ((size_t)grp * PAIRS + pair) * 28;
-#pragma unroll
-    for (int k = 0; k < 27; ++k) r[k] = acc[k];
-    r[27] = db;
-  }
-  __syncthreads();
-  float* out = partials + ((size_t)blockIdx.y * gridDim.x + blockIdx.x) * NV;
-  for (int i = threadIdx.x; i < PAIRS * 28; i += TV) {
-    const int pr = i / 28, k = i % 28;
-    float s = 0.f;
-    for (int gg = 0; gg < GROUPS; ++gg) s += r_s[((size_t)gg * PAIRS + pr) * 28 + k];
-    if (k < 27)
-      out[pr * 27 + k] = s;                        // [co][ci][tap] with pr = co*CI + ci
-    else if (pr % CI == 0)
-      out[PAIRS * 27 + pr / CI] = s;               // bias of co = pr / CI (ci == 0 carries it)
-  }
+constexpr int WG_G_HALF = CTX * CTY * 16;         // 2048: one channel half of the G tile
+constexpr int WG_G_BYTES = 2 * WG_G_HALF;
+constexpr int WG_STAGE = WG_G_BYTES + TC_A_BYTES; // G tile, then the halo (both halves)
+constexpr int WG_ONES = 2 * WG_STAGE;             // 128 x 16 bf16 ones (4096 bytes)
+constexpr int WG_HALO_REACH = 8704 + (2 * CHY + 2 * 7 + 2) * CHX * 16 + 15 * 16 + CHX * 16 + 128;
+constexpr int WG_SMEM = 80 * 1024;                // at most two blocks per SM (256 tensor-memory columns each)
+constexpr int WG_NCOL = 256;
+constexpr int WG_REGIONS = 13;                    // 12 tap groups and the bias
+static_assert(WG_STAGE % 128 == 0 && WG_STAGE + WG_G_BYTES + WG_HALO_REACH <= WG_ONES + 4096 &&
+                  WG_ONES + 4096 + 128 <= WG_SMEM && WG_REGIONS * 16 <= WG_NCOL,
+              "weight-gradient shared and tensor memory");
+
+__device__ __forceinline__ void tma_5d(uint32_t dst, const CUtensorMap* map, int c1, int c2, int c3, int c4,
+                                       uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+      ::"r"(dst), "l"(reinterpret_cast<uint64_t>(map)), "r"(0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_f16(uint32_t d, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t accum) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+               ::"r"(d), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
 }
 
 template <int CI, int CO>
-static cudaError_t wgrad(cudaStream_t st, const __nv_bfloat16* a, const __nv_bfloat16* g, Dims d, int B,
-                         float* partials, int* nblocks) {
-  constexpr int PAIRS = CO * CI;
-  constexpr int GROUPS = TV / PAIRS >= 1 ? TV / PAIRS : 1;
-  const size_t smem = sizeof(float) * (CI * HVP + CO * TV + GROUPS * PAIRS * 28);
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(wgrad_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
+__global__ void __launch_bounds__(128) wgrad_tc_kernel(const __grid_constant__ CUtensorMap halo_map,
+                                                       const __grid_constant__ CUtensorMap g_map, Dims d, int B,
+                                                       float* __restrict__ partials, int* flag) {
+  constexpr int NV = CO * CI * 27 + CO;
+  constexpr int HI = halves(CI);
+  extern __shared__ __align__(1024) unsigned char wsm_raw[];
+  unsigned char* sm = wsm_raw + ((128u - (smem_u32(wsm_raw) & 127u)) & 127u);
+  __shared__ __align__(8) uint64_t lbar[2];   // tensor copies of a stage
+  __shared__ __align__(8) uint64_t mbar[2];   // MMAs that read a stage
+  __shared__ uint32_t tslot;
+  __shared__ int s_ok;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tilesx = (d.X + CTX - 1) / CTX, tilesy = (d.Y + CTY - 1) / CTY;
+  const int tiles = tilesx * tilesy * d.Z;
+  const int jobs = tiles * B;
+  const int nj = jobs > (int)blockIdx.x ? (jobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  // the ones of the bias gradient; a channel half of G that no copy fills is zero
+  for (int i = tid; i < 2048; i += 128) reinterpret_cast<uint16_t*>(sm + WG_ONES)[i] = 0x3F80u;
+  if (halves(CO) < 2)
+    for (int st = 0; st < 2; ++st)
+      for (int i = tid; i < WG_G_HALF / 16; i += 128)
+        reinterpret_cast<uint4*>(sm + st * WG_STAGE + WG_G_HALF)[i] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid == 0) {
+    for (int st = 0; st < 2; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&lbar[st])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar[st])), "r"(1));
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;");
   }
-  const int tiles = ((d.X + TX - 1) / TX) * ((d.Y + TY - 1) / TY) * ((d.Z + TZ - 1) / TZ);
-  wgrad_kernel<CI, CO><<<dim3(tiles, B), TV, smem, st>>>(a, g, d, partials);
-  *nblocks = tiles * B;
+  asm volatile("fence.proxy.async.shared::cta;");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(WG_NCOL));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  if (tid == 0) {
+    // D f32, A and B bf16, both MN-major (bits 15, 16), N = 16, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((16u >> 3) << 17) |
+                           ((128u >> 4) << 24);
+    // MN-major descriptors: leading byte offset = the K step, stride byte
+    // offset = the M/N step.  The start address is the low field in 16-byte
+    // units (shared addresses stay below 2^18 bytes), so a descriptor moves
+    // by adding the byte offset / 16.
+    const uint64_t odesc = umma_desc(smem_u32(sm + WG_ONES), 128, 256);
+    auto load = [&](int st, int job) {
+      const int b = job / tiles, tile = job % tiles;
+      const int tz0 = tile / (tilesx * tilesy);
+      const int ty0 = ((tile / tilesx) % tilesy) * CTY;
+      const int tx0 = (tile % tilesx) * CTX;
+      const uint32_t bar = smem_u32(&lbar[st]);
+      constexpr uint32_t bytes = (uint32_t)halves(CO) * WG_G_HALF + (uint32_t)HI * TC_A_HALF;
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+      unsigned char* base = sm + st * WG_STAGE;
+#pragma unroll
+      for (int hf = 0; hf < halves(CO); ++hf)
+        tma_5d(smem_u32(base + hf * WG_G_HALF), &g_map, tx0, ty0, tz0, b * halves(CO) + hf, bar);
+#pragma unroll
+      for (int hf = 0; hf < HI; ++hf)
+        tma_5d(smem_u32(base + WG_G_BYTES + hf * TC_A_HSTRIDE), &halo_map, tx0 - 1, ty0 - 1, tz0 - 1,
+               b * HI + hf, bar);
+    };
+    int ok = 1;
+    uint32_t lph[2] = {0u, 0u}, mph[2] = {0u, 0u};
+    bool lout[2] = {false, false}, mout[2] = {false, false};
+    int last = -1;   // stage of the latest committed MMAs
+    if (nj > 0) {
+      load(0, blockIdx.x);
+      lout[0] = true;
+    }
+    for (int i = 0; i < nj; ++i) {
+      const int st = i & 1;
+      if (i + 1 < nj) {
+        if (mout[st ^ 1]) {   // the MMAs of job i - 1 read the other stage
+          if (!mbar_wait(smem_u32(&mbar[st ^ 1]), mph[st ^ 1])) {
+            ok = 0;
+            break;
+          }
+          mph[st ^ 1] ^= 1u;
+          mout[st ^ 1] = false;
+        }
+        load(st ^ 1, blockIdx.x + (i + 1) * gridDim.x);
+        lout[st ^ 1] = true;
+      }
+      if (!mbar_wait(smem_u32(&lbar[st]), lph[st])) {
+        ok = 0;
+        break;
+      }
+      lph[st] ^= 1u;
+      lout[st] = false;
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      const uint32_t g0 = smem_u32(sm + st * WG_STAGE), h0 = g0 + WG_G_BYTES;
+      const uint64_t gdesc = umma_desc(g0, 128, WG_G_HALF);
+      const uint64_t hdesc = umma_desc(h0, CHX * 16, 16);
+#pragma unroll 1
+      for (int j2 = 0; j2 < CTY / 2; ++j2) {
+        const uint64_t gd = gdesc + (uint64_t)(j2 * 16);        // two tile rows: 256 bytes
+        const uint32_t accum = (i > 0 || j2 > 0) ? 1u : 0u;
+#pragma unroll
+        for (int r = 0; r < 12; ++r) {
+          // region r = (dz * 2 + half) * 2 + dyg: taps dz, dy = 2 dyg + (0, 1), dx = 0..2
+          const int dz = r / 4, hf = (r / 2) % 2, dyg = r % 2;
+          if (hf >= HI) continue;
+          const uint64_t ad = hdesc + (uint64_t)((hf * TC_A_HSTRIDE) / 16 + (dz * CHY + 2 * j2 + 2 * dyg) * CHX);
+          mma_f16(taddr + r * 16, ad, gd, idesc, accum);
+        }
+        mma_f16(taddr + 12 * 16, odesc, gd, idesc, accum);
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mbar[st])));
+      mout[st] = true;
+      last = st;
+    }
+    // the MMAs complete in order: the latest commit covers the earlier ones
+    if (last >= 0 && mout[last] && !mbar_wait(smem_u32(&mbar[last]), mph[last])) ok = 0;
+    if (!ok) {
+      atomicOr(flag, 1);
+      for (int st = 0; st < 2; ++st)
+        if (lout[st]) mbar_wait(smem_u32(&lbar[st]), lph[st]);
+    }
+    s_ok = ok;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  if (s_ok) {
+    // row m of a region: core n = m / 8 (the window shifted by dx + 10 dy'),
+    // channel m % 8 of the half; warp w holds rows 32 w .. 32 w + 31
+    float* out = partials + (size_t)blockIdx.x * NV;
+    const int m = warp * 32 + lane, n = m / 8, dx = n % 10, dyp = n / 10;
+    for (int r = 0; r < WG_REGIONS; ++r) {
+      if (r < 12 && r / 2 % 2 >= HI) continue;   // a channel half the layer does not have (uniform)
+      uint32_t v[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+            "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(r * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      if (r == 12) {
+        if (m == 0)
+#pragma unroll
+          for (int co = 0; co < CO; ++co) out[CO * CI * 27 + co] = nj > 0 ? __uint_as_float(v[co]) : 0.f;
+        continue;
+      }
+      const int dz = r / 4, hf = (r / 2) % 2, dyg = r % 2;
+      const int ci = hf * 8 + m % 8, dy = 2 * dyg + dyp;
+      if (n < 16 && dx < 3 && dy < 3 && dyp < 2 && ci < CI) {
+        const int tap = (dz * 3 + dy) * 3 + dx;
+#pragma unroll
+        for (int co = 0; co < CO; ++co) out[(co * CI + ci) * 27 + tap] = nj > 0 ? __uint_as_float(v[co]) : 0.f;
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(WG_NCOL));
+}
+
+// The tensor-core weight gradient of a layer: a (input activations, CI
+// channels) and g (gradient of the pre-activations, CO channels), both half-
+// major bf16.  At most max_blocks blocks (the partials buffer's rows); the
+// number launched goes to *nblocks.
+template <int CI, int CO>
+static cudaError_t wgrad_tc(cudaStream_t st, const __nv_bfloat16* a, const __nv_bfloat16* g, Dims d, int B,
+                            float* partials, int max_blocks, int* nblocks, int* flag) {
+  if ((((uintptr_t)a | (uintptr_t)g) & 15u) != 0) return cudaErrorMisalignedAddress;
+  CUtensorMap amap, gmap;
+  {
+    cudaError_t e = half_major_map(&amap, a, d, B, halves(CI), CHX, CHY, CHZ);
+    if (e == cudaSuccess) e = half_major_map(&gmap, g, d, B, halves(CO), CTX, CTY, 1);
+    if (e != cudaSuccess) return e;
+  }
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(wgrad_tc_kernel<CI, CO>, cudaFuncAttributeMaxDynamicSharedMemorySize, WG_SMEM);
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
+  }
+  const int64_t jobs = (int64_t)((d.X + CTX - 1) / CTX) * ((d.Y + CTY - 1) / CTY) * d.Z * B;
+  int64_t grid = jobs < 2 * sms ? jobs : 2 * sms;   // two blocks per SM: two threads issue MMAs
+  if (grid > max_blocks) grid = max_blocks;
+  if (grid < 1) grid = 1;
+  wgrad_tc_kernel<CI, CO><<<(int)grid, 128, WG_SMEM, st>>>(amap, gmap, d, B, partials, flag);
+  *nblocks = (int)grid;
   return cudaGetLastError();
 }
 
@@ -707,6 +867,7 @@ struct msstab_cnn_s {
   bool use_stencil = false;
   float* sbuf = nullptr;        // K * (out - t) of the batch
   float* partials = nullptr;
+  int partial_rows = 0;         // blocks whose weight-gradient partials fit in partials
   double* dpart = nullptr;
   double* chunk_sums = nullptr; // [RED_CHUNKS][values] of the weight-gradient reduction
   double* h_small = nullptr;
@@ -809,15 +970,15 @@ msstab_status backward_batch(msstab_cnn_t h, int B, int D, double* loss) {
   CCK(cudaGetLastError());
   int nb = 0;
   // layer 3 (16 -> 1)
-  CCK((wgrad<16, 1>(st, h->act[3], h->dz[3], d, B, h->partials, &nb)));
+  CCK((wgrad_tc<16, 1>(st, h->act[3], h->dz[3], d, B, h->partials, h->partial_rows, &nb, h->tcflag)));
   CKA(reduce_partials(h, nb, 16 * 27 + 1, h->grad + w_offset(3)));
   CCK((conv<1, 16, BWD_DATA>(st, h->dz[3], d, B, h->wt[3], nullptr, nullptr, h->dz[2], h->z[2], h->tcflag)));
   for (int l = 2; l >= 1; --l) {
-    CCK((wgrad<16, 16>(st, h->act[l], h->dz[l], d, B, h->partials, &nb)));
+    CCK((wgrad_tc<16, 16>(st, h->act[l], h->dz[l], d, B, h->partials, h->partial_rows, &nb, h->tcflag)));
     CKA(reduce_partials(h, nb, 16 * 16 * 27 + 16, h->grad + w_offset(l)));
     CCK((conv<16, 16, BWD_DATA>(st, h->dz[l], d, B, h->wt[l], nullptr, nullptr, h->dz[l - 1], h->z[l - 1], h->tcflag)));
   }
-  CCK((wgrad<2, 16>(st, h->act[0], h->dz[0], d, B, h->partials, &nb)));
+  CCK((wgrad_tc<2, 16>(st, h->act[0], h->dz[0], d, B, h->partials, h->partial_rows, &nb, h->tcflag)));
   CKA(reduce_partials(h, nb, 2 * 16 * 27 + 16, h->grad + w_offset(0)));
   CCK(cudaGetLastError());
   if (loss) {
@@ -914,8 +1075,8 @@ msstab_status msstab_cnn_create(int32_t nx, int32_t ny, int32_t nz, const float*
   CKC(calloc_(h, &h->sbuf, bv));
   CKC(calloc_(h, &h->kst, 27));
   CKC(calloc_(h, &h->tcflag, 1));
-  const int64_t tiles = ((crop + TX - 1) / TX) * (int64_t)((crop + TY - 1) / TY) * ((crop + TZ - 1) / TZ) * max_batch;
-  CKC(calloc_(h, &h->partials, (size_t)tiles * (16 * 16 * 27 + 16)));
+  h->partial_rows = WG_MAX_BLOCKS;
+  CKC(calloc_(h, &h->partials, (size_t)h->partial_rows * (16 * 16 * 27 + 16)));
   CKC(calloc_(h, &h->dpart, 4096));
   CKC(calloc_(h, &h->chunk_sums, (size_t)RED_CHUNKS * (16 * 16 * 27 + 16)));
   CKC(calloc_(h, &h->origins, 4 * (size_t)max_batch));
