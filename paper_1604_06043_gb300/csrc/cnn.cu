@@ -140,12 +140,31 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ CU
   const int tiles = tilesx * tilesy * d.Z;
   const int64_t vol = d.vol();
   // weights once per block: w[co][ci][tap] -> tap * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2,
-  // zero for the padding channels (ci >= CI or co >= CO)
+  // zero for the padding channels (ci >= CI or co >= CO).  w is first copied
+  // as it is into the halo buffer (free until the first tile) with independent
+  // 16-byte loads, all in flight at once (one element per load took a global
+  // round trip per element, the bulk of a launch on a small volume), then
+  // rearranged from there.
+  constexpr int WBYTES = CO * CI * 27 * 2;
+  static_assert(WBYTES % 16 == 0 && WBYTES <= TC_A_BYTES, "weights staged in the halo buffer");
+  {
+    constexpr int NV = WBYTES / 16, PER = (NV + 127) / 128;
+    uint4 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (u * 128 + tid < NV) v[u] = __ldg(reinterpret_cast<const uint4*>(w) + u * 128 + tid);
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (u * 128 + tid < NV) reinterpret_cast<uint4*>(As)[u * 128 + tid] = v[u];
+  }
+  __syncthreads();
+  const __nv_bfloat16* ws = reinterpret_cast<const __nv_bfloat16*>(As);
   for (int i = tid; i < 16 * 16 * 27; i += 128) {
     const int co = i / (16 * 27), r = i % (16 * 27), ci = r / 27, tap = r % 27;
-    const __nv_bfloat16 v = (co < CO && ci < CI) ? w[(co * CI + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
+    const __nv_bfloat16 v = (co < CO && ci < CI) ? ws[(co * CI + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
     *reinterpret_cast<__nv_bfloat16*>(Bs + tap * 512 + (ci >> 3) * 256 + co * 16 + (ci & 7) * 2) = v;
   }
+  __syncthreads();   // the halo buffer is overwritten below
   // fewer than 9 input channels: the second half of the halo stays zero (the
   // weights of those channels are zero too, and 0 * 0 keeps the sums finite)
   if (halves(CI) < 2)
@@ -321,7 +340,8 @@ static cudaError_t halo_map(CUtensorMap* m, const __nv_bfloat16* in, Dims d, int
 template <int CI, int CO, int MODE>
 static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
                            const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
-  if (((uintptr_t)in & 15u) != 0) return cudaErrorMisalignedAddress;   // tensor-copy base: 16-byte aligned
+  // tensor-copy base and the weights' vector loads: 16-byte aligned
+  if ((((uintptr_t)in | (uintptr_t)w) & 15u) != 0) return cudaErrorMisalignedAddress;
   CUtensorMap map;
   {
     const cudaError_t e = halo_map(&map, in, d, B, halves(CI));
