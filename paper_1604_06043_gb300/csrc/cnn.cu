@@ -85,13 +85,15 @@ __device__ __forceinline__ uint32_t bf16_bits(float v) {
 // between x-consecutive voxels, 160 bytes (one halo row) between the 8-row
 // groups, 8640 bytes (one half) between the two K halves; the weights as
 // [tap][half][co][8] -- 128 bytes between co groups, 256 between halves.
-// One thread issues the 27 MMAs (kind::f16, BF16 operands, FP32 accumulator
-// of 128 lanes x 16 columns in tensor memory; 32 columns allocated) and
-// commits them to an mbarrier; after a bounded wait each warp reads its 32
-// rows with tcgen05.ld for the epilogue (bias, GELU or GELU', bf16 rounding).
-// Blocks are persistent (weights, tensor memory and the mbarrier set up once,
-// tiles taken in a grid-stride loop).  A wait that runs out raises *flag and
-// ends the block's loop; tensor memory is always freed before the block exits.
+// A block is a two-stage pipeline: one thread of warp 4 issues the halo copy
+// of the next tile and the 27 MMAs of a tile (kind::f16, BF16 operands, FP32
+// accumulator of 128 lanes x 16 columns in tensor memory, two accumulators)
+// and commits them to an mbarrier; warps 0-3 read their 32 rows of the other
+// accumulator with tcgen05.ld for the epilogue (bias, GELU or GELU', bf16
+// rounding) meanwhile.  Blocks are persistent (weights, tensor memory and the
+// mbarriers set up once, tiles taken in a grid-stride loop).  A wait that runs
+// out raises *flag and ends the block's loop; the copies and MMAs in flight get
+// a second bounded wait, and tensor memory is freed before the block exits.
 // ---------------------------------------------------------------------------
 constexpr int CTX = 8, CTY = 16;
 constexpr int CHX = CTX + 2, CHY = CTY + 2, CHZ = 3, CHV = CHX * CHY * CHZ;   // 540 halo voxels
@@ -99,7 +101,8 @@ constexpr int TC_A_HALF = CHV * 16;                 // bytes of one channel half
 constexpr int TC_A_HSTRIDE = 8704;                  // the halves 128-byte aligned (tensor-copy destinations)
 constexpr int TC_A_BYTES = 2 * TC_A_HSTRIDE;
 constexpr int TC_B_BYTES = 27 * 512;                // weights of the 27 taps
-constexpr int TC_SMEM = TC_A_BYTES + TC_B_BYTES + 128;   // + alignment slack
+constexpr int TC_SMEM = TC_B_BYTES + 2 * TC_A_BYTES + 128;   // weights, two halo stages, alignment slack
+constexpr int TC_THREADS = 160;                     // warps 0-3: the epilogue; warp 4: copies and MMAs
 constexpr long long TC_WAIT_LIMIT = 1LL << 22;
 static_assert(TC_A_HALF <= TC_A_HSTRIDE && TC_A_HSTRIDE % 128 == 0, "halo halves");
 
@@ -122,56 +125,64 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t phase) {
 }
 
 template <int CI, int CO, int MODE>
-__global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ CUtensorMap halo_map, Dims d, int B,
-                                                      const __nv_bfloat16* __restrict__ w,
-                                                      const float* __restrict__ bias, float* __restrict__ z,
-                                                      __nv_bfloat16* __restrict__ act,
-                                                      const float* __restrict__ zaux, int* flag) {
+__global__ void __launch_bounds__(TC_THREADS) conv_tc_kernel(const __grid_constant__ CUtensorMap halo_map, Dims d,
+                                                             int B, const __nv_bfloat16* __restrict__ w,
+                                                             const float* __restrict__ bias, float* __restrict__ z,
+                                                             __nv_bfloat16* __restrict__ act,
+                                                             const float* __restrict__ zaux, int* flag) {
   extern __shared__ __align__(1024) unsigned char tsm_raw[];
   // the tensor copies want 128-byte aligned destinations
   unsigned char* tsm = tsm_raw + ((128u - (smem_u32(tsm_raw) & 127u)) & 127u);
-  unsigned char* As = tsm;
-  unsigned char* Bs = tsm + TC_A_BYTES;
-  __shared__ __align__(8) uint64_t mbar;
-  __shared__ __align__(8) uint64_t tbar;   // completion of the halo's tensor copies
+  unsigned char* Bs = tsm;                  // weights
+  unsigned char* As = tsm + TC_B_BYTES;     // halo stage s at As + s * TC_A_BYTES
+  __shared__ __align__(8) uint64_t full[2];    // the halo copies of stage s have landed
+  __shared__ __align__(8) uint64_t done[2];    // the MMAs into accumulator s (reading stage s) are complete
+  __shared__ __align__(8) uint64_t freed[2];   // the four epilogue warps have read accumulator s
   __shared__ uint32_t tslot;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int tilesx = (d.X + CTX - 1) / CTX, tilesy = (d.Y + CTY - 1) / CTY;
   const int tiles = tilesx * tilesy * d.Z;
+  const int jobs = tiles * B;
+  const int nj = jobs > (int)blockIdx.x ? (jobs - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int64_t vol = d.vol();
   // weights once per block: w[co][ci][tap] -> tap * 512 + (ci / 8) * 256 + co * 16 + (ci % 8) * 2,
   // zero for the padding channels (ci >= CI or co >= CO).  w is first copied
-  // as it is into the halo buffer (free until the first tile) with independent
+  // as it is into a halo stage (free until the first tile) with independent
   // 16-byte loads, all in flight at once (one element per load took a global
   // round trip per element, the bulk of a launch on a small volume), then
   // rearranged from there.
   constexpr int WBYTES = CO * CI * 27 * 2;
-  static_assert(WBYTES % 16 == 0 && WBYTES <= TC_A_BYTES, "weights staged in the halo buffer");
+  static_assert(WBYTES % 16 == 0 && WBYTES <= TC_A_BYTES, "weights staged in a halo stage");
   {
-    constexpr int NV = WBYTES / 16, PER = (NV + 127) / 128;
+    constexpr int NV = WBYTES / 16, PER = (NV + TC_THREADS - 1) / TC_THREADS;
     uint4 v[PER];
 #pragma unroll
     for (int u = 0; u < PER; ++u)
-      if (u * 128 + tid < NV) v[u] = __ldg(reinterpret_cast<const uint4*>(w) + u * 128 + tid);
+      if (u * TC_THREADS + tid < NV) v[u] = __ldg(reinterpret_cast<const uint4*>(w) + u * TC_THREADS + tid);
 #pragma unroll
     for (int u = 0; u < PER; ++u)
-      if (u * 128 + tid < NV) reinterpret_cast<uint4*>(As)[u * 128 + tid] = v[u];
+      if (u * TC_THREADS + tid < NV) reinterpret_cast<uint4*>(As)[u * TC_THREADS + tid] = v[u];
   }
   __syncthreads();
   const __nv_bfloat16* ws = reinterpret_cast<const __nv_bfloat16*>(As);
-  for (int i = tid; i < 16 * 16 * 27; i += 128) {
+  for (int i = tid; i < 16 * 16 * 27; i += TC_THREADS) {
     const int co = i / (16 * 27), r = i % (16 * 27), ci = r / 27, tap = r % 27;
     const __nv_bfloat16 v = (co < CO && ci < CI) ? ws[(co * CI + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
     *reinterpret_cast<__nv_bfloat16*>(Bs + tap * 512 + (ci >> 3) * 256 + co * 16 + (ci & 7) * 2) = v;
   }
-  __syncthreads();   // the halo buffer is overwritten below
-  // fewer than 9 input channels: the second half of the halo stays zero (the
-  // weights of those channels are zero too, and 0 * 0 keeps the sums finite)
+  __syncthreads();   // the halo stages are overwritten below
+  // fewer than 9 input channels: the second half of each halo stage stays zero
+  // (the weights of those channels are zero too, and 0 * 0 keeps the sums finite)
   if (halves(CI) < 2)
-    for (int i = tid; i < TC_A_HALF / 16; i += 128) reinterpret_cast<uint4*>(As + TC_A_HSTRIDE)[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int st = 0; st < 2; ++st)
+      for (int i = tid; i < TC_A_HALF / 16; i += TC_THREADS)
+        reinterpret_cast<uint4*>(As + st * TC_A_BYTES + TC_A_HSTRIDE)[i] = make_uint4(0u, 0u, 0u, 0u);
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tbar)), "r"(1));
+    for (int st = 0; st < 2; ++st) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[st])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&done[st])), "r"(1));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&freed[st])), "r"(4));
+    }
     asm volatile("fence.mbarrier_init.release.cluster;");
   }
   asm volatile("fence.proxy.async.shared::cta;");
@@ -184,121 +195,161 @@ __global__ void __launch_bounds__(128) conv_tc_kernel(const __grid_constant__ CU
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t taddr = tslot;
-  // D f32, A and B bf16, both K-major, N = 16, M = 128
-  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
-  bool ok = true;
-  uint32_t phase = 0;
-  for (int job = blockIdx.x; job < tiles * B && ok; job += gridDim.x, phase ^= 1u) {
-    const int b = job / tiles, tile = job % tiles;
-    const int tz0 = tile / (tilesx * tilesy);
-    const int ty0 = ((tile / tilesx) % tilesy) * CTY;
-    const int tx0 = (tile % tilesx) * CTX;
-    // halo: one tiled tensor copy per channel half, box (8 channels, 10 x,
-    // 18 y, 3 z) at (0, tx0 - 1, ty0 - 1, tz0 - 1, b * halves + half); the
-    // copy fills out-of-range voxels with zeros.  The previous tile's MMAs have
-    // completed (their mbarrier was waited on), so the buffer is free.
-    if (tid == 0) {
-      constexpr uint32_t bytes = (uint32_t)halves(CI) * TC_A_HALF;
-      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&tbar)), "r"(bytes)
-                   : "memory");
+  if (warp == 4) {
+    // ---- producer: one thread issues the halo copies (one tile ahead) and
+    // the 27 MMAs of each tile into accumulator i % 2 ----
+    if (lane == 0) {
+      // D f32, A and B bf16, both K-major, N = 16, M = 128
+      const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+      auto load = [&](int st, int job) {
+        const int b = job / tiles, tile = job % tiles;
+        const int tz0 = tile / (tilesx * tilesy);
+        const int ty0 = ((tile / tilesx) % tilesy) * CTY;
+        const int tx0 = (tile % tilesx) * CTX;
+        // halo: one tiled tensor copy per channel half, box (8 channels, 10 x,
+        // 18 y, 3 z) at (0, tx0 - 1, ty0 - 1, tz0 - 1, b * halves + half); the
+        // copy fills out-of-range voxels with zeros
+        const uint32_t bar = smem_u32(&full[st]);
+        constexpr uint32_t bytes = (uint32_t)halves(CI) * TC_A_HALF;
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 #pragma unroll
-      for (int hf = 0; hf < halves(CI); ++hf)
-        asm volatile(
-            "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-            "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
-            ::"r"(smem_u32(As + hf * TC_A_HSTRIDE)), "l"(reinterpret_cast<uint64_t>(&halo_map)), "r"(0),
-              "r"(tx0 - 1), "r"(ty0 - 1), "r"(tz0 - 1), "r"(b * halves(CI) + hf), "r"(smem_u32(&tbar))
-            : "memory");
-    }
-    const bool halo_ok = mbar_wait(smem_u32(&tbar), phase);
-    // the previous tile's tensor-memory reads are done before the MMAs
-    // overwrite the accumulator
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    const int all_loaded = __syncthreads_and((int)halo_ok);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!all_loaded) {
-      // give the copy in flight a second bounded wait before leaving
-      if (tid == 0) {
-        atomicOr(flag, 1);
-        mbar_wait(smem_u32(&tbar), phase);
+        for (int hf = 0; hf < halves(CI); ++hf)
+          asm volatile(
+              "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+              "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+              ::"r"(smem_u32(As + st * TC_A_BYTES + hf * TC_A_HSTRIDE)),
+                "l"(reinterpret_cast<uint64_t>(&halo_map)), "r"(0), "r"(tx0 - 1), "r"(ty0 - 1), "r"(tz0 - 1),
+                "r"(b * halves(CI) + hf), "r"(bar)
+              : "memory");
+      };
+      int ok = 1;
+      uint32_t lph[2] = {0u, 0u}, mph[2] = {0u, 0u}, fph[2] = {0u, 0u};
+      bool lout[2] = {false, false}, mout[2] = {false, false};
+      if (nj > 0) {
+        load(0, blockIdx.x);
+        lout[0] = true;
       }
-      __syncthreads();
-      ok = false;
-      break;
-    }
-    if (tid == 0) {
-      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
-      for (int tap = 0; tap < 27; ++tap) {
-        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-        const uint64_t ad = umma_desc(a0 + ((dz * CHY + dy) * CHX + dx) * 16, TC_A_HSTRIDE, CHX * 16);
-        const uint64_t bd = umma_desc(b0 + tap * 512, 256, 128);
-        const uint32_t accum = tap > 0;
-        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
-                     ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
-                   ::"r"(smem_u32(&mbar)));
-    }
-    // this thread's output voxel; the backward mode's pre-activations are
-    // loaded while the MMAs run
-    const int m = warp * 32 + lane;
-    const int gx = tx0 + (m & 7), gy = ty0 + (m >> 3), gz = tz0;
-    const bool inside = gx < d.X && gy < d.Y;
-    const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
-    const int64_t ob = (int64_t)b * CO * vol;
-    float za[MODE == BWD_DATA ? CO : 1];
-    if constexpr (MODE == BWD_DATA) {
-#pragma unroll
-      for (int co = 0; co < CO; ++co) za[co] = inside ? __ldg(zaux + ob + (int64_t)co * vol + p) : 0.f;
-    }
-    const bool done = mbar_wait(smem_u32(&mbar), phase);
-    // one decision for the whole block (tcgen05.ld below is warp-collective)
-    const int all_done = __syncthreads_and((int)done);
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (!all_done) {
-      if (tid == 0) atomicOr(flag, 1);
-      ok = false;
-      break;
-    }
-    uint32_t r[16];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                 "[%16];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
-                   "=r"(r[15])
-                 : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
-    asm volatile("tcgen05.wait::ld.sync.aligned;");
-    if (inside) {
-      // bf16 outputs of the 16 channels, as two 16-byte half-major rows
-      uint32_t packed[8];
-#pragma unroll
-      for (int co = 0; co < 16; ++co) {
-        float out = 0.f;
-        if (co < CO) {
-          const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
-          const int64_t o = ob + (int64_t)co * vol + p;
-          if (MODE == FWD_HIDDEN) {
-            z[o] = acc;
-            out = gelu(acc);
-          } else if (MODE == FWD_LAST) {
-            z[o] = acc;
-          } else if (MODE == INFER_HIDDEN) {
-            out = gelu(acc);
-          } else {
-            out = acc * gelu_grad(za[MODE == BWD_DATA ? co : 0]);
+      for (int i = 0; i < nj; ++i) {
+        const int st = i & 1;
+        if (i + 1 < nj) {
+          if (mout[st ^ 1]) {   // the MMAs of tile i - 1 read the other stage
+            if (!mbar_wait(smem_u32(&done[st ^ 1]), mph[st ^ 1])) {
+              ok = 0;
+              break;
+            }
+            mph[st ^ 1] ^= 1u;
+            mout[st ^ 1] = false;
           }
+          load(st ^ 1, blockIdx.x + (i + 1) * gridDim.x);
+          lout[st ^ 1] = true;
         }
-        if (co % 2 == 0)
-          packed[co / 2] = bf16_bits(out);
-        else
-          packed[co / 2] |= bf16_bits(out) << 16;
+        if (!mbar_wait(smem_u32(&full[st]), lph[st])) {
+          ok = 0;
+          break;
+        }
+        lph[st] ^= 1u;
+        lout[st] = false;
+        if (i >= 2) {   // the epilogue of tile i - 2 has read accumulator st
+          if (!mbar_wait(smem_u32(&freed[st]), fph[st])) {
+            ok = 0;
+            break;
+          }
+          fph[st] ^= 1u;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        const uint32_t a0 = smem_u32(As + st * TC_A_BYTES), b0 = smem_u32(Bs);
+        for (int tap = 0; tap < 27; ++tap) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const uint64_t ad = umma_desc(a0 + ((dz * CHY + dy) * CHX + dx) * 16, TC_A_HSTRIDE, CHX * 16);
+          const uint64_t bd = umma_desc(b0 + tap * 512, 256, 128);
+          const uint32_t accum = tap > 0;
+          asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                       ::"r"(taddr + st * 16), "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"(smem_u32(&done[st])));
+        mout[st] = true;
       }
-      if constexpr (MODE != FWD_LAST) {
-        static_assert(MODE == FWD_LAST || CO == 16, "bf16 outputs have 16 channels");
-        uint4* dst = reinterpret_cast<uint4*>(act);
-        dst[((int64_t)b * 2 + 0) * vol + p] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        dst[((int64_t)b * 2 + 1) * vol + p] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+      if (!ok) {
+        // give the copies and MMAs in flight a second bounded wait before leaving
+        atomicOr(flag, 1);
+        for (int st = 0; st < 2; ++st) {
+          if (lout[st]) mbar_wait(smem_u32(&full[st]), lph[st]);
+          if (mout[st]) mbar_wait(smem_u32(&done[st]), mph[st]);
+        }
+      }
+    }
+  } else {
+    // ---- epilogue warps: thread m holds output voxel m of each tile ----
+    uint32_t dph[2] = {0u, 0u};
+    for (int i = 0; i < nj; ++i) {
+      const int st = i & 1;
+      const int job = blockIdx.x + i * gridDim.x;
+      const int b = job / tiles, tile = job % tiles;
+      const int tz0 = tile / (tilesx * tilesy);
+      const int ty0 = ((tile / tilesx) % tilesy) * CTY;
+      const int tx0 = (tile % tilesx) * CTX;
+      const int m = warp * 32 + lane;
+      const int gx = tx0 + (m & 7), gy = ty0 + (m >> 3), gz = tz0;
+      const bool inside = gx < d.X && gy < d.Y;
+      const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
+      const int64_t ob = (int64_t)b * CO * vol;
+      // the backward mode's pre-activations are loaded while the MMAs run
+      float za[MODE == BWD_DATA ? CO : 1];
+      if constexpr (MODE == BWD_DATA) {
+#pragma unroll
+        for (int co = 0; co < CO; ++co) za[co] = inside ? __ldg(zaux + ob + (int64_t)co * vol + p) : 0.f;
+      }
+      // one decision per warp (tcgen05.ld below is warp-collective)
+      const bool got = __all_sync(0xffffffffu, mbar_wait(smem_u32(&done[st]), dph[st]));
+      dph[st] ^= 1u;
+      if (!got) {
+        if (lane == 0) atomicOr(flag, 1);
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;");
+      uint32_t r[16];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr + ((uint32_t)(warp * 32) << 16) + (uint32_t)(st * 16)));
+      asm volatile("tcgen05.wait::ld.sync.aligned;");
+      asm volatile("tcgen05.fence::before_thread_sync;");
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&freed[st])) : "memory");
+      if (inside) {
+        // bf16 outputs of the 16 channels, as two 16-byte half-major rows
+        uint32_t packed[8];
+#pragma unroll
+        for (int co = 0; co < 16; ++co) {
+          float out = 0.f;
+          if (co < CO) {
+            const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
+            const int64_t o = ob + (int64_t)co * vol + p;
+            if (MODE == FWD_HIDDEN) {
+              z[o] = acc;
+              out = gelu(acc);
+            } else if (MODE == FWD_LAST) {
+              z[o] = acc;
+            } else if (MODE == INFER_HIDDEN) {
+              out = gelu(acc);
+            } else {
+              out = acc * gelu_grad(za[MODE == BWD_DATA ? co : 0]);
+            }
+          }
+          if (co % 2 == 0)
+            packed[co / 2] = bf16_bits(out);
+          else
+            packed[co / 2] |= bf16_bits(out) << 16;
+        }
+        if constexpr (MODE != FWD_LAST) {
+          static_assert(MODE == FWD_LAST || CO == 16, "bf16 outputs have 16 channels");
+          uint4* dst = reinterpret_cast<uint4*>(act);
+          dst[((int64_t)b * 2 + 0) * vol + p] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[((int64_t)b * 2 + 1) * vol + p] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+        }
       }
     }
   }
@@ -359,10 +410,10 @@ static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_tc_kernel<CI, CO, MODE>, 128, (size_t)TC_SMEM);
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, conv_tc_kernel<CI, CO, MODE>, TC_THREADS, (size_t)TC_SMEM);
     if (e != cudaSuccess) return e;
     // the occupancy query answers one block per SM for this kernel, although
-    // shared memory (the binding limit) admits seven; blocks beyond the
+    // shared memory (the binding limit) admits four; blocks beyond the
     // resident ones only queue (no block waits on another), so launch as many
     // as shared memory admits
     const int by_smem = (227 * 1024) / (TC_SMEM + 2048);
@@ -371,7 +422,7 @@ static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int
   }
   const int64_t jobs = (int64_t)((d.X + CTX - 1) / CTX) * ((d.Y + CTY - 1) / CTY) * d.Z * B;
   const int grid = (int)(jobs < cap ? jobs : cap);   // persistent blocks, tiles in a grid-stride loop
-  conv_tc_kernel<CI, CO, MODE><<<grid, 128, TC_SMEM, st>>>(map, d, B, w, bias, z, act, zaux, flag);
+  conv_tc_kernel<CI, CO, MODE><<<grid, TC_THREADS, TC_SMEM, st>>>(map, d, B, w, bias, z, act, zaux, flag);
   return cudaGetLastError();
 }
 
