@@ -426,6 +426,240 @@ static cudaError_t conv_tc(cudaStream_t st, const __nv_bfloat16* in, Dims d, int
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Layers with one or two input channels (the network's input layer and the
+// backward-data pass of its one-channel output layer): the taps are packed
+// into K.  Each thread writes its voxel's row of an im2col tile, K element
+// k = tap * CI + ci (27 CI values, zero up to the next multiple of 16), so a
+// tile takes ceil(27 CI / 16) MMAs (4 for two channels, 2 for one) instead of
+// 27 with 16 - CI zero channels each: at N = 16 an MMA costs several times
+// its arithmetic, and the MMA count bounded these layers.  Both operands
+// K-major without swizzle: the tile [m/8][k/8][m%8][k%8] (128 bytes per
+// 8-element K chunk, 1024 per group of 8 rows), the weights [co/8][k/8][co%8]
+// [k%8] likewise.  Single-stage persistent blocks (as many per SM as shared
+// memory admits overlap one another's copies, MMAs and epilogues); bounded
+// waits; tensor memory freed on every path.
+// ---------------------------------------------------------------------------
+constexpr int TK_A_BYTES = 16 * 1024;     // 128 rows x 64 K elements
+constexpr int TK_B_BYTES = 2 * 1024;      // 16 output channels x 64 K elements
+constexpr int TK_SMEM = TC_A_HSTRIDE + TK_A_BYTES + TK_B_BYTES + 128;
+
+template <int CI, int CO, int MODE>
+__global__ void __launch_bounds__(128) conv_k_kernel(const __grid_constant__ CUtensorMap halo_map, Dims d, int B,
+                                                     const __nv_bfloat16* __restrict__ w,
+                                                     const float* __restrict__ bias, float* __restrict__ z,
+                                                     __nv_bfloat16* __restrict__ act,
+                                                     const float* __restrict__ zaux, int* flag) {
+  static_assert(CI <= 2 && CO == 16, "taps packed into K: one or two input channels, 16 outputs");
+  constexpr int KE = 27 * CI, KS = (KE + 15) / 16, KC = 2 * KS;   // K elements, MMAs, 8-element chunks
+  extern __shared__ __align__(1024) unsigned char ksm_raw[];
+  unsigned char* ksm = ksm_raw + ((128u - (smem_u32(ksm_raw) & 127u)) & 127u);
+  unsigned char* Hs = ksm;                   // halo (channel half 0), tensor-copy destination
+  unsigned char* As = ksm + TC_A_HSTRIDE;    // im2col tile
+  unsigned char* Bs = As + TK_A_BYTES;       // weights
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t tbar;
+  __shared__ uint32_t tslot;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int tilesx = (d.X + CTX - 1) / CTX, tilesy = (d.Y + CTY - 1) / CTY;
+  const int tiles = tilesx * tilesy * d.Z;
+  const int64_t vol = d.vol();
+  // weights: w[co][ci][tap] copied as it is into the halo buffer with 16-byte
+  // loads, then rearranged to B[k][co], k = tap * CI + ci (zero for k >= KE)
+  constexpr int WBYTES = CO * CI * 27 * 2;
+  static_assert(WBYTES % 16 == 0 && WBYTES <= TC_A_HSTRIDE, "weights staged in the halo buffer");
+  {
+    constexpr int NV = WBYTES / 16, PER = (NV + 127) / 128;
+    uint4 v[PER];
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (u * 128 + tid < NV) v[u] = __ldg(reinterpret_cast<const uint4*>(w) + u * 128 + tid);
+#pragma unroll
+    for (int u = 0; u < PER; ++u)
+      if (u * 128 + tid < NV) reinterpret_cast<uint4*>(Hs)[u * 128 + tid] = v[u];
+  }
+  __syncthreads();
+  {
+    const __nv_bfloat16* ws = reinterpret_cast<const __nv_bfloat16*>(Hs);
+    for (int i = tid; i < 16 * KC * 8; i += 128) {
+      const int co = i / (KC * 8), k = i % (KC * 8), tap = k / CI, ci = k % CI;
+      const __nv_bfloat16 v = k < KE ? ws[(co * CI + ci) * 27 + tap] : __float2bfloat16_rn(0.f);
+      *reinterpret_cast<__nv_bfloat16*>(Bs + (co >> 3) * 1024 + (k >> 3) * 128 + (co & 7) * 16 + (k & 7) * 2) = v;
+    }
+  }
+  __syncthreads();   // the halo buffer is overwritten below
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+  }
+  asm volatile("fence.proxy.async.shared::cta;");
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tslot)),
+                 "r"(32));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t taddr = tslot;
+  // D f32, A and B bf16, both K-major, N = 16, M = 128
+  const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((16u >> 3) << 17) | ((128u >> 4) << 24);
+  const int m = tid, mx = m & 7, my = m >> 3;
+  bool ok = true;
+  uint32_t phase = 0;
+  for (int job = blockIdx.x; job < tiles * B && ok; job += gridDim.x, phase ^= 1u) {
+    const int b = job / tiles, tile = job % tiles;
+    const int tz0 = tile / (tilesx * tilesy);
+    const int ty0 = ((tile / tilesx) % tilesy) * CTY;
+    const int tx0 = (tile % tilesx) * CTX;
+    // halo: one tiled tensor copy (channel half 0) at (0, tx0 - 1, ty0 - 1,
+    // tz0 - 1, b); out-of-range voxels read as zero.  The previous tile's
+    // im2col is complete (block barrier below), so the buffer is free.
+    if (tid == 0) {
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&tbar)), "r"(TC_A_HALF)
+                   : "memory");
+      asm volatile(
+          "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+          "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];"
+          ::"r"(smem_u32(Hs)), "l"(reinterpret_cast<uint64_t>(&halo_map)), "r"(0), "r"(tx0 - 1), "r"(ty0 - 1),
+            "r"(tz0 - 1), "r"(b), "r"(smem_u32(&tbar))
+          : "memory");
+    }
+    const bool halo_ok = mbar_wait(smem_u32(&tbar), phase);
+    // the previous tile's MMAs (waited on) and tensor-memory reads are done
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    const int all_loaded = __syncthreads_and((int)halo_ok);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!all_loaded) {
+      if (tid == 0) {
+        atomicOr(flag, 1);
+        mbar_wait(smem_u32(&tbar), phase);
+      }
+      __syncthreads();
+      ok = false;
+      break;
+    }
+    // this thread's im2col row: 16-bit K elements, two per word
+    uint32_t kw[KC * 4];
+#pragma unroll
+    for (int j = 0; j < KC * 4; ++j) {
+      uint32_t v = 0u;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = 2 * j + h, tap = k / CI, ci = k % CI;
+        if (k < KE) {
+          const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+          const uint32_t e = *reinterpret_cast<const uint16_t*>(
+              Hs + ((dz * CHY + my + dy) * CHX + mx + dx) * 16 + ci * 2);
+          v |= e << (16 * h);
+        }
+      }
+      kw[j] = v;
+    }
+#pragma unroll
+    for (int c = 0; c < KC; ++c)
+      *reinterpret_cast<uint4*>(As + (m >> 3) * 1024 + c * 128 + (m & 7) * 16) =
+          make_uint4(kw[4 * c], kw[4 * c + 1], kw[4 * c + 2], kw[4 * c + 3]);
+    // the tile, written by threads, is read by the tensor cores
+    asm volatile("fence.proxy.async.shared::cta;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const uint32_t a0 = smem_u32(As), b0 = smem_u32(Bs);
+#pragma unroll
+      for (int kk = 0; kk < KS; ++kk) {
+        const uint64_t ad = umma_desc(a0 + kk * 256, 128, 1024);
+        const uint64_t bd = umma_desc(b0 + kk * 256, 128, 1024);
+        asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                     "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+                     ::"r"(taddr), "l"(ad), "l"(bd), "r"(idesc), "r"(kk > 0 ? 1 : 0));
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                   ::"r"(smem_u32(&mbar)));
+    }
+    const int gx = tx0 + mx, gy = ty0 + my, gz = tz0;
+    const bool inside = gx < d.X && gy < d.Y;
+    const int64_t p = ((int64_t)gz * d.Y + gy) * d.X + gx;
+    const int64_t ob = (int64_t)b * CO * vol;
+    float za[MODE == BWD_DATA ? CO : 1];
+    if constexpr (MODE == BWD_DATA) {
+#pragma unroll
+      for (int co = 0; co < CO; ++co) za[co] = inside ? __ldg(zaux + ob + (int64_t)co * vol + p) : 0.f;
+    }
+    const bool done = mbar_wait(smem_u32(&mbar), phase);
+    const int all_done = __syncthreads_and((int)done);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!all_done) {
+      if (tid == 0) atomicOr(flag, 1);
+      ok = false;
+      break;
+    }
+    uint32_t r[16];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                 "[%16];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                   "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+                   "=r"(r[15])
+                 : "r"(taddr + ((uint32_t)(warp * 32) << 16)));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+    if (inside) {
+      uint32_t packed[8];
+#pragma unroll
+      for (int co = 0; co < 16; ++co) {
+        const float acc = __uint_as_float(r[co]) + (bias ? bias[co] : 0.f);
+        const int64_t o = ob + (int64_t)co * vol + p;
+        float out;
+        if (MODE == FWD_HIDDEN) {
+          z[o] = acc;
+          out = gelu(acc);
+        } else if (MODE == INFER_HIDDEN) {
+          out = gelu(acc);
+        } else {
+          out = acc * gelu_grad(za[MODE == BWD_DATA ? co : 0]);
+        }
+        if (co % 2 == 0)
+          packed[co / 2] = bf16_bits(out);
+        else
+          packed[co / 2] |= bf16_bits(out) << 16;
+      }
+      static_assert(MODE != FWD_LAST, "the packed-K layers have 16 bf16 outputs");
+      uint4* dst = reinterpret_cast<uint4*>(act);
+      dst[((int64_t)b * 2 + 0) * vol + p] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+      dst[((int64_t)b * 2 + 1) * vol + p] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(32));
+}
+
+template <int CI, int CO, int MODE>
+static cudaError_t conv_k(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
+                          const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
+  if ((((uintptr_t)in | (uintptr_t)w) & 15u) != 0) return cudaErrorMisalignedAddress;
+  CUtensorMap map;
+  {
+    const cudaError_t e = halo_map(&map, in, d, B, halves(CI));
+    if (e != cudaSuccess) return e;
+  }
+  static int cap = 0;
+  if (!cap) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(conv_k_kernel<CI, CO, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, TK_SMEM);
+    if (e != cudaSuccess) return e;
+    // as many blocks per SM as shared memory admits (at most 8: 32 tensor-memory columns each)
+    cap = std::min(8, (227 * 1024) / (TK_SMEM + 2048)) * (sms > 0 ? sms : 1);
+  }
+  const int64_t jobs = (int64_t)((d.X + CTX - 1) / CTX) * ((d.Y + CTY - 1) / CTY) * d.Z * B;
+  const int grid = (int)(jobs < cap ? jobs : cap);
+  conv_k_kernel<CI, CO, MODE><<<grid, 128, TK_SMEM, st>>>(map, d, B, w, bias, z, act, zaux, flag);
+  return cudaGetLastError();
+}
+
 // Every layer on the tensor cores: fewer than 16 input or output channels
 // (2 -> 16, 16 -> 1, 1 -> 16) are padded with zero channels to K = 16 per tap
 // and N = 16 (the MMAs cost little; the halo loads and the stores skip the
@@ -438,7 +672,10 @@ template <int CI, int CO, int MODE>
 static cudaError_t conv(cudaStream_t st, const __nv_bfloat16* in, Dims d, int B, const __nv_bfloat16* w,
                         const float* bias, float* z, __nv_bfloat16* act, const float* zaux, int* flag) {
   static_assert(CI <= 16 && CO <= 16, "the tensor-core convolution takes up to 16 channels");
-  return conv_tc<CI, CO, MODE>(st, in, d, B, w, bias, z, act, zaux, flag);
+  if constexpr (CI <= 2)
+    return conv_k<CI, CO, MODE>(st, in, d, B, w, bias, z, act, zaux, flag);
+  else
+    return conv_tc<CI, CO, MODE>(st, in, d, B, w, bias, z, act, zaux, flag);
 }
 
 // ---------------------------------------------------------------------------
