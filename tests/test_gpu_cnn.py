@@ -135,6 +135,29 @@ def test_gradient_matches_oracle(M):
         o += n
 
 
+def test_gradient_matches_oracle_several_tiles_per_block(M):
+    # 5 crops of 32^3 = 1280 tiles of 8 x 16 voxels: more than the persistent
+    # grids of the convolutions (608 and 1064 blocks) and of the weight
+    # gradient (304), so blocks take two or more tiles (the two-stage pipelines,
+    # the accumulation over tiles in tensor memory, the mbarrier phases)
+    B, D = 5, 32
+    th = _params(8)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((B, 2, D, D, D)).astype(np.float32)
+    t = rng.standard_normal((B, 1, D, D, D)).astype(np.float32)
+    net = M.CNN((D, D, D), th, max_batch=B, crop=D, device=DEV)
+    g, loss = net.grad(_t(x), _t(t), B, D)
+    ref_loss, ref_g = C.loss_and_grad(th, x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - ref_loss) <= 1e-4 * ref_loss
+    g = g.cpu().numpy()
+    _check_elementwise(g, ref_g, _gradient_terms(th, x.astype(np.float64), t.astype(np.float64)), 1.0)
+    o = 0
+    for ci, co in C.LAYERS:
+        n = co * ci * 27 + co
+        assert _rel(g[o:o + n], ref_g[o:o + n]) <= 5e-3, (ci, co)
+        o += n
+
+
 def test_operator_weighted_gradient_matches_oracle(M):
     B, D = 2, 10
     th = _params(9)
