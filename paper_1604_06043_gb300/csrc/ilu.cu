@@ -401,12 +401,32 @@ __device__ __forceinline__ double chunk_solve(const ChunkArgs& a, const ChunkRow
   return sum;
 }
 
+// L1 prefetch of the static data of position idx (a hint: nothing is computed
+// from it; every address lies inside the packed arrays)
+template <int W>
+__device__ __forceinline__ void chunk_prefetch(const ChunkArgs& a, int idx) {
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a.prow + idx));
+  asm volatile("prefetch.global.L1 [%0];" ::"l"(a.pcnt + idx));
+#pragma unroll
+  for (int j = 0; j < W; ++j) {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a.pcol + (int64_t)j * a.npos + idx));
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a.pval + (int64_t)j * a.npos + idx));
+  }
+  if (a.pdiag) asm volatile("prefetch.global.L1 [%0];" ::"l"(a.pdiag + idx));
+}
+
 template <int W>
 __global__ void __launch_bounds__(CTS, 1) ilu_sweep_chunk_kernel(ChunkArgs a) {
   __shared__ double sv[2 * GMAX];   // the values of the previous and of the current group
   const int q0 = a.gofs[blockIdx.x], q1 = a.gofs[blockIdx.x + 1];
   for (int q = q0; q < q1; ++q) {
     const int beg = __ldg(a.gptr + q), end = __ldg(a.gptr + q + 1);
+    // the next group's static data on its way to L1 while this group waits
+    // on its dependencies
+    if (q + 1 < q1) {
+      const int nend = __ldg(a.gptr + q + 2);
+      for (int idx = end + threadIdx.x; idx < nend; idx += CTS) chunk_prefetch<W>(a, idx);
+    }
     const double* prev = sv + ((q - 1) & 1) * GMAX;
     double* cur = sv + (q & 1) * GMAX;
     for (int idx = beg + threadIdx.x; idx < end; idx += CTS) {
