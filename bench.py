@@ -571,6 +571,30 @@ def ilu_report(V, A, tv, create_ms):
 
 
 
+# bytes per voxel that the four convolutions of one inference read and write:
+# the half-major bf16 input (16 bytes per voxel and channel half) and output
+# (bf16 halves, or FP32 for the one-channel last layer)
+CNN_LAYER_BYTES = [16 * 1 + 32, 32 + 32, 32 + 32, 32 + 4]
+
+
+def cnn_roofline(n, inf_ms, peaks):
+    """The CNN inference against both of its roofs: useful convolution FLOPs
+    (2 n ci co 27 per layer) over the measured bf16 burst rate, and the
+    convolutions' algorithmic bytes over the measured HBM bandwidth."""
+    fl = sum(2 * n * ci * co * 27 for ci, co in ((2, 16), (16, 16), (16, 16), (16, 1)))
+    by = n * sum(CNN_LAYER_BYTES)
+    t = inf_ms * 1e-3
+    tf_peak = float(peaks.get("bf16_tflops", 1900.0))
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
+    src = "measured" if "bf16_tflops" in peaks and "hbm_gbs" in peaks else "fallback"
+    return {"tensor": {"achieved": round(fl / t / 1e12, 2), "peak": tf_peak, "unit": "TFLOP/s",
+                       "frac": round(fl / t / 1e12 / tf_peak, 4), "flops": fl},
+            "hbm": {"achieved": round(by / t / 1e9, 1), "peak": hbm_peak, "unit": "GB/s",
+                    "frac": round(by / t / 1e9 / hbm_peak, 4), "bytes": by},
+            "peak_source": src + " (MEASURED_PEAKS.json bf16_tflops, hbm_gbs)",
+            "note": "whole four-layer inference; per layer the tensor-core MMA count at N = 16 binds it"}
+
+
 def cnn_bench(args):
     """The learned-guess network alone on the 128^3 grid: inference (2 -> 16
     -> 16 -> 16 -> 1, 3x3x3; the two 16 -> 16 layers on the tensor cores) and
@@ -619,6 +643,12 @@ def cnn_bench(args):
             "inference_tflops": round(sum(fl) / (inf_ms * 1e-3) / 1e12, 2),
             "tensor_core_layer_gflop": [round(fl[1] / 1e9, 2), round(fl[2] / 1e9, 2)],
             "train_iter_ms": round(tr_ms, 4), "train_batch": "8 crops of 32^3"}
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    line["roofline"] = cnn_roofline(n, inf_ms, peaks)
     print(json.dumps(line), flush=True)
 
 

@@ -35,3 +35,17 @@ def test_reference_arm_without_a_record_reports_unavailable():
     assert out.returncode == 0, out.stderr[-2000:]
     line = json.loads(out.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and "unavailable" in line
+
+
+def test_cnn_roofline_fractions():
+    # 128^3 voxels in 0.46 ms: the FLOPs and bytes follow from the layer shapes
+    n = 128 ** 3
+    r = bench.cnn_roofline(n, 0.46, {"bf16_tflops": 2000.0, "hbm_gbs": 8000.0})
+    fl = 2 * n * 27 * (2 * 16 + 16 * 16 + 16 * 16 + 16 * 1)
+    assert r["tensor"]["flops"] == fl
+    assert abs(r["tensor"]["achieved"] - fl / 0.46e-3 / 1e12) < 0.01
+    assert abs(r["tensor"]["frac"] - r["tensor"]["achieved"] / 2000.0) < 1e-4
+    assert r["hbm"]["bytes"] == n * (48 + 64 + 64 + 36)
+    assert abs(r["hbm"]["frac"] - r["hbm"]["achieved"] / 8000.0) < 1e-4
+    assert r["peak_source"].startswith("measured")
+    assert bench.cnn_roofline(n, 0.46, {})["peak_source"].startswith("fallback")
